@@ -1,0 +1,208 @@
+/*
+ * qubo.h - C ABI of the GB300 exhaustive dense-QUBO solver (libqubo.so).
+ *
+ * The library scans all 2^n states x in {0,1}^n of E(x) = sum_{i,j} Q_ij x_i x_j (Sec. 1) and
+ * returns the exact minimum, every minimiser (the tie set) and optionally the K lowest
+ * states.  The scan is the prefix/suffix decomposition of Sec. 2 (eq. 3-4 and the chunk energy
+ * E(C_xp) = E_p(x_p) 1 + x_p M_int + E_s(U_B)) walked in Gray order (Sec. 3.2, eq. incremental
+ * update), split into independent work units by fixing leading bits (Sec. 3.3.1) and by
+ * columns (Sec. 3.3.2).
+ *
+ * Conventions shared by every entry point:
+ *   - State code: bit i of a uint64_t is variable i (LSB = variable 0).
+ *   - Q: n x n, row-major, element type given by qubo_dtype.  Every entry counts (the objective
+ *     sums over all i, j); an upper-triangular Q is the special case the paper uses (Sec. 2.1).
+ *   - Ownership: the caller owns every pointer it passes.  Pointers named *_host are host
+ *     memory; pointers named d_* are device memory of the current CUDA device.  The library
+ *     allocates and frees its own device scratch (kept per device and reused between calls).
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Unless stated otherwise a call has finished all its GPU work when it returns.
+ *   - Errors: every entry point returns a qubo_status; no exception crosses the ABI.  Outputs
+ *     are unspecified after a negative status.
+ *   - Threads: calls on different host threads are serialised on an internal per-device lock.
+ */
+#ifndef QUBO_H
+#define QUBO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Element type of Q. */
+typedef enum { QUBO_I16 = 1, QUBO_I32 = 2, QUBO_F32 = 3, QUBO_F64 = 4 } qubo_dtype;
+
+/* Accumulator the scan ran in (reported in qubo_result.acc). */
+typedef enum { QUBO_ACC_I32 = 1, QUBO_ACC_I64 = 2, QUBO_ACC_F32 = 3, QUBO_ACC_F64 = 4 } qubo_acc;
+
+typedef enum {
+    QUBO_OK = 0,
+    QUBO_TRUNCATED = 1,      /* warning: the tie set had more members than states_cap; the
+                                results are valid, n_ties is exact, out_states holds the
+                                states_cap smallest codes */
+    QUBO_ERR_ARG = -1,       /* bad argument: n<1, n>64, null pointer, bad dtype, topk, ... */
+    QUBO_ERR_OVERFLOW = -2,  /* integer energies cannot be bounded by any supported accumulator */
+    QUBO_ERR_CUDA = -3,      /* CUDA runtime error (no device, launch failure, ...) */
+    QUBO_ERR_NOMEM = -4,     /* device or host allocation failed */
+    QUBO_ERR_TIMEOUT = -5,   /* the time limit expired or qubo_abort() was called; partial */
+    QUBO_ERR_INTERNAL = -6   /* an internal consistency check failed (states scanned != 2^n) */
+} qubo_status;
+
+/* Largest supported K for the K-lowest-states output. */
+#define QUBO_MAX_TOPK 1024
+
+/* qubo_options.flags */
+#define QUBO_FLAG_PLAIN 0x1u  /* scan in the wide accumulator (int64 for integer Q, FP64 for
+                                 float Q) instead of int32 / FP32: the plain form used as the
+                                 comparison baseline */
+
+/*
+ * Per-call options.  Zero-initialise and set what you need; zero means "default".
+ */
+typedef struct {
+    int32_t split_k;      /* fixed bits per work unit (Sec. 3.3.1): 2^split_k units along the
+                             prefix; <= 0 chooses automatically */
+    int32_t topk;         /* K lowest states to return, 0..QUBO_MAX_TOPK (0 = none) */
+    int32_t fix_bits;     /* restrict the scan to the sub-cube whose top fix_bits code bits equal
+                             fix_value (Sec. 3.3.1 subproblem); 0 = whole cube */
+    int32_t walk_bits;    /* prefix bits walked in Gray order per unit; <= 0 = automatic */
+    uint64_t fix_value;
+    uint32_t flags;       /* QUBO_FLAG_* */
+    uint32_t reserved;
+    double margin;        /* float Q: candidate margin above the running FP32 minimum; states
+                             within it are rescored in FP64 (<= 0 means 1e-3) */
+    double time_limit_s;  /* wall-clock limit for the GPU work; <= 0 = none */
+} qubo_options;
+
+/*
+ * Result details (caller-allocated; filled on return).
+ */
+typedef struct {
+    int64_t min_i;            /* integer Q: the exact minimum energy */
+    double min_f;             /* float Q: the FP64 minimum (direct, fixed-order FP64 sum of the
+                                 folded upper-triangular matrix); integer Q: (double)min_i */
+    uint64_t n_ties;          /* exact number of states with E == min */
+    uint64_t n_written;       /* codes written to out_states (<= states_cap) */
+    int32_t truncated;        /* 1 if n_ties > states_cap */
+    int32_t acc;              /* qubo_acc the scan ran in */
+    int32_t n_topk;           /* entries written to out_topk (min(topk, states in the scan)) */
+    int32_t reserved0;
+    double fp32_max_abs_err;  /* float Q: max |E_scan - E_fp64| over the rescored candidates */
+    double fp32_max_drift;    /* float Q: max |incremental - recomputed| energy at re-anchoring */
+    uint64_t n_near_ties;     /* float Q: states within 1e-9*max(1,|min|) of min (among the
+                                 rescored candidates, which contain all of them) */
+    uint64_t states_scanned;  /* states evaluated by the scan; equals the sub-cube size */
+    uint64_t candidates;      /* states that passed the threshold and were recorded */
+    double seconds;           /* wall time of the call */
+    double seconds_gpu;       /* device time of tables + scan + finalize (CUDA events) */
+    double states_per_s;      /* states_scanned / seconds */
+    int32_t n, split_k, walk_bits, suffix_bits; /* plan: n = split_k + walk_bits + suffix_bits */
+    int32_t cols_per_thread, threads, blocks, passes; /* launch shape; passes > 1 if the
+                                 candidate buffer overflowed and the scan was repeated */
+} qubo_result;
+
+/*
+ * Solve one instance (Sec. 3.2 Alg. 2 generalised: min, full tie set, K lowest).
+ *   Q_host     n x n row-major host matrix of type dtype.
+ *   split_k    as qubo_options.split_k.   topk  as qubo_options.topk.
+ *   out_min    host; int64_t* for integer dtypes, double* for float dtypes.
+ *   out_states host array of states_cap codes: the smallest min(n_ties, states_cap) tie
+ *              codes in ascending order.  May be NULL when states_cap == 0.
+ *   out_topk   host array of topk codes ordered by (E, code) ascending (NULL if topk == 0).
+ *   out_topk_E host array of topk energies (int64_t or double, like out_min).
+ *   info       optional (may be NULL).
+ * Returns QUBO_OK, QUBO_TRUNCATED or a negative qubo_status.
+ */
+int qubo_solve(const void *Q_host, int n, qubo_dtype dtype, int split_k, int topk, void *out_min,
+               uint64_t *out_states, size_t states_cap, uint64_t *out_topk, void *out_topk_E,
+               qubo_result *info, void *stream);
+
+/* qubo_solve with every option (sub-cube restriction, plain accumulator, margin, time limit).
+ * opt may be NULL for defaults. */
+int qubo_solve_ex(const void *Q_host, int n, qubo_dtype dtype, const qubo_options *opt,
+                  void *out_min, uint64_t *out_states, size_t states_cap, uint64_t *out_topk,
+                  void *out_topk_E, qubo_result *info, void *stream);
+
+/*
+ * Solve `count` independent instances of uneven size in one persistent launch (the map-reduce
+ * of Sec. 3.3 across problems).  Instance i is the n[i] x n[i] row-major matrix starting
+ * offsets[i] elements into Q_packed (host).  Per instance i the outputs are:
+ *   out_min[i] (int64_t or double), out_states[i*states_cap_per_inst ...] (ascending tie codes),
+ *   out_topk[i*topk ...] and out_topk_E[i*topk ...] (may be NULL if topk == 0), info[i].
+ * Every instance needs 1 <= n[i] <= 40.  Returns the worst status over the instances.
+ */
+int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets, int count,
+                       qubo_dtype dtype, int topk, void *out_min, uint64_t *out_states,
+                       size_t states_cap_per_inst, uint64_t *out_topk, void *out_topk_E,
+                       qubo_result *info, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Device-resident problems: upload once, run many times (sub-cube by sub-cube), fetch.       */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct qubo_problem qubo_problem;
+
+/* Fold Q (host) into its upper-triangular form, check the integer bound, plan the scan and
+ * upload everything the GPU needs.  opt may be NULL.  *out receives the handle. */
+int qubo_problem_create(const void *Q_host, int n, qubo_dtype dtype, const qubo_options *opt,
+                        qubo_problem **out);
+
+/* Enqueue one full pass (tables, scan, finalize) over the sub-cube whose top fix_bits code
+ * bits equal fix_value, on `stream`.  Returns without waiting for the GPU. */
+int qubo_problem_run(qubo_problem *p, int fix_bits, uint64_t fix_value, void *stream);
+
+/* Wait for the last run, copy its results to the host buffers (same meaning as qubo_solve),
+ * repeating the scan if the candidate buffer overflowed. */
+int qubo_problem_fetch(qubo_problem *p, void *out_min, uint64_t *out_states, size_t states_cap,
+                       uint64_t *out_topk, void *out_topk_E, qubo_result *info);
+
+void qubo_problem_destroy(qubo_problem *p);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Result merge (map-reduce of Sec. 3.3: global result from the results of disjoint parts).  */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t is_float;         /* energies are double (1) or int64_t (0) */
+    int32_t n_topk;           /* valid entries in topk / topk_E */
+    int64_t min_i;
+    double min_f;
+    uint64_t n_ties;          /* exact tie count of this part */
+    uint64_t n_written;       /* valid entries in ties (ascending) */
+    uint64_t states_scanned;
+    uint64_t *ties;           /* caller-owned, capacity given to qubo_merge */
+    uint64_t *topk;           /* caller-owned, capacity topk */
+    void *topk_E;             /* caller-owned, int64_t or double */
+} qubo_partial;
+
+/* out = merge(a, b) over disjoint state sets: the smaller minimum wins, tie counts add when
+ * the minima are equal, tie codes are merged ascending and cut at cap, the K lowest are
+ * merged by (E, code).  out's arrays must hold cap and topk entries; out may alias neither
+ * input.  Host only. */
+int qubo_merge(const qubo_partial *a, const qubo_partial *b, size_t cap, int topk, qubo_partial *out);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Utilities.                                                                                 */
+/* ---------------------------------------------------------------------------------------- */
+
+/* Human-readable text of a qubo_status. */
+const char *qubo_strerror(int status);
+
+/* Ask every running call on this process to stop at its next work unit (returns
+ * QUBO_ERR_TIMEOUT).  Safe from any thread.  qubo_abort_clear() re-arms. */
+void qubo_abort(void);
+void qubo_abort_clear(void);
+
+/* Number of SMs of the current device, or a negative qubo_status. */
+int qubo_device_sm_count(void);
+
+/* Library version string. */
+const char *qubo_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QUBO_H */

@@ -1,0 +1,324 @@
+"""GB300 exhaustive dense-QUBO solver: Python binding of libqubo.so (include/qubo.h).
+
+Argument marshalling only: every step of the scan runs in the CUDA library.  The library must be
+built first (``paper_2607_04857_gb300.build.build()``); importing the functions below raises if it
+is missing, there is no fallback.
+
+Conventions (as in qubo.h): a state code holds variable i in bit i; Q is any n x n matrix and
+every entry counts, E(x) = sum_ij Q_ij x_i x_j.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqubo.so")
+
+QUBO_I16, QUBO_I32, QUBO_F32, QUBO_F64 = 1, 2, 3, 4
+ACC_NAMES = {1: "i32", 2: "i64", 3: "f32", 4: "f64"}
+QUBO_OK, QUBO_TRUNCATED = 0, 1
+QUBO_ERR_ARG, QUBO_ERR_OVERFLOW, QUBO_ERR_CUDA = -1, -2, -3
+QUBO_ERR_NOMEM, QUBO_ERR_TIMEOUT, QUBO_ERR_INTERNAL = -4, -5, -6
+QUBO_FLAG_PLAIN = 0x1
+MAX_TOPK = 1024
+
+# every entry point declared in include/qubo.h
+EXPORTS = (
+    "qubo_solve", "qubo_solve_ex", "qubo_solve_batched", "qubo_problem_create", "qubo_problem_run",
+    "qubo_problem_fetch", "qubo_problem_destroy", "qubo_merge", "qubo_strerror", "qubo_abort",
+    "qubo_abort_clear", "qubo_device_sm_count", "qubo_version",
+)
+
+
+class QuboError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("split_k", ctypes.c_int32), ("topk", ctypes.c_int32), ("fix_bits", ctypes.c_int32),
+        ("walk_bits", ctypes.c_int32), ("fix_value", ctypes.c_uint64), ("flags", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32), ("margin", ctypes.c_double), ("time_limit_s", ctypes.c_double),
+    ]
+
+
+class ResultInfo(ctypes.Structure):
+    _fields_ = [
+        ("min_i", ctypes.c_int64), ("min_f", ctypes.c_double), ("n_ties", ctypes.c_uint64),
+        ("n_written", ctypes.c_uint64), ("truncated", ctypes.c_int32), ("acc", ctypes.c_int32),
+        ("n_topk", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("fp32_max_abs_err", ctypes.c_double),
+        ("fp32_max_drift", ctypes.c_double), ("n_near_ties", ctypes.c_uint64),
+        ("states_scanned", ctypes.c_uint64), ("candidates", ctypes.c_uint64), ("seconds", ctypes.c_double),
+        ("seconds_gpu", ctypes.c_double), ("states_per_s", ctypes.c_double), ("n", ctypes.c_int32),
+        ("split_k", ctypes.c_int32), ("walk_bits", ctypes.c_int32), ("suffix_bits", ctypes.c_int32),
+        ("cols_per_thread", ctypes.c_int32), ("threads", ctypes.c_int32), ("blocks", ctypes.c_int32),
+        ("passes", ctypes.c_int32),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {name: getattr(self, name) for name, _ in self._fields_ if not name.startswith("reserved")}
+        d["acc"] = ACC_NAMES.get(d["acc"], d["acc"])
+        return d
+
+
+class Partial(ctypes.Structure):
+    _fields_ = [
+        ("is_float", ctypes.c_int32), ("n_topk", ctypes.c_int32), ("min_i", ctypes.c_int64),
+        ("min_f", ctypes.c_double), ("n_ties", ctypes.c_uint64), ("n_written", ctypes.c_uint64),
+        ("states_scanned", ctypes.c_uint64), ("ties", ctypes.c_void_p), ("topk", ctypes.c_void_p),
+        ("topk_E", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libqubo.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2607_04857_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, I, U64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t
+    lib.qubo_solve.argtypes = [P, I, I, I, I, P, P, SZ, P, P, P, P]
+    lib.qubo_solve_ex.argtypes = [P, I, I, P, P, P, SZ, P, P, P, P]
+    lib.qubo_solve_batched.argtypes = [P, P, P, I, I, I, P, P, SZ, P, P, P, P]
+    lib.qubo_problem_create.argtypes = [P, I, I, P, P]
+    lib.qubo_problem_run.argtypes = [P, I, U64, P]
+    lib.qubo_problem_fetch.argtypes = [P, P, P, SZ, P, P, P]
+    lib.qubo_problem_destroy.argtypes = [P]
+    lib.qubo_problem_destroy.restype = None
+    lib.qubo_merge.argtypes = [P, P, SZ, I, P]
+    lib.qubo_strerror.argtypes = [I]
+    lib.qubo_strerror.restype = ctypes.c_char_p
+    lib.qubo_version.restype = ctypes.c_char_p
+    lib.qubo_abort.restype = None
+    lib.qubo_abort_clear.restype = None
+    for name in ("qubo_solve", "qubo_solve_ex", "qubo_solve_batched", "qubo_problem_create", "qubo_problem_run",
+                 "qubo_problem_fetch", "qubo_merge", "qubo_device_sm_count"):
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def strerror(status: int) -> str:
+    return load_library().qubo_strerror(int(status)).decode()
+
+
+def version() -> str:
+    return load_library().qubo_version().decode()
+
+
+def device_sm_count() -> int:
+    r = load_library().qubo_device_sm_count()
+    if r < 0:
+        raise QuboError(r, "qubo_device_sm_count")
+    return r
+
+
+def abort() -> None:
+    load_library().qubo_abort()
+
+
+def abort_clear() -> None:
+    load_library().qubo_abort_clear()
+
+
+def _stream_ptr(stream):
+    """cudaStream_t as an integer: an int, an object with .cuda_stream (torch), or the current
+    torch stream when torch with CUDA is available; else the default stream."""
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return int(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+def as_qubo_matrix(Q):
+    """numpy matrix and its qubo_dtype (int16/int32/float32/float64; int64 narrowed if exact)."""
+    if hasattr(Q, "detach"):  # torch tensor on the host
+        Q = Q.detach().cpu().numpy()
+    Q = np.asarray(Q)
+    if Q.ndim != 2 or Q.shape[0] != Q.shape[1]:
+        raise ValueError("Q must be a square matrix")
+    if Q.dtype == np.int16:
+        return np.ascontiguousarray(Q), QUBO_I16
+    if Q.dtype.kind in "iub":
+        Q32 = Q.astype(np.int32)
+        if not np.array_equal(Q32, Q):
+            raise ValueError("integer Q must fit in int32")
+        return np.ascontiguousarray(Q32), QUBO_I32
+    if Q.dtype == np.float32:
+        return np.ascontiguousarray(Q), QUBO_F32
+    if Q.dtype.kind == "f":
+        return np.ascontiguousarray(Q, dtype=np.float64), QUBO_F64
+    raise ValueError(f"unsupported dtype {Q.dtype}")
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data) if a.size else None
+
+
+@dataclass
+class Result:
+    min: object                      # int (integer Q) or float (float Q)
+    n_ties: int                      # exact number of minimisers
+    ties: np.ndarray                 # smallest tie codes ascending (<= states_cap), uint64
+    topk: np.ndarray                 # K lowest codes by (E, code)
+    topk_E: np.ndarray
+    status: int = 0
+    info: dict = field(default_factory=dict)
+
+    @property
+    def truncated(self) -> bool:
+        return self.n_ties > len(self.ties)
+
+
+def _check(st: int, where: str) -> int:
+    if st < 0:
+        raise QuboError(st, where)
+    return st
+
+
+def solve(Q, topk: int = 0, states_cap: int = 1 << 16, split_k: int = 0, walk_bits: int = 0, fix_bits: int = 0,
+          fix_value: int = 0, plain: bool = False, margin: float = 0.0, time_limit: float = 0.0,
+          stream=None) -> Result:
+    """Exact minimum, tie set and K lowest states (qubo_solve_ex)."""
+    lib = load_library()
+    Qm, dt = as_qubo_matrix(Q)
+    n = Qm.shape[0]
+    isf = dt in (QUBO_F32, QUBO_F64)
+    edt = np.float64 if isf else np.int64
+    o = Options(split_k=split_k, topk=topk, fix_bits=fix_bits, walk_bits=walk_bits, fix_value=fix_value,
+                flags=QUBO_FLAG_PLAIN if plain else 0, margin=margin, time_limit_s=time_limit)
+    mn = np.zeros(1, dtype=edt)
+    ties = np.zeros(max(states_cap, 0), dtype=np.uint64)
+    tk = np.zeros(max(topk, 0), dtype=np.uint64)
+    tkE = np.zeros(max(topk, 0), dtype=edt)
+    info = ResultInfo()
+    st = lib.qubo_solve_ex(_ptr(Qm), n, dt, ctypes.byref(o), _ptr(mn), _ptr(ties), states_cap, _ptr(tk), _ptr(tkE),
+                           ctypes.byref(info), _stream_ptr(stream))
+    _check(st, "qubo_solve_ex")
+    k = info.n_topk
+    return Result(float(mn[0]) if isf else int(mn[0]), int(info.n_ties), ties[: info.n_written].copy(), tk[:k].copy(),
+                  tkE[:k].copy(), st, info.as_dict())
+
+
+def solve_batched(Qs, topk: int = 0, states_cap: int = 64, stream=None) -> list[Result]:
+    """Solve many instances in one persistent launch (qubo_solve_batched).  All matrices must
+    share one dtype."""
+    lib = load_library()
+    mats = [as_qubo_matrix(Q) for Q in Qs]
+    dts = {d for _, d in mats}
+    if len(dts) != 1:
+        raise ValueError("all instances of a batch must share one dtype")
+    dt = dts.pop()
+    ns = np.array([m.shape[0] for m, _ in mats], dtype=np.int32)
+    offs = np.zeros(len(mats), dtype=np.uint64)
+    offs[1:] = np.cumsum(ns[:-1].astype(np.uint64) ** 2)
+    packed = np.concatenate([m.ravel() for m, _ in mats])
+    count = len(mats)
+    isf = dt in (QUBO_F32, QUBO_F64)
+    edt = np.float64 if isf else np.int64
+    mn = np.zeros(count, dtype=edt)
+    ties = np.zeros(count * states_cap, dtype=np.uint64)
+    tk = np.zeros(count * topk, dtype=np.uint64)
+    tkE = np.zeros(count * topk, dtype=edt)
+    infos = (ResultInfo * count)()
+    st = lib.qubo_solve_batched(_ptr(packed), _ptr(ns), _ptr(offs), count, dt, topk, _ptr(mn), _ptr(ties),
+                                states_cap, _ptr(tk), _ptr(tkE), infos, _stream_ptr(stream))
+    _check(st, "qubo_solve_batched")
+    out = []
+    for i in range(count):
+        inf = infos[i]
+        k = inf.n_topk
+        out.append(Result(float(mn[i]) if isf else int(mn[i]), int(inf.n_ties),
+                          ties[i * states_cap: i * states_cap + inf.n_written].copy(),
+                          tk[i * topk: i * topk + k].copy(), tkE[i * topk: i * topk + k].copy(),
+                          QUBO_TRUNCATED if inf.n_ties > states_cap else QUBO_OK, inf.as_dict()))
+    return out
+
+
+class Problem:
+    """Device-resident problem: upload once, run sub-cubes, fetch (qubo_problem_*)."""
+
+    def __init__(self, Q, topk: int = 0, split_k: int = 0, walk_bits: int = 0, plain: bool = False,
+                 margin: float = 0.0, time_limit: float = 0.0):
+        self._lib = load_library()
+        Qm, dt = as_qubo_matrix(Q)
+        self.n = Qm.shape[0]
+        self.topk = topk
+        self.is_float = dt in (QUBO_F32, QUBO_F64)
+        o = Options(split_k=split_k, topk=topk, walk_bits=walk_bits, flags=QUBO_FLAG_PLAIN if plain else 0,
+                    margin=margin, time_limit_s=time_limit)
+        h = ctypes.c_void_p()
+        _check(self._lib.qubo_problem_create(_ptr(Qm), self.n, dt, ctypes.byref(o), ctypes.byref(h)),
+               "qubo_problem_create")
+        self._h = h
+
+    def run(self, fix_bits: int = 0, fix_value: int = 0, stream=None) -> None:
+        _check(self._lib.qubo_problem_run(self._h, fix_bits, fix_value, _stream_ptr(stream)), "qubo_problem_run")
+
+    def fetch(self, states_cap: int = 1 << 16) -> Result:
+        edt = np.float64 if self.is_float else np.int64
+        mn = np.zeros(1, dtype=edt)
+        ties = np.zeros(states_cap, dtype=np.uint64)
+        tk = np.zeros(self.topk, dtype=np.uint64)
+        tkE = np.zeros(self.topk, dtype=edt)
+        info = ResultInfo()
+        st = _check(self._lib.qubo_problem_fetch(self._h, _ptr(mn), _ptr(ties), states_cap, _ptr(tk), _ptr(tkE),
+                                                 ctypes.byref(info)), "qubo_problem_fetch")
+        k = info.n_topk
+        return Result(float(mn[0]) if self.is_float else int(mn[0]), int(info.n_ties),
+                      ties[: info.n_written].copy(), tk[:k].copy(), tkE[:k].copy(), st, info.as_dict())
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.qubo_problem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def merge(a: Result, b: Result, states_cap: int, topk: int) -> Result:
+    """Merge the results of two disjoint state sets (qubo_merge)."""
+    lib = load_library()
+    isf = isinstance(a.min, float)
+    edt = np.float64 if isf else np.int64
+
+    def part(r: Result, keep):
+        ties = np.ascontiguousarray(r.ties, dtype=np.uint64)
+        tk = np.ascontiguousarray(r.topk, dtype=np.uint64)
+        tkE = np.ascontiguousarray(r.topk_E, dtype=edt)
+        keep.extend([ties, tk, tkE])
+        return Partial(is_float=int(isf), n_topk=len(tk), min_i=0 if isf else int(r.min), min_f=float(r.min),
+                       n_ties=r.n_ties, n_written=len(ties), states_scanned=int(r.info.get("states_scanned", 1)),
+                       ties=ties.ctypes.data if ties.size else None, topk=tk.ctypes.data if tk.size else None,
+                       topk_E=tkE.ctypes.data if tkE.size else None)
+
+    keep = []
+    pa, pb = part(a, keep), part(b, keep)
+    ot = np.zeros(max(states_cap, 1), dtype=np.uint64)
+    ok = np.zeros(max(topk, 1), dtype=np.uint64)
+    okE = np.zeros(max(topk, 1), dtype=edt)
+    po = Partial(ties=ot.ctypes.data, topk=ok.ctypes.data, topk_E=okE.ctypes.data)
+    _check(lib.qubo_merge(ctypes.byref(pa), ctypes.byref(pb), states_cap, topk, ctypes.byref(po)), "qubo_merge")
+    mval = po.min_f if isf else po.min_i
+    return Result(float(mval) if isf else int(mval), int(po.n_ties), ot[: po.n_written].copy(),
+                  ok[: po.n_topk].copy(), okE[: po.n_topk].copy(), 0,
+                  {"states_scanned": int(po.states_scanned)})

@@ -1,0 +1,1377 @@
+// Host driver of libqubo.so: input folding and bound check, planning, the initial threshold,
+// device workspace, kernel sequencing, the time limit, result merging, and the C ABI of qubo.h.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <random>
+#include <thread>
+#include <unordered_set>
+#include <utility>
+#include <vector>
+
+#include "../../include/qubo.h"
+#include "internal.h"
+
+using namespace qubo;
+
+namespace {
+
+constexpr unsigned long long kDefaultRecCap = 1ull << 22;  // candidate records per job (64 MiB)
+constexpr double kDefaultMargin = 1e-3;
+constexpr int kTargetUnitsLog2 = 15;   // aim for >= 2^15 work units per scan
+constexpr int kDefaultMaxWalkBits = 12;
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------------------------------------------
+// Host-side preparation of one instance.
+// ------------------------------------------------------------------------------------------------
+
+struct HostInst {
+    int n = 0;
+    bool is_float = false;
+    Acc acc = ACC_I32;
+    std::vector<int64_t> Ui;  // folded upper-triangular (integer Q)
+    std::vector<double> Uf;   // folded upper-triangular (float Q), FP64
+    double beta = 0.0;        // sum |U_ij|
+    // plan of the current run
+    int B = 0, L = 0, k = 0, small = 0;
+    int fix_bits = 0;
+    uint64_t fix_value = 0;
+    uint64_t unit_begin = 0, units = 0, sub_base = 0, sub_count = 0;
+    uint64_t items = 0, states = 0;
+    double thr0 = 0.0;  // initial threshold (a bound on the K-th lowest energy of the range)
+};
+
+bool dtype_ok(qubo_dtype dt) { return dt == QUBO_I16 || dt == QUBO_I32 || dt == QUBO_F32 || dt == QUBO_F64; }
+bool dtype_float(qubo_dtype dt) { return dt == QUBO_F32 || dt == QUBO_F64; }
+
+// Fold Q into U (U_ii = Q_ii, U_ij = Q_ij + Q_ji for i < j) and choose the accumulator.
+int prepare(const void *Q, int n, qubo_dtype dt, uint32_t flags, HostInst &h)
+{
+    if (!Q || n < 1 || n > 64 || !dtype_ok(dt))
+        return QUBO_ERR_ARG;
+    h = HostInst();
+    h.n = n;
+    h.is_float = dtype_float(dt);
+    auto qi = [&](int i, int j) -> int64_t {
+        const size_t o = (size_t)i * n + j;
+        return dt == QUBO_I16 ? (int64_t)((const int16_t *)Q)[o] : (int64_t)((const int32_t *)Q)[o];
+    };
+    auto qf = [&](int i, int j) -> double {
+        const size_t o = (size_t)i * n + j;
+        return dt == QUBO_F32 ? (double)((const float *)Q)[o] : ((const double *)Q)[o];
+    };
+    if (h.is_float) {
+        h.Uf.assign((size_t)n * n, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int j = i; j < n; ++j) {
+                const double v = i == j ? qf(i, i) : qf(i, j) + qf(j, i);
+                if (!std::isfinite(v))
+                    return QUBO_ERR_ARG;
+                h.Uf[(size_t)i * n + j] = v;
+                h.beta += std::fabs(v);
+            }
+        h.acc = (flags & QUBO_FLAG_PLAIN) ? ACC_F64 : ACC_F32;
+    } else {
+        h.Ui.assign((size_t)n * n, 0);
+        int64_t beta = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i; j < n; ++j) {
+                const int64_t v = i == j ? qi(i, i) : qi(i, j) + qi(j, i);
+                h.Ui[(size_t)i * n + j] = v;
+                beta += v < 0 ? -v : v;
+            }
+        h.beta = (double)beta;
+        // Every partial sum the scan forms (table entries, running energies, thresholds minus a
+        // prefix energy) is bounded by 2*beta in magnitude: int32 is exact when beta < 2^30.
+        if (beta >= (1ll << 62))
+            return QUBO_ERR_OVERFLOW;
+        h.acc = ((flags & QUBO_FLAG_PLAIN) || beta >= (1ll << 30)) ? ACC_I64 : ACC_I32;
+    }
+    return QUBO_OK;
+}
+
+int acc_bytes(Acc a) { return (a == ACC_I32 || a == ACC_F32) ? 4 : 8; }
+
+int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bits)
+{
+    const int n = h.n;
+    if (fix_bits < 0 || fix_bits > n || (fix_bits < 64 && fix_bits > 0 && (fix_value >> fix_bits) != 0))
+        return QUBO_ERR_ARG;
+    if (fix_bits == 0)
+        fix_value = 0;
+    h.fix_bits = fix_bits;
+    h.fix_value = fix_value;
+    const int free_bits = n - fix_bits;
+    if (free_bits > 63)
+        return QUBO_ERR_ARG;
+    h.states = 1ull << free_bits;
+    h.B = suffix_bits(acc_bytes(h.acc));
+    if (free_bits < h.B + kRegRows + 1) {
+        h.small = 1;
+        h.L = h.k = 0;
+        h.sub_base = fix_bits ? (fix_value << free_bits) : 0;
+        h.sub_count = h.states;
+        h.units = 0;
+        h.items = 1;
+        return QUBO_OK;
+    }
+    h.small = 0;
+    int L;
+    if (split_k > 0)
+        L = n - h.B - split_k;
+    else if (walk_bits > 0)
+        L = walk_bits;
+    else
+        L = std::max(kRegRows + 1, std::min(kDefaultMaxWalkBits, free_bits - h.B - kTargetUnitsLog2));
+    const int k = n - h.B - L;
+    if (L < kRegRows + 1 || L > kMaxWalkBits || k < fix_bits || k > 63)
+        return QUBO_ERR_ARG;
+    h.L = L;
+    h.k = k;
+    h.units = 1ull << (k - fix_bits);
+    h.unit_begin = fix_bits ? (fix_value << (k - fix_bits)) : 0;
+    h.items = h.units;
+    return QUBO_OK;
+}
+
+// Upper bound on the K-th lowest energy (with multiplicity) of the run's sub-cube: the K-th lowest
+// energy among distinct states met by greedy one-flip descents from seeded random starts.  Any
+// K distinct states of the range bound it from above; with fewer than K found, beta does.
+double threshold_bound(const HostInst &h, int K)
+{
+    const int n = h.n, fb = h.fix_bits, free_bits = n - fb;
+    const uint64_t base = fb ? (h.fix_value << free_bits) : 0;
+    const uint64_t fmask = free_bits >= 64 ? ~0ull : ((1ull << free_bits) - 1);
+    auto U = [&](int i, int j) -> double {
+        if (i > j)
+            std::swap(i, j);
+        return h.is_float ? h.Uf[(size_t)i * n + j] : (double)h.Ui[(size_t)i * n + j];
+    };
+    auto energy = [&](uint64_t x) {
+        double acc = 0.0;
+        for (int i = 0; i < n; ++i) {
+            if (!((x >> i) & 1))
+                continue;
+            acc += U(i, i);
+            for (int j = i + 1; j < n; ++j)
+                if ((x >> j) & 1)
+                    acc += U(i, j);
+        }
+        return acc;
+    };
+    std::vector<std::pair<double, uint64_t>> seen;
+    std::unordered_set<uint64_t> codes;
+    auto offer = [&](double E, uint64_t x) {
+        if (codes.insert(x).second)
+            seen.emplace_back(E, x);
+    };
+    std::mt19937_64 rng(0x9e3779b97f4a7c15ull ^ h.fix_value ^ ((uint64_t)n << 56));
+    const int restarts = 24;
+    std::vector<double> hf(n);
+    for (int r = 0; r < restarts; ++r) {
+        uint64_t x = base | (r == 0 ? 0 : (rng() & fmask));
+        double E = energy(x);
+        for (int j = 0; j < n; ++j) {
+            double a = 0.0;
+            for (int i = 0; i < n; ++i)
+                if (i != j && ((x >> i) & 1))
+                    a += U(i, j);
+            hf[j] = a;
+        }
+        for (int it = 0; it < 4 * n + 8; ++it) {
+            int best = -1;
+            double bd = 0.0;
+            for (int v = 0; v < free_bits; ++v) {
+                const double d = ((x >> v) & 1) ? -(U(v, v) + hf[v]) : (U(v, v) + hf[v]);
+                if (d < bd) {
+                    bd = d;
+                    best = v;
+                }
+            }
+            if (best < 0)
+                break;
+            const bool up = !((x >> best) & 1);
+            x ^= 1ull << best;
+            E += bd;
+            for (int j = 0; j < n; ++j)
+                if (j != best)
+                    hf[j] += up ? U(best, j) : -U(best, j);
+        }
+        // the local minimum and all its one-flip neighbours
+        offer(E, x);
+        for (int v = 0; v < free_bits; ++v)
+            offer(E + (((x >> v) & 1) ? -(U(v, v) + hf[v]) : (U(v, v) + hf[v])), x ^ (1ull << v));
+    }
+    if ((int)seen.size() < K)
+        return h.beta;
+    std::nth_element(seen.begin(), seen.begin() + (K - 1), seen.end());
+    double t = seen[K - 1].first;
+    if (h.is_float) {
+        // the incremental energies above differ from the exact ones by rounding only
+        t = energy(seen[K - 1].second);
+        t += 1e-9 * (1.0 + h.beta);
+    } else {
+        t = std::nearbyint(t);
+    }
+    return std::min(t, h.beta);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Encodings shared with the device (ordered integers for atomics).
+// ------------------------------------------------------------------------------------------------
+
+uint32_t ord32h(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+uint64_t ord64h(double d)
+{
+    uint64_t u;
+    std::memcpy(&u, &d, 8);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+double bits_to_double(int64_t b)
+{
+    double d;
+    std::memcpy(&d, &b, 8);
+    return d;
+}
+double ubits_to_double(unsigned long long b)
+{
+    double d;
+    std::memcpy(&d, &b, 8);
+    return d;
+}
+
+unsigned long long encode_thr(Acc acc, double t)
+{
+    switch (acc) {
+    case ACC_I32: return (unsigned long long)(uint32_t)(int32_t)t;
+    case ACC_I64: return (unsigned long long)(int64_t)t;
+    case ACC_F32: {
+        float f = (float)t;
+        if ((double)f < t)
+            f = std::nextafter(f, INFINITY);
+        return ord32h(f);
+    }
+    case ACC_F64: return ord64h(t);
+    }
+    return 0;
+}
+
+unsigned long long encode_max(Acc acc)
+{
+    switch (acc) {
+    case ACC_I32: return (unsigned long long)(uint32_t)INT32_MAX;
+    case ACC_I64: return (unsigned long long)INT64_MAX;
+    case ACC_F32: return ord32h(INFINITY);
+    case ACC_F64: return ord64h(INFINITY);
+    }
+    return 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Partial results and their merge (map-reduce of Sec. 3.3).
+// ------------------------------------------------------------------------------------------------
+
+struct Part {
+    bool has = false;
+    bool is_float = false;
+    int64_t min_i = 0;
+    double min_f = 0.0;
+    uint64_t n_ties = 0, n_near = 0;
+    std::vector<uint64_t> ties;                    // ascending, <= cap
+    std::vector<std::pair<double, uint64_t>> topf;  // float: (E, code) ascending
+    std::vector<std::pair<int64_t, uint64_t>> topi; // int
+    uint64_t scanned = 0, candidates = 0;
+    double drift = 0.0, err = 0.0;
+    bool overflow = false;
+};
+
+bool part_less_min(const Part &a, const Part &b)
+{
+    return a.is_float ? a.min_f < b.min_f : a.min_i < b.min_i;
+}
+bool part_eq_min(const Part &a, const Part &b) { return a.is_float ? a.min_f == b.min_f : a.min_i == b.min_i; }
+
+Part merge_parts(const Part &a, const Part &b, size_t cap, int K)
+{
+    if (!a.has)
+        return b;
+    if (!b.has)
+        return a;
+    Part o;
+    o.has = true;
+    o.is_float = a.is_float;
+    o.scanned = a.scanned + b.scanned;
+    o.candidates = a.candidates + b.candidates;
+    o.drift = std::max(a.drift, b.drift);
+    o.err = std::max(a.err, b.err);
+    o.overflow = a.overflow || b.overflow;
+    if (part_eq_min(a, b)) {
+        o.min_i = a.min_i;
+        o.min_f = a.min_f;
+        o.n_ties = a.n_ties + b.n_ties;
+        o.n_near = a.n_near + b.n_near;
+        o.ties.resize(a.ties.size() + b.ties.size());
+        std::merge(a.ties.begin(), a.ties.end(), b.ties.begin(), b.ties.end(), o.ties.begin());
+        if (o.ties.size() > cap)
+            o.ties.resize(cap);
+    } else {
+        const Part &w = part_less_min(a, b) ? a : b;
+        o.min_i = w.min_i;
+        o.min_f = w.min_f;
+        o.n_ties = w.n_ties;
+        o.n_near = w.n_near;
+        o.ties = w.ties;
+    }
+    o.topf.resize(a.topf.size() + b.topf.size());
+    std::merge(a.topf.begin(), a.topf.end(), b.topf.begin(), b.topf.end(), o.topf.begin());
+    if ((int)o.topf.size() > K)
+        o.topf.resize(K);
+    o.topi.resize(a.topi.size() + b.topi.size());
+    std::merge(a.topi.begin(), a.topi.end(), b.topi.begin(), b.topi.end(), o.topi.begin());
+    if ((int)o.topi.size() > K)
+        o.topi.resize(K);
+    return o;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Device workspace: grow-only buffers per device, reused between calls.
+// ------------------------------------------------------------------------------------------------
+
+std::atomic<int> g_abort_all{0};
+
+struct Workspace {
+    int dev = -1;
+    int sms = 0;
+    void *d_arena = nullptr;
+    size_t arena_cap = 0;
+    Rec *d_rec = nullptr;
+    unsigned long long rec_cap = 0;
+    void *h_up = nullptr;
+    size_t up_cap = 0;
+    void *h_down = nullptr;
+    size_t down_cap = 0;
+    int *h_abort = nullptr;        // host-mapped flag read by the scan kernel
+    const int *d_abort = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    std::mutex mu;
+
+    ~Workspace() { release(); }
+
+    void release()
+    {
+        if (dev < 0)
+            return;
+        int cur = -1;
+        cudaGetDevice(&cur);
+        cudaSetDevice(dev);
+        if (d_arena)
+            cudaFree(d_arena);
+        if (d_rec)
+            cudaFree(d_rec);
+        if (h_up)
+            cudaFreeHost(h_up);
+        if (h_down)
+            cudaFreeHost(h_down);
+        if (h_abort)
+            cudaFreeHost(h_abort);
+        for (auto &e : ev)
+            if (e)
+                cudaEventDestroy(e);
+        if (cur >= 0)
+            cudaSetDevice(cur);
+        d_arena = nullptr;
+        d_rec = nullptr;
+        h_up = h_down = nullptr;
+        h_abort = nullptr;
+        dev = -1;
+    }
+
+    int init(int device)
+    {
+        if (dev == device)
+            return QUBO_OK;
+        release();
+        cudaDeviceProp prop;
+        if (cudaGetDeviceProperties(&prop, device) != cudaSuccess)
+            return QUBO_ERR_CUDA;
+        sms = prop.multiProcessorCount;
+        if (cudaHostAlloc((void **)&h_abort, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
+            return QUBO_ERR_NOMEM;
+        *h_abort = 0;
+        int *dp = nullptr;
+        if (cudaHostGetDevicePointer((void **)&dp, h_abort, 0) != cudaSuccess)
+            return QUBO_ERR_CUDA;
+        d_abort = dp;
+        for (auto &e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess)
+                return QUBO_ERR_CUDA;
+        dev = device;
+        return QUBO_OK;
+    }
+
+    static int grow_dev(void **p, size_t *cap, size_t need)
+    {
+        if (*cap >= need)
+            return QUBO_OK;
+        if (*p)
+            cudaFree(*p);
+        *p = nullptr;
+        *cap = 0;
+        size_t sz = std::max(need, (size_t)1 << 20);
+        if (cudaMalloc(p, sz) != cudaSuccess) {
+            cudaGetLastError();
+            return QUBO_ERR_NOMEM;
+        }
+        *cap = sz;
+        return QUBO_OK;
+    }
+    static int grow_host(void **p, size_t *cap, size_t need)
+    {
+        if (*cap >= need)
+            return QUBO_OK;
+        if (*p)
+            cudaFreeHost(*p);
+        *p = nullptr;
+        *cap = 0;
+        size_t sz = std::max(need, (size_t)1 << 20);
+        if (cudaMallocHost(p, sz) != cudaSuccess) {
+            cudaGetLastError();
+            return QUBO_ERR_NOMEM;
+        }
+        *cap = sz;
+        return QUBO_OK;
+    }
+    int ensure(size_t arena, unsigned long long recs, size_t up, size_t down)
+    {
+        int st;
+        if ((st = grow_dev(&d_arena, &arena_cap, arena)))
+            return st;
+        if (rec_cap < recs) {
+            if (d_rec)
+                cudaFree(d_rec);
+            d_rec = nullptr;
+            rec_cap = 0;
+            if (cudaMalloc((void **)&d_rec, sizeof(Rec) * recs) != cudaSuccess) {
+                cudaGetLastError();
+                return QUBO_ERR_NOMEM;
+            }
+            rec_cap = recs;
+        }
+        if ((st = grow_host(&h_up, &up_cap, up)))
+            return st;
+        return grow_host(&h_down, &down_cap, down);
+    }
+};
+
+std::mutex g_ws_mu;
+Workspace *g_ws[64] = {};
+std::vector<Workspace *> g_all_ws;
+
+Workspace *shared_workspace(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    if (dev < 0 || dev >= 64)
+        return nullptr;
+    if (!g_ws[dev]) {
+        g_ws[dev] = new (std::nothrow) Workspace();
+        if (g_ws[dev])
+            g_all_ws.push_back(g_ws[dev]);
+    }
+    return g_ws[dev];
+}
+
+void register_ws(Workspace *w)
+{
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    g_all_ws.push_back(w);
+}
+void unregister_ws(Workspace *w)
+{
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    g_all_ws.erase(std::remove(g_all_ws.begin(), g_all_ws.end(), w), g_all_ws.end());
+}
+
+// Candidate-buffer records per job; QUBO_MAX_RECORDS lowers it (exercises the overflow path).
+unsigned long long record_capacity()
+{
+    const char *v = std::getenv("QUBO_MAX_RECORDS");
+    if (v) {
+        const unsigned long long x = std::strtoull(v, nullptr, 10);
+        if (x >= 1 && x < kDefaultRecCap)
+            return x;
+    }
+    return kDefaultRecCap;
+}
+
+int scan_variant()
+{
+    const char *v = std::getenv("QUBO_SCAN_VARIANT");
+    if (!v)
+        return 0;
+    const int x = std::atoi(v);
+    return (x >= 0 && x < kScanVariants) ? x : 0;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            cudaGetLastError();                                                                    \
+            return QUBO_ERR_CUDA;                                                                  \
+        }                                                                                          \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ------------------------------------------------------------------------------------------------
+// One job: a set of instances with one accumulator type, scanned by one persistent launch.
+// ------------------------------------------------------------------------------------------------
+
+struct Job {
+    std::vector<HostInst *> insts;
+    Acc acc = ACC_I32;
+    int K = 0;
+    size_t cap = 0;      // tie codes kept per instance
+    double margin = 0.0;
+    double time_limit = 0.0;
+    int variant = 0;
+    cudaStream_t stream = nullptr;
+    // layout (byte offsets into the arena)
+    size_t off_inst = 0, off_state = 0, off_items = 0, up_bytes = 0;
+    size_t off_res = 0, off_ties = 0, off_topk = 0, off_topke = 0, off_starts = 0, off_ctr = 0;
+    size_t arena_bytes = 0, down_bytes = 0;
+    std::vector<size_t> off_W, off_W64, off_U64, off_Es, off_M, off_EL;
+    int max_entries = 0;
+    int blocks = 0;
+    unsigned long long rec_cap = 0;
+    double t_start = 0.0;
+    bool aborted = false;
+};
+
+int job_layout(Job &j)
+{
+    const int ni = (int)j.insts.size();
+    const int eb = acc_bytes(j.acc);
+    size_t o = 0;
+    j.off_inst = o;
+    o = align_up(o + sizeof(Inst) * ni, 256);
+    j.off_state = o;
+    o = align_up(o + sizeof(InstState) * ni, 256);
+    j.off_items = o;
+    o = align_up(o + sizeof(uint64_t) * (ni + 1), 256);
+    j.off_W.resize(ni);
+    j.off_W64.resize(ni);
+    j.off_U64.resize(ni);
+    j.off_Es.resize(ni);
+    j.off_M.resize(ni);
+    j.off_EL.resize(ni);
+    for (int i = 0; i < ni; ++i) {
+        const HostInst &h = *j.insts[i];
+        const size_t nn = (size_t)h.n * h.n;
+        if (h.is_float) {
+            j.off_W[i] = 0;
+            j.off_W64[i] = o;
+            o = align_up(o + 8 * nn, 256);
+            j.off_U64[i] = o;
+            o = align_up(o + 8 * nn, 256);
+        } else {
+            j.off_W[i] = o;
+            o = align_up(o + (size_t)eb * nn, 256);
+        }
+    }
+    j.up_bytes = o;
+    j.max_entries = 1;
+    for (int i = 0; i < ni; ++i) {
+        const HostInst &h = *j.insts[i];
+        if (h.small)
+            continue;
+        const size_t NB = 1ull << h.B, NL = 1ull << h.L;
+        j.off_Es[i] = o;
+        o = align_up(o + eb * NB, 256);
+        j.off_M[i] = o;
+        o = align_up(o + eb * NB * h.L, 256);
+        j.off_EL[i] = o;
+        o = align_up(o + eb * NL, 256);
+        j.max_entries = std::max(j.max_entries, (int)(NB * (h.L + 1) + NL));
+    }
+    // results
+    size_t d = 0;
+    j.off_res = o;
+    o = align_up(o + sizeof(ResOut) * ni, 256);
+    j.off_ties = o;
+    o = align_up(o + 8 * j.cap * ni, 256);
+    j.off_topk = o;
+    o = align_up(o + 8 * (size_t)j.K * ni, 256);
+    j.off_topke = o;
+    o = align_up(o + 8 * (size_t)j.K * ni, 256);
+    j.off_starts = o;
+    o = align_up(o + 16 * (size_t)ni, 256);
+    j.off_ctr = o;
+    o = align_up(o + 16 * 8, 256);
+    j.arena_bytes = o;
+    d = sizeof(ResOut) * ni + sizeof(InstState) * ni + 8 * j.cap * ni + 16 * (size_t)j.K * ni + 16 * 8 + 4096;
+    j.down_bytes = d;
+    return QUBO_OK;
+}
+
+// Stage, upload and launch tables + scan.  Does not wait.
+int job_launch(Workspace &ws, Job &j)
+{
+    const int ni = (int)j.insts.size();
+    int st;
+    if ((st = job_layout(j)))
+        return st;
+    if ((st = ws.ensure(j.arena_bytes, kDefaultRecCap, j.up_bytes, j.down_bytes)))
+        return st;
+    char *up = (char *)ws.h_up;
+    char *dev = (char *)ws.d_arena;
+    Inst *hi = (Inst *)(up + j.off_inst);
+    InstState *hs = (InstState *)(up + j.off_state);
+    uint64_t *items = (uint64_t *)(up + j.off_items);
+    uint64_t total = 0;
+    const bool k1 = j.K <= 1;
+    for (int i = 0; i < ni; ++i) {
+        HostInst &h = *j.insts[i];
+        const size_t nn = (size_t)h.n * h.n;
+        Inst d{};
+        d.n = h.n;
+        d.B = h.B;
+        d.L = h.L;
+        d.k = h.k;
+        d.small = h.small;
+        d.unit_begin = h.unit_begin;
+        d.units = h.units;
+        d.sub_base = h.sub_base;
+        d.sub_count = h.sub_count;
+        if (h.is_float) {
+            double *W64 = (double *)(up + j.off_W64[i]);
+            double *U64 = (double *)(up + j.off_U64[i]);
+            for (int a = 0; a < h.n; ++a)
+                for (int b = 0; b < h.n; ++b) {
+                    const int lo = std::min(a, b), hi2 = std::max(a, b);
+                    W64[(size_t)a * h.n + b] = h.Uf[(size_t)lo * h.n + hi2];
+                    U64[(size_t)a * h.n + b] = h.Uf[(size_t)a * h.n + b];
+                }
+            d.W = nullptr;
+            d.W64 = (const double *)(dev + j.off_W64[i]);
+            d.U64 = (const double *)(dev + j.off_U64[i]);
+        } else {
+            if (j.acc == ACC_I32) {
+                int32_t *W = (int32_t *)(up + j.off_W[i]);
+                for (int a = 0; a < h.n; ++a)
+                    for (int b = 0; b < h.n; ++b)
+                        W[(size_t)a * h.n + b] = (int32_t)h.Ui[(size_t)std::min(a, b) * h.n + std::max(a, b)];
+            } else {
+                int64_t *W = (int64_t *)(up + j.off_W[i]);
+                for (int a = 0; a < h.n; ++a)
+                    for (int b = 0; b < h.n; ++b)
+                        W[(size_t)a * h.n + b] = h.Ui[(size_t)std::min(a, b) * h.n + std::max(a, b)];
+            }
+            d.W = dev + j.off_W[i];
+            d.W64 = nullptr;
+            d.U64 = nullptr;
+        }
+        (void)nn;
+        d.Es = h.small ? nullptr : dev + j.off_Es[i];
+        d.M = h.small ? nullptr : dev + j.off_M[i];
+        d.EL = h.small ? nullptr : dev + j.off_EL[i];
+        d.thr0 = 0;
+        hi[i] = d;
+        InstState s{};
+        s.thr = encode_thr(j.acc, h.thr0);
+        s.gmin = encode_max(j.acc);
+        hs[i] = s;
+        items[i] = total;
+        total += h.items;
+    }
+    items[ni] = total;
+
+    cudaStream_t s = j.stream;
+    *ws.h_abort = g_abort_all.load() ? 1 : 0;
+    CK(cudaMemcpyAsync(dev, up, j.up_bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(dev + j.off_ctr, 0, 16 * 8, s));
+    CK(cudaEventRecord(ws.ev[0], s));
+    CK(launch_tables(j.acc, (const Inst *)(dev + j.off_inst), ni, j.max_entries, s));
+    ScanArgs a{};
+    a.inst = (const Inst *)(dev + j.off_inst);
+    a.state = (InstState *)(dev + j.off_state);
+    a.item_base = (const uint64_t *)(dev + j.off_items);
+    a.n_inst = ni;
+    a.k1 = k1 ? 1 : 0;
+    a.total_items = total;
+    a.queue = (unsigned long long *)(dev + j.off_ctr);
+    a.rec = ws.d_rec;
+    a.rec_cap = std::min(ws.rec_cap, record_capacity());
+    j.rec_cap = a.rec_cap;
+    a.nrec = (unsigned long long *)(dev + j.off_ctr) + 1;
+    a.abort_flag = ws.d_abort;
+    a.margin = (j.acc == ACC_F32 || j.acc == ACC_F64) ? j.margin : 0.0;
+    int bps = scan_blocks_per_sm(j.acc, k1, j.variant);
+    if (bps < 1)
+        bps = 1;
+    j.blocks = ws.sms * bps;
+    const uint64_t need_blocks = (total * 32 + kScanThreads - 1) / kScanThreads;
+    if ((uint64_t)j.blocks > need_blocks)
+        j.blocks = (int)std::max<uint64_t>(1, need_blocks);
+    CK(launch_scan(j.acc, a, j.blocks, j.variant, s));
+    CK(cudaEventRecord(ws.ev[1], s));
+    j.t_start = now_s();
+    return QUBO_OK;
+}
+
+// Wait for the scan (honouring the time limit and qubo_abort), then finalize and download.
+int job_finish(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seconds)
+{
+    const int ni = (int)j.insts.size();
+    char *dev = (char *)ws.d_arena;
+    cudaStream_t s = j.stream;
+    // watchdog: poll the scan's completion event
+    for (;;) {
+        const cudaError_t q = cudaEventQuery(ws.ev[1]);
+        if (q == cudaSuccess)
+            break;
+        if (q != cudaErrorNotReady) {
+            cudaGetLastError();
+            return QUBO_ERR_CUDA;
+        }
+        const bool over = j.time_limit > 0 && now_s() - j.t_start > j.time_limit;
+        if ((over || g_abort_all.load()) && !*(volatile int *)ws.h_abort) {
+            *(volatile int *)ws.h_abort = 1;
+            j.aborted = true;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    if (*(volatile int *)ws.h_abort)
+        j.aborted = true;
+    unsigned long long nrec = 0;
+    CK(cudaMemcpy(&nrec, dev + j.off_ctr + 8, 8, cudaMemcpyDeviceToHost));
+    const unsigned long long cnt = std::min(nrec, j.rec_cap);
+    unsigned long long P = 1;
+    while (P < cnt)
+        P <<= 1;
+    const bool batched = ni > 1;
+    const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
+    const unsigned long long *d_nrec = (const unsigned long long *)(dev + j.off_ctr) + 1;
+    if (is_float)
+        CK(launch_rescore((const Inst *)(dev + j.off_inst), (InstState *)(dev + j.off_state), ws.d_rec, d_nrec,
+                          j.rec_cap, batched, cnt, s));
+    CK(launch_sort(ws.d_rec, d_nrec, j.rec_cap, P, batched, is_float, s));
+    CK(launch_extract((const Inst *)(dev + j.off_inst), ws.d_rec, d_nrec, j.rec_cap, ni, batched, is_float, j.K,
+                      j.cap, (ResOut *)(dev + j.off_res), (uint64_t *)(dev + j.off_ties),
+                      (uint64_t *)(dev + j.off_topk), (int64_t *)(dev + j.off_topke),
+                      (unsigned long long *)(dev + j.off_starts), s));
+    CK(cudaEventRecord(ws.ev[2], s));
+    // download
+    char *down = (char *)ws.h_down;
+    size_t o = 0;
+    ResOut *res = (ResOut *)(down + o);
+    o += sizeof(ResOut) * ni;
+    InstState *sts = (InstState *)(down + o);
+    o += sizeof(InstState) * ni;
+    uint64_t *ties = (uint64_t *)(down + o);
+    o += 8 * j.cap * ni;
+    uint64_t *tk = (uint64_t *)(down + o);
+    o += 8 * (size_t)j.K * ni;
+    int64_t *tke = (int64_t *)(down + o);
+    CK(cudaMemcpyAsync(res, dev + j.off_res, sizeof(ResOut) * ni, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(sts, dev + j.off_state, sizeof(InstState) * ni, cudaMemcpyDeviceToHost, s));
+    if (j.cap)
+        CK(cudaMemcpyAsync(ties, dev + j.off_ties, 8 * j.cap * ni, cudaMemcpyDeviceToHost, s));
+    if (j.K) {
+        CK(cudaMemcpyAsync(tk, dev + j.off_topk, 8 * (size_t)j.K * ni, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(tke, dev + j.off_topke, 8 * (size_t)j.K * ni, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ws.ev[0], ws.ev[2]) == cudaSuccess && gpu_seconds)
+        *gpu_seconds = ms * 1e-3;
+    parts.assign(ni, Part());
+    for (int i = 0; i < ni; ++i) {
+        Part &p = parts[i];
+        const ResOut &r = res[i];
+        p.is_float = is_float;
+        p.has = r.has != 0;
+        p.min_i = r.min_i;
+        p.min_f = is_float ? r.min_f : (double)r.min_i;
+        p.n_ties = r.n_ties;
+        p.n_near = r.n_near;
+        p.ties.assign(ties + (size_t)i * j.cap, ties + (size_t)i * j.cap + r.n_written);
+        for (int t = 0; t < r.nk; ++t) {
+            const uint64_t c = tk[(size_t)i * j.K + t];
+            const int64_t e = tke[(size_t)i * j.K + t];
+            if (is_float)
+                p.topf.emplace_back(bits_to_double(e), c);
+            else
+                p.topi.emplace_back(e, c);
+        }
+        p.scanned = sts[i].scanned;
+        p.candidates = sts[i].nrec;
+        p.drift = ubits_to_double(sts[i].drift);
+        p.err = ubits_to_double(sts[i].err);
+        p.overflow = sts[i].dropped > 0;
+    }
+    return j.aborted ? QUBO_ERR_TIMEOUT : QUBO_OK;
+}
+
+struct SolveCfg {
+    int K = 0;
+    size_t cap = 0;
+    uint32_t flags = 0;
+    double margin = kDefaultMargin;
+    double time_limit = 0.0;
+    int split_k = 0, walk_bits = 0;
+    int variant = 0;
+};
+
+struct SolveStats {
+    double gpu_seconds = 0.0;
+    int passes = 0;
+    int blocks = 0;
+};
+
+// Solve the sub-cube (fix_bits, fix_value) of one prepared instance.  When the candidate buffer
+// overflows, the sub-cube is split in two along its next code bit and both halves are solved
+// and merged, down to halves small enough to fit.
+int solve_range(Workspace &ws, HostInst &h, int fix_bits, uint64_t fix_value, const SolveCfg &c,
+                cudaStream_t stream, Part &out, SolveStats &stats, double t_deadline)
+{
+    int st = plan(h, fix_bits, fix_value, c.split_k, c.walk_bits);
+    if (st)
+        return st;
+    h.thr0 = threshold_bound(h, std::max(1, c.K));
+    Job j;
+    j.insts = {&h};
+    j.acc = h.acc;
+    j.K = c.K;
+    j.cap = c.cap;
+    j.margin = c.margin;
+    j.time_limit = t_deadline > 0 ? std::max(1e-3, t_deadline - now_s()) : 0.0;
+    j.variant = c.variant;
+    j.stream = stream;
+    if ((st = job_launch(ws, j)))
+        return st;
+    std::vector<Part> parts;
+    double gs = 0.0;
+    st = job_finish(ws, j, parts, &gs);
+    stats.gpu_seconds += gs;
+    stats.passes += 1;
+    stats.blocks = std::max(stats.blocks, j.blocks);
+    if (st)
+        return st;
+    Part p = parts[0];
+    if (!p.overflow) {
+        out = p;
+        return QUBO_OK;
+    }
+    if (fix_bits >= h.n)
+        return QUBO_ERR_INTERNAL;  // a single state cannot overflow the buffer
+    Part a, b;
+    if ((st = solve_range(ws, h, fix_bits + 1, fix_value << 1, c, stream, a, stats, t_deadline)))
+        return st;
+    if ((st = solve_range(ws, h, fix_bits + 1, (fix_value << 1) | 1, c, stream, b, stats, t_deadline)))
+        return st;
+    out = merge_parts(a, b, c.cap, c.K);
+    return QUBO_OK;
+}
+
+// Float scans: the FP32 candidate margin must exceed twice the drift measured at re-anchoring
+// (plus rounding of the threshold arithmetic); otherwise the instance is rescanned in FP64.
+bool float_margin_ok(const HostInst &h, const Part &p, double margin)
+{
+    if (h.acc != ACC_F32)
+        return true;
+    const double slack = 8.0 * std::ldexp(1.0, -24) * (1.0 + h.beta);
+    return 2.0 * p.drift + slack < margin;
+}
+
+void fill_outputs(const HostInst &h, const Part &p, int K, size_t cap, void *out_min, uint64_t *out_states,
+                  uint64_t *out_topk, void *out_topk_E, qubo_result *info)
+{
+    if (out_min) {
+        if (h.is_float)
+            *(double *)out_min = p.min_f;
+        else
+            *(int64_t *)out_min = p.min_i;
+    }
+    const size_t nw = std::min(cap, p.ties.size());
+    if (out_states)
+        for (size_t t = 0; t < nw; ++t)
+            out_states[t] = p.ties[t];
+    const int nk = h.is_float ? (int)p.topf.size() : (int)p.topi.size();
+    if (K > 0 && out_topk)
+        for (int t = 0; t < nk && t < K; ++t) {
+            out_topk[t] = h.is_float ? p.topf[t].second : p.topi[t].second;
+            if (out_topk_E) {
+                if (h.is_float)
+                    ((double *)out_topk_E)[t] = p.topf[t].first;
+                else
+                    ((int64_t *)out_topk_E)[t] = p.topi[t].first;
+            }
+        }
+    if (info) {
+        info->min_i = h.is_float ? (int64_t)0 : p.min_i;
+        info->min_f = p.min_f;
+        info->n_ties = p.n_ties;
+        info->n_written = nw;
+        info->truncated = p.n_ties > cap ? 1 : 0;
+        info->acc = (int32_t)h.acc;
+        info->n_topk = std::min(nk, K);
+        info->fp32_max_abs_err = h.is_float ? p.err : 0.0;
+        info->fp32_max_drift = h.is_float ? p.drift : 0.0;
+        info->n_near_ties = p.n_near;
+        info->states_scanned = p.scanned;
+        info->candidates = p.candidates;
+    }
+}
+
+int resolve_device(Workspace **out)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return QUBO_ERR_CUDA;
+    }
+    Workspace *w = shared_workspace(dev);
+    if (!w)
+        return QUBO_ERR_NOMEM;
+    *out = w;
+    return QUBO_OK;
+}
+
+int check_opts(const qubo_options *o, size_t states_cap, const uint64_t *out_states, const uint64_t *out_topk)
+{
+    if (o->topk < 0 || o->topk > QUBO_MAX_TOPK)
+        return QUBO_ERR_ARG;
+    if (states_cap > 0 && !out_states)
+        return QUBO_ERR_ARG;
+    if (o->topk > 0 && !out_topk)
+        return QUBO_ERR_ARG;
+    return QUBO_OK;
+}
+
+int solve_one(Workspace &ws, HostInst &h, const qubo_options &o, size_t states_cap, cudaStream_t stream, Part &p,
+              SolveStats &stats)
+{
+    SolveCfg c;
+    c.K = o.topk;
+    c.cap = states_cap;
+    c.flags = o.flags;
+    c.margin = o.margin > 0 ? o.margin : kDefaultMargin;
+    c.time_limit = o.time_limit_s;
+    c.split_k = o.split_k;
+    c.walk_bits = o.walk_bits;
+    c.variant = scan_variant();
+    const double deadline = o.time_limit_s > 0 ? now_s() + o.time_limit_s : 0.0;
+    int st = solve_range(ws, h, o.fix_bits, o.fix_value, c, stream, p, stats, deadline);
+    if (st)
+        return st;
+    if (!float_margin_ok(h, p, c.margin)) {
+        h.acc = ACC_F64;
+        p = Part();
+        st = solve_range(ws, h, o.fix_bits, o.fix_value, c, stream, p, stats, deadline);
+        if (st)
+            return st;
+    }
+    const uint64_t expect = 1ull << (h.n - o.fix_bits);
+    if (p.scanned != expect || !p.has)
+        return QUBO_ERR_INTERNAL;
+    return QUBO_OK;
+}
+
+void fill_plan_info(const HostInst &h, const SolveStats &stats, double t0, qubo_result *info)
+{
+    if (!info)
+        return;
+    info->seconds = now_s() - t0;
+    info->seconds_gpu = stats.gpu_seconds;
+    info->states_per_s = info->seconds > 0 ? (double)info->states_scanned / info->seconds : 0.0;
+    info->n = h.n;
+    info->split_k = h.k;
+    info->walk_bits = h.L;
+    info->suffix_bits = h.small ? 0 : h.B;
+    info->cols_per_thread = h.small ? 0 : cols_per_thread(acc_bytes(h.acc));
+    info->threads = kScanThreads;
+    info->blocks = stats.blocks;
+    info->passes = stats.passes;
+}
+
+}  // namespace
+
+// ================================================================================================
+// C ABI
+// ================================================================================================
+
+struct qubo_problem {
+    HostInst h;
+    qubo_options opt{};
+    Workspace ws;
+    Job job;
+    bool launched = false;
+    int launch_status = QUBO_OK;
+    int fix_bits = 0;
+    uint64_t fix_value = 0;
+    double t0 = 0.0;
+    cudaStream_t stream = nullptr;
+};
+
+extern "C" {
+
+const char *qubo_version(void) { return "qubo-gb300 0.1 (sm_103a)"; }
+
+const char *qubo_strerror(int status)
+{
+    switch (status) {
+    case QUBO_OK: return "ok";
+    case QUBO_TRUNCATED: return "tie set truncated to states_cap (results valid, count exact)";
+    case QUBO_ERR_ARG: return "bad argument";
+    case QUBO_ERR_OVERFLOW: return "integer energies exceed every supported accumulator";
+    case QUBO_ERR_CUDA: return "CUDA error";
+    case QUBO_ERR_NOMEM: return "out of memory";
+    case QUBO_ERR_TIMEOUT: return "time limit expired or aborted";
+    case QUBO_ERR_INTERNAL: return "internal consistency check failed";
+    }
+    return "unknown status";
+}
+
+void qubo_abort(void)
+{
+    g_abort_all.store(1);
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    for (Workspace *w : g_all_ws)
+        if (w->h_abort)
+            *(volatile int *)w->h_abort = 1;
+}
+
+void qubo_abort_clear(void) { g_abort_all.store(0); }
+
+int qubo_device_sm_count(void)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return QUBO_ERR_CUDA;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return QUBO_ERR_CUDA;
+    }
+    return sms;
+}
+
+int qubo_solve_ex(const void *Q_host, int n, qubo_dtype dtype, const qubo_options *opt, void *out_min,
+                  uint64_t *out_states, size_t states_cap, uint64_t *out_topk, void *out_topk_E, qubo_result *info,
+                  void *stream)
+{
+    const double t0 = now_s();
+    qubo_options o{};
+    if (opt)
+        o = *opt;
+    int st = check_opts(&o, states_cap, out_states, out_topk);
+    if (st)
+        return st;
+    if (!out_min)
+        return QUBO_ERR_ARG;
+    HostInst h;
+    if ((st = prepare(Q_host, n, dtype, o.flags, h)))
+        return st;
+    if (o.fix_bits < 0 || o.fix_bits > n)
+        return QUBO_ERR_ARG;
+    if (o.topk > 0 && (uint64_t)o.topk > (1ull << std::min(62, n - o.fix_bits)))
+        return QUBO_ERR_ARG;
+    Workspace *ws = nullptr;
+    if ((st = resolve_device(&ws)))
+        return st;
+    std::lock_guard<std::mutex> lk(ws->mu);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if ((st = ws->init(dev)))
+        return st;
+    Part p;
+    SolveStats stats;
+    st = solve_one(*ws, h, o, states_cap, (cudaStream_t)stream, p, stats);
+    if (st)
+        return st;
+    if (info)
+        std::memset(info, 0, sizeof(*info));
+    fill_outputs(h, p, o.topk, states_cap, out_min, out_states, out_topk, out_topk_E, info);
+    fill_plan_info(h, stats, t0, info);
+    return p.n_ties > states_cap ? QUBO_TRUNCATED : QUBO_OK;
+}
+
+int qubo_solve(const void *Q_host, int n, qubo_dtype dtype, int split_k, int topk, void *out_min,
+               uint64_t *out_states, size_t states_cap, uint64_t *out_topk, void *out_topk_E, qubo_result *info,
+               void *stream)
+{
+    qubo_options o{};
+    o.split_k = split_k;
+    o.topk = topk;
+    return qubo_solve_ex(Q_host, n, dtype, &o, out_min, out_states, states_cap, out_topk, out_topk_E, info, stream);
+}
+
+int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets, int count, qubo_dtype dtype,
+                       int topk, void *out_min, uint64_t *out_states, size_t states_cap_per_inst, uint64_t *out_topk,
+                       void *out_topk_E, qubo_result *info, void *stream)
+{
+    const double t0 = now_s();
+    if (!Q_packed || !n || !offsets || count < 1 || count > 65535 || !out_min || !dtype_ok(dtype))
+        return QUBO_ERR_ARG;
+    if (topk < 0 || topk > QUBO_MAX_TOPK || (topk > 0 && !out_topk) || (states_cap_per_inst > 0 && !out_states))
+        return QUBO_ERR_ARG;
+    const size_t esz = dtype == QUBO_I16 ? 2 : (dtype == QUBO_I32 || dtype == QUBO_F32) ? 4 : 8;
+    std::vector<HostInst> hs(count);
+    int st;
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 1 || n[i] > kMaxBatchedN)
+            return QUBO_ERR_ARG;
+        if (topk > 0 && (uint64_t)topk > (1ull << n[i]))
+            return QUBO_ERR_ARG;
+        if ((st = prepare((const char *)Q_packed + offsets[i] * esz, n[i], dtype, 0, hs[i])))
+            return st;
+    }
+    // one accumulator for the whole batch: the widest any instance needs
+    Acc acc = hs[0].acc;
+    for (auto &h : hs)
+        if (acc_bytes(h.acc) > acc_bytes(acc))
+            acc = h.acc;
+    for (auto &h : hs)
+        h.acc = acc;
+    for (auto &h : hs) {
+        if ((st = plan(h, 0, 0, 0, 0)))
+            return st;
+        h.thr0 = threshold_bound(h, std::max(1, topk));
+    }
+    // longest work first (LPT order) so the tail of the persistent launch is short
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i)
+        order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a].states > hs[b].states; });
+    Workspace *ws = nullptr;
+    if ((st = resolve_device(&ws)))
+        return st;
+    std::lock_guard<std::mutex> lk(ws->mu);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if ((st = ws->init(dev)))
+        return st;
+    Job j;
+    for (int i : order)
+        j.insts.push_back(&hs[i]);
+    j.acc = acc;
+    j.K = topk;
+    j.cap = states_cap_per_inst;
+    j.margin = kDefaultMargin;
+    j.variant = scan_variant();
+    j.stream = (cudaStream_t)stream;
+    if ((st = job_launch(*ws, j)))
+        return st;
+    std::vector<Part> parts;
+    double gs = 0.0;
+    if ((st = job_finish(*ws, j, parts, &gs)))
+        return st;
+    int worst = QUBO_OK;
+    SolveCfg c;
+    c.K = topk;
+    c.cap = states_cap_per_inst;
+    c.variant = j.variant;
+    for (int r = 0; r < count; ++r) {
+        const int i = order[r];
+        Part &p = parts[r];
+        HostInst &h = hs[i];
+        SolveStats stats;
+        stats.gpu_seconds = gs;
+        stats.passes = 1;
+        stats.blocks = j.blocks;
+        if (p.overflow || !float_margin_ok(h, p, c.margin)) {
+            // rare: this instance overflowed the shared candidate buffer; solve it alone
+            if (!float_margin_ok(h, p, c.margin))
+                h.acc = ACC_F64;
+            p = Part();
+            if ((st = solve_range(*ws, h, 0, 0, c, (cudaStream_t)stream, p, stats, 0.0)))
+                return st;
+        }
+        if (p.scanned != (1ull << h.n) || !p.has)
+            return QUBO_ERR_INTERNAL;
+        void *om = h.is_float ? (void *)((double *)out_min + i) : (void *)((int64_t *)out_min + i);
+        void *otke = nullptr;
+        if (out_topk_E)
+            otke = h.is_float ? (void *)((double *)out_topk_E + (size_t)i * topk)
+                              : (void *)((int64_t *)out_topk_E + (size_t)i * topk);
+        qubo_result *inf = info ? info + i : nullptr;
+        if (inf)
+            std::memset(inf, 0, sizeof(*inf));
+        fill_outputs(h, p, topk, states_cap_per_inst, om,
+                     out_states ? out_states + (size_t)i * states_cap_per_inst : nullptr,
+                     out_topk ? out_topk + (size_t)i * topk : nullptr, otke, inf);
+        fill_plan_info(h, stats, t0, inf);
+        if (p.n_ties > states_cap_per_inst)
+            worst = std::max(worst, (int)QUBO_TRUNCATED);
+    }
+    return worst;
+}
+
+int qubo_problem_create(const void *Q_host, int n, qubo_dtype dtype, const qubo_options *opt, qubo_problem **out)
+{
+    if (!out)
+        return QUBO_ERR_ARG;
+    *out = nullptr;
+    qubo_problem *p = new (std::nothrow) qubo_problem();
+    if (!p)
+        return QUBO_ERR_NOMEM;
+    if (opt)
+        p->opt = *opt;
+    if (p->opt.topk < 0 || p->opt.topk > QUBO_MAX_TOPK) {
+        delete p;
+        return QUBO_ERR_ARG;
+    }
+    int st = prepare(Q_host, n, dtype, p->opt.flags, p->h);
+    int dev = -1;
+    if (!st && cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        st = QUBO_ERR_CUDA;
+    }
+    if (!st)
+        st = p->ws.init(dev);
+    if (st) {
+        delete p;
+        return st;
+    }
+    register_ws(&p->ws);
+    *out = p;
+    return QUBO_OK;
+}
+
+int qubo_problem_run(qubo_problem *p, int fix_bits, uint64_t fix_value, void *stream)
+{
+    if (!p)
+        return QUBO_ERR_ARG;
+    p->t0 = now_s();
+    p->fix_bits = fix_bits;
+    p->fix_value = fix_value;
+    p->stream = (cudaStream_t)stream;
+    int st = plan(p->h, fix_bits, fix_value, p->opt.split_k, p->opt.walk_bits);
+    if (st)
+        return st;
+    p->h.thr0 = threshold_bound(p->h, std::max(1, p->opt.topk));
+    p->job = Job();
+    p->job.insts = {&p->h};
+    p->job.acc = p->h.acc;
+    p->job.K = p->opt.topk;
+    p->job.cap = 1 << 16;
+    p->job.margin = p->opt.margin > 0 ? p->opt.margin : kDefaultMargin;
+    p->job.time_limit = p->opt.time_limit_s;
+    p->job.variant = scan_variant();
+    p->job.stream = p->stream;
+    st = job_launch(p->ws, p->job);
+    p->launched = st == QUBO_OK;
+    p->launch_status = st;
+    return st;
+}
+
+int qubo_problem_fetch(qubo_problem *p, void *out_min, uint64_t *out_states, size_t states_cap, uint64_t *out_topk,
+                       void *out_topk_E, qubo_result *info)
+{
+    if (!p || !out_min || (states_cap > 0 && !out_states) || (p->opt.topk > 0 && !out_topk))
+        return QUBO_ERR_ARG;
+    if (!p->launched)
+        return p->launch_status ? p->launch_status : QUBO_ERR_ARG;
+    p->launched = false;
+    std::vector<Part> parts;
+    SolveStats stats;
+    int st = job_finish(p->ws, p->job, parts, &stats.gpu_seconds);
+    stats.passes = 1;
+    stats.blocks = p->job.blocks;
+    if (st)
+        return st;
+    Part part = parts[0];
+    const size_t cap = std::min<size_t>(states_cap, p->job.cap);
+    if (part.overflow || !float_margin_ok(p->h, part, p->job.margin) || states_cap > p->job.cap) {
+        // repeat through the splitting path (exact, uses this problem's workspace)
+        qubo_options o = p->opt;
+        o.fix_bits = p->fix_bits;
+        o.fix_value = p->fix_value;
+        part = Part();
+        if ((st = solve_one(p->ws, p->h, o, states_cap, p->stream, part, stats)))
+            return st;
+    }
+    if (part.scanned != (1ull << (p->h.n - p->fix_bits)) || !part.has)
+        return QUBO_ERR_INTERNAL;
+    if (info)
+        std::memset(info, 0, sizeof(*info));
+    fill_outputs(p->h, part, p->opt.topk, states_cap, out_min, out_states, out_topk, out_topk_E, info);
+    fill_plan_info(p->h, stats, p->t0, info);
+    (void)cap;
+    return part.n_ties > states_cap ? QUBO_TRUNCATED : QUBO_OK;
+}
+
+void qubo_problem_destroy(qubo_problem *p)
+{
+    if (!p)
+        return;
+    unregister_ws(&p->ws);
+    delete p;
+}
+
+int qubo_merge(const qubo_partial *a, const qubo_partial *b, size_t cap, int topk, qubo_partial *out)
+{
+    if (!a || !b || !out || topk < 0 || topk > QUBO_MAX_TOPK || a->is_float != b->is_float)
+        return QUBO_ERR_ARG;
+    if ((cap > 0 && !out->ties) || (topk > 0 && (!out->topk || !out->topk_E)))
+        return QUBO_ERR_ARG;
+    auto to_part = [&](const qubo_partial *x) {
+        Part p;
+        p.has = x->states_scanned > 0;
+        p.is_float = x->is_float != 0;
+        p.min_i = x->min_i;
+        p.min_f = x->min_f;
+        p.n_ties = x->n_ties;
+        p.scanned = x->states_scanned;
+        if (x->n_written && x->ties)
+            p.ties.assign(x->ties, x->ties + x->n_written);
+        for (int t = 0; t < x->n_topk; ++t) {
+            if (p.is_float)
+                p.topf.emplace_back(((const double *)x->topk_E)[t], x->topk[t]);
+            else
+                p.topi.emplace_back(((const int64_t *)x->topk_E)[t], x->topk[t]);
+        }
+        return p;
+    };
+    const Part m = merge_parts(to_part(a), to_part(b), cap, topk);
+    out->is_float = a->is_float;
+    out->min_i = m.min_i;
+    out->min_f = m.min_f;
+    out->n_ties = m.n_ties;
+    out->states_scanned = m.scanned;
+    out->n_written = std::min(cap, m.ties.size());
+    for (size_t t = 0; t < out->n_written; ++t)
+        out->ties[t] = m.ties[t];
+    const int nk = std::min(topk, m.is_float ? (int)m.topf.size() : (int)m.topi.size());
+    out->n_topk = nk;
+    for (int t = 0; t < nk; ++t) {
+        if (m.is_float) {
+            out->topk[t] = m.topf[t].second;
+            ((double *)out->topk_E)[t] = m.topf[t].first;
+        } else {
+            out->topk[t] = m.topi[t].second;
+            ((int64_t *)out->topk_E)[t] = m.topi[t].first;
+        }
+    }
+    return QUBO_OK;
+}
+
+}  // extern "C"

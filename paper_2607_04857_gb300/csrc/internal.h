@@ -1,0 +1,119 @@
+// Internal declarations shared by the host driver (api.cu) and the kernels of libqubo.so.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qubo {
+
+enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4 };
+
+// Walked prefix rows kept in registers by the scan kernel (the largest of the compiled
+// variants); the inner loop is unrolled over 2^(RC+1) Gray steps so that every register-row
+// flip has a compile-time sign.  A plan needs walk_bits >= kRegRows + 1.
+constexpr int kRegRows = 3;
+// Compiled scan variants: (register rows, minimum resident blocks per SM).
+constexpr int kScanVariants = 3;
+constexpr int kVariantRegRows[kScanVariants] = {3, 2, 3};
+constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 3};
+// Threads per block of the scan kernel (4 warps; every warp owns one work unit at a time).
+constexpr int kScanThreads = 128;
+// Longest Gray walk inside one work unit (also the FP32 re-anchoring period).
+constexpr int kMaxWalkBits = 16;
+// Batched instances carry their index in the top bits of a candidate key.
+constexpr int kInstShift = 40;
+constexpr int kMaxBatchedN = 40;
+
+// Candidate record.  `key` is the state code (single instance) or (instance << 40) | code
+// (batched).  `e` is an int64 energy or the bit pattern of a double energy.
+struct Rec {
+    uint64_t key;
+    int64_t e;
+};
+
+// Immutable per-instance description of one scan (device copy lives in the arena).
+struct Inst {
+    int32_t n;          // variables
+    int32_t B;          // suffix bits (columns)
+    int32_t L;          // walked prefix bits
+    int32_t k;          // fixed bits per unit (n = B + L + k on the tabled path)
+    int32_t small;      // 1: no split, every state evaluated directly
+    int32_t pad0;
+    uint64_t unit_begin;  // first unit (value of the fixed bits) of this run
+    uint64_t units;       // units in this run
+    uint64_t sub_base;    // small path: first code
+    uint64_t sub_count;   // small path: number of codes
+    const void *W;        // symmetric coupling matrix in the accumulator type, n*n
+    const double *W64;    // symmetric coupling matrix in FP64 (float instances), n*n
+    const double *U64;    // folded upper-triangular matrix in FP64 (float rescore), n*n
+    void *Es;             // 2^B suffix energies
+    void *M;              // L x 2^B interaction rows (M_int restricted to the walked rows)
+    void *EL;             // 2^L walked-prefix energies in Gray-walk order
+    int64_t thr0;         // initial threshold (int64 value or double bits)
+};
+
+// Mutable per-instance state, updated with atomics.
+struct InstState {
+    unsigned long long thr;      // threshold in the accumulator's ordered encoding
+    unsigned long long gmin;     // smallest recorded energy, same encoding
+    unsigned long long scanned;  // states evaluated
+    unsigned long long nrec;     // candidates offered
+    unsigned long long dropped;  // candidates not stored (buffer full)
+    unsigned long long drift;    // float: max re-anchoring drift (bits of a non-negative double)
+    unsigned long long err;      // float: max |E_scan - E64| (bits of a non-negative double)
+    unsigned long long pad;
+};
+
+// Per-instance result written by the extraction kernel.
+struct ResOut {
+    int64_t min_i;
+    double min_f;
+    unsigned long long n_ties;
+    unsigned long long n_written;
+    unsigned long long n_near;
+    int32_t nk;
+    int32_t has;
+};
+
+struct ScanArgs {
+    const Inst *inst;
+    InstState *state;
+    const uint64_t *item_base;   // n_inst + 1 prefix sums of the per-instance item counts
+    int32_t n_inst;
+    int32_t k1;                  // K <= 1: thresholds tighten as lower states are found
+    uint64_t total_items;
+    unsigned long long *queue;   // dynamic work counter (zeroed before launch)
+    Rec *rec;
+    unsigned long long rec_cap;
+    unsigned long long *nrec;    // total candidates offered
+    const volatile int *abort_flag;
+    double margin;               // float scans: candidate margin above the threshold
+};
+
+// Columns per thread (S) of the scan kernel for an accumulator of `bytes` bytes; a work unit
+// covers 32*S columns, so the suffix has log2(32*S) bits.
+constexpr int cols_per_thread(int bytes) { return bytes == 4 ? 32 : 16; }
+constexpr int suffix_bits(int bytes) { return bytes == 4 ? 10 : 9; }
+
+// ---- launchers (scan_*.cu, one translation unit per accumulator type) -------------------------
+template <class T>
+cudaError_t launch_tables_t(const Inst *d_inst, int n_inst, int max_entries, cudaStream_t s);
+template <class T>
+cudaError_t launch_scan_t(const ScanArgs &a, int blocks, int variant, cudaStream_t s);
+template <class T>
+int scan_blocks_per_sm_t(bool k1, int variant);
+
+// ---- dispatch and finalize (finalize.cu) -----------------------------------------------------
+cudaError_t launch_tables(Acc acc, const Inst *d_inst, int n_inst, int max_entries, cudaStream_t s);
+cudaError_t launch_scan(Acc acc, const ScanArgs &a, int blocks, int variant, cudaStream_t s);
+int scan_blocks_per_sm(Acc acc, bool k1, int variant);
+cudaError_t launch_rescore(const Inst *d_inst, InstState *d_state, Rec *rec, const unsigned long long *d_nrec,
+                           unsigned long long cap, bool batched, unsigned long long max_count, cudaStream_t s);
+cudaError_t launch_sort(Rec *rec, const unsigned long long *d_nrec, unsigned long long cap, unsigned long long max_pow2,
+                        bool batched, bool is_float, cudaStream_t s);
+cudaError_t launch_extract(const Inst *d_inst, const Rec *rec, const unsigned long long *d_nrec, unsigned long long cap,
+                           int n_inst, bool batched, bool is_float, int topk, unsigned long long states_cap,
+                           ResOut *res, uint64_t *ties, uint64_t *topk_codes, int64_t *topk_e,
+                           unsigned long long *d_starts, cudaStream_t s);
+
+}  // namespace qubo

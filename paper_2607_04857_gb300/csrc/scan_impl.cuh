@@ -1,0 +1,532 @@
+// Exhaustive-scan kernels (table build and the persistent Gray-walk enumeration).
+//
+// Decomposition (Sec. 2, eq. 3-4; Sec. 3.3): a state code is split, low bits first, into
+//   j   : B suffix bits, the columns (Sec. 3.3.2 column-wise split; 32 * S columns per unit),
+//   g   : L prefix bits walked in reflected Gray order inside a unit (Sec. 3.2),
+//   x_f : k = n - B - L fixed bits, one work unit per value (Sec. 3.3.1 straightforward split).
+// For a unit, E(x_f, g, j) = c(x_f) + lin(x_f, g) + E_L(g) + E_sd(g, j) with
+//   E_sd(0, j) = E_s(j) + sum_b j_b v_b(x_f)            (Q' = Q_rr + diag(x_f Q_fr))
+//   E_sd(g', j) = E_sd(g, j) +/- M_k[j]                  (eq. incremental update)
+// so each state costs one add, then one min over the thread's S columns and one compare of
+// that min with a per-step threshold (the argmin / strict-less update of Alg. 2, extended to
+// keep every state at or below the running K-th best).
+#pragma once
+
+#include <cstdint>
+#include <utility>
+
+#include "internal.h"
+
+namespace qubo {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t ord32(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unord32(uint32_t o)
+{
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+__device__ __forceinline__ unsigned long long ord64(double d)
+{
+    unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double unord64(unsigned long long o)
+{
+    return __longlong_as_double((long long)((o & 0x8000000000000000ull) ? (o & 0x7fffffffffffffffull) : ~o));
+}
+
+// ---- accumulator traits ----------------------------------------------------------------------
+template <class T>
+struct Tr;
+
+template <>
+struct Tr<int32_t> {
+    using F = int32_t;  // precision of the per-unit fields and of the tables
+    using Vec = int4;
+    static constexpr int V = 4;
+    static constexpr bool kFloat = false;
+    __device__ static int32_t thr_load(const InstState *s) { return *(const volatile int32_t *)&s->thr; }
+    __device__ static void thr_min(InstState *s, int32_t v) { atomicMin((int *)&s->thr, v); }
+    __device__ static void gmin_min(InstState *s, int32_t v) { atomicMin((int *)&s->gmin, v); }
+    __device__ static int64_t bits(int32_t v) { return v; }
+    __device__ static int32_t tmin(int32_t a, int32_t b) { return min(a, b); }
+};
+
+template <>
+struct Tr<int64_t> {
+    using F = int64_t;
+    using Vec = longlong2;
+    static constexpr int V = 2;
+    static constexpr bool kFloat = false;
+    __device__ static int64_t thr_load(const InstState *s) { return *(const volatile long long *)&s->thr; }
+    __device__ static void thr_min(InstState *s, int64_t v) { atomicMin((long long *)&s->thr, (long long)v); }
+    __device__ static void gmin_min(InstState *s, int64_t v) { atomicMin((long long *)&s->gmin, (long long)v); }
+    __device__ static int64_t bits(int64_t v) { return v; }
+    __device__ static int64_t tmin(int64_t a, int64_t b) { return min(a, b); }
+};
+
+template <>
+struct Tr<float> {
+    using F = double;
+    using Vec = float4;
+    static constexpr int V = 4;
+    static constexpr bool kFloat = true;
+    __device__ static float thr_load(const InstState *s) { return unord32(*(const volatile uint32_t *)&s->thr); }
+    __device__ static void thr_min(InstState *s, float v) { atomicMin((unsigned *)&s->thr, ord32(v)); }
+    __device__ static void gmin_min(InstState *s, float v) { atomicMin((unsigned *)&s->gmin, ord32(v)); }
+    __device__ static int64_t bits(float v) { return __double_as_longlong((double)v); }
+    __device__ static float tmin(float a, float b) { return fminf(a, b); }
+};
+
+template <>
+struct Tr<double> {
+    using F = double;
+    using Vec = double2;
+    static constexpr int V = 2;
+    static constexpr bool kFloat = true;
+    __device__ static double thr_load(const InstState *s)
+    {
+        return unord64(*(const volatile unsigned long long *)&s->thr);
+    }
+    __device__ static void thr_min(InstState *s, double v) { atomicMin(&s->thr, ord64(v)); }
+    __device__ static void gmin_min(InstState *s, double v) { atomicMin(&s->gmin, ord64(v)); }
+    __device__ static int64_t bits(double v) { return __double_as_longlong(v); }
+    __device__ static double tmin(double a, double b) { return fmin(a, b); }
+};
+
+template <class T>
+__device__ __forceinline__ const typename Tr<T>::F *field_matrix(const Inst &d)
+{
+    if constexpr (Tr<T>::kFloat)
+        return d.W64;
+    else
+        return (const typename Tr<T>::F *)d.W;
+}
+
+__device__ __forceinline__ void vsplit(const int4 &v, int32_t (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+__device__ __forceinline__ void vsplit(const float4 &v, float (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
+__device__ __forceinline__ void vsplit(const longlong2 &v, int64_t (&o)[2]) { o[0] = v.x; o[1] = v.y; }
+__device__ __forceinline__ void vsplit(const double2 &v, double (&o)[2]) { o[0] = v.x; o[1] = v.y; }
+
+// 16-byte read-only load of V consecutive table entries.
+template <class T>
+__device__ __forceinline__ void vload(const T *p, T (&o)[Tr<T>::V])
+{
+    vsplit(__ldg((const typename Tr<T>::Vec *)p), o);
+}
+
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+__host__ __device__ constexpr int ctzc(int v) { return (v & 1) ? 0 : 1 + ctzc(v >> 1); }
+
+template <int N, class Fn>
+__device__ __forceinline__ void static_for(Fn &&fn)
+{
+    [&]<int... I>(std::integer_sequence<int, I...>) { (fn(std::integral_constant<int, I>{}), ...); }(
+        std::make_integer_sequence<int, N>{});
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// min over S register values (tree, S a power of two)
+template <class T, int S>
+__device__ __forceinline__ T tree_min(const T (&E)[S])
+{
+    T m[S / 2];
+#pragma unroll
+    for (int q = 0; q < S / 2; ++q)
+        m[q] = Tr<T>::tmin(E[2 * q], E[2 * q + 1]);
+#pragma unroll
+    for (int w = S / 4; w >= 1; w >>= 1)
+#pragma unroll
+        for (int q = 0; q < w; ++q)
+            m[q] = Tr<T>::tmin(m[2 * q], m[2 * q + 1]);
+    return m[0];
+}
+
+// Offer one state to the candidate buffer.
+template <class T>
+__device__ __forceinline__ void record(const ScanArgs &a, int inst, T E, uint64_t code)
+{
+    InstState *st = a.state + inst;
+    atomicAdd(&st->nrec, 1ull);
+    const unsigned long long idx = atomicAdd(a.nrec, 1ull);
+    if (idx < a.rec_cap) {
+        Rec r;
+        r.key = a.n_inst > 1 ? (((uint64_t)inst << kInstShift) | code) : code;
+        r.e = Tr<T>::bits(E);
+        a.rec[idx] = r;
+    } else {
+        atomicAdd(&st->dropped, 1ull);
+    }
+    Tr<T>::gmin_min(st, E);
+}
+
+// ---- table build (preprocessing of Alg. 1-2: E(U_B), M_int = Q_ps U_B^T, E(U_A)) ------------------
+// One thread per table entry; entries are subset sums of the symmetric coupling matrix W.
+template <class T>
+__global__ void tables_kernel(const Inst *insts)
+{
+    using F = typename Tr<T>::F;
+    const Inst &d = insts[blockIdx.y];
+    if (d.small)
+        return;
+    const int n = d.n, B = d.B, L = d.L;
+    const long NB = 1l << B, NL = 1l << L;
+    const long total = NB * (L + 1) + NL;
+    const F *W = field_matrix<T>(d);
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        if (idx < NB) {  // E_s(j): energy of the suffix pattern j alone
+            const long j = idx;
+            F acc = 0;
+            for (int b = 0; b < B; ++b) {
+                if (!((j >> b) & 1))
+                    continue;
+                acc += W[b * n + b];
+                for (int b2 = b + 1; b2 < B; ++b2)
+                    if ((j >> b2) & 1)
+                        acc += W[b * n + b2];
+            }
+            ((T *)d.Es)[j] = (T)acc;
+        } else if (idx < NB * (L + 1)) {  // M_int row r: coupling of walked variable r to pattern j
+            const long r = (idx - NB) / NB, j = (idx - NB) % NB;
+            const int vr = B + (int)r;
+            F acc = 0;
+            for (int b = 0; b < B; ++b)
+                if ((j >> b) & 1)
+                    acc += W[vr * n + b];
+            ((T *)d.M)[r * NB + j] = (T)acc;
+        } else {  // E_L(g(i)): energy of the i-th walked pattern, stored in walk order
+            const long i = idx - NB * (L + 1);
+            const long g = i ^ (i >> 1);
+            F acc = 0;
+            for (int r = 0; r < L; ++r) {
+                if (!((g >> r) & 1))
+                    continue;
+                acc += W[(B + r) * n + (B + r)];
+                for (int r2 = r + 1; r2 < L; ++r2)
+                    if ((g >> r2) & 1)
+                        acc += W[(B + r) * n + (B + r2)];
+            }
+            ((T *)d.EL)[i] = (T)acc;
+        }
+    }
+}
+
+// ---- direct evaluation for sub-cubes too small to split ---------------------------------------
+template <class T>
+__device__ void small_unit(const ScanArgs &a, const Inst &d, int inst, int lane)
+{
+    using F = typename Tr<T>::F;
+    const int n = d.n;
+    const F *W = field_matrix<T>(d);
+    for (uint64_t s = lane; s < d.sub_count; s += 32) {
+        const uint64_t x = d.sub_base + s;
+        F acc = 0;
+        for (int i = 0; i < n; ++i) {
+            if (!((x >> i) & 1))
+                continue;
+            acc += W[i * n + i];
+            for (int j = i + 1; j < n; ++j)
+                if ((x >> j) & 1)
+                    acc += W[i * n + j];
+        }
+        record<T>(a, inst, (T)acc, x);
+    }
+    if (lane == 0)
+        atomicAdd(&a.state[inst].scanned, (unsigned long long)d.sub_count);
+}
+
+// Fields of the set fixed bits of unit x_f: lane l returns in f0 the coupling of variable l
+// (l < B + L) to the set fixed variables, and every lane returns c(x_f), the energy of the fixed
+// variables alone (Sec. 3.3.1: Q' = Q_rr + diag(x_f Q_fr), c(x_f) = x_f Q_ff x_f^T).
+template <class T>
+__device__ __forceinline__ void unit_fields(const typename Tr<T>::F *W, int n, int k, int BL, uint64_t unit, int lane,
+                                            typename Tr<T>::F &f0, typename Tr<T>::F &cx)
+{
+    using F = typename Tr<T>::F;
+    F a0 = 0, up0 = 0, up1 = 0;
+    for (int f = 0; f < k; ++f) {
+        if (!((unit >> f) & 1ull))
+            continue;
+        const int vf = BL + f;
+        const F *row = W + (size_t)vf * n;
+        if (lane < n && lane != vf) {
+            const F w = row[lane];
+            a0 += w;
+            if (vf > lane)
+                up0 += w;
+        }
+        if (lane + 32 < n && lane + 32 != vf && vf > lane + 32)
+            up1 += row[lane + 32];
+    }
+    F cpart = 0;
+    if (lane >= BL && lane < n && ((unit >> (lane - BL)) & 1ull))
+        cpart += W[lane * n + lane] + up0;
+    if (lane + 32 >= BL && lane + 32 < n && ((unit >> (lane + 32 - BL)) & 1ull))
+        cpart += W[(lane + 32) * n + lane + 32] + up1;
+    f0 = a0;
+    cx = warp_sum(cpart);
+}
+
+// Subset sums of the suffix fields over the bits of this thread's columns
+// j = (g * 32 + lane) * V + e: lin(j) = lin_e[e] + lin_t + lin_g[g].
+template <class F, int V, int G>
+__device__ __forceinline__ void column_fields(F f0, int lane, F &lin_t, F (&lin_e)[V], F (&lin_g)[G])
+{
+    constexpr int LOGV = ilog2c(V), LOGG = ilog2c(G);
+    lin_t = 0;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const F vb = __shfl_sync(kFull, f0, LOGV + i);
+        if ((lane >> i) & 1)
+            lin_t += vb;
+    }
+    lin_e[0] = 0;
+#pragma unroll
+    for (int i = 0; i < LOGV; ++i) {
+        const F vb = __shfl_sync(kFull, f0, i);
+#pragma unroll
+        for (int e = 0; e < (1 << i); ++e)
+            lin_e[e + (1 << i)] = lin_e[e] + vb;
+    }
+    lin_g[0] = 0;
+#pragma unroll
+    for (int i = 0; i < LOGG; ++i) {
+        const F vb = __shfl_sync(kFull, f0, LOGV + 5 + i);
+#pragma unroll
+        for (int g = 0; g < (1 << i); ++g)
+            lin_g[g + (1 << i)] = lin_g[g] + vb;
+    }
+}
+
+// ---- one work unit: all 2^(B+L) states with fixed bits x_f = unit --------------------------------
+template <class T, int S, int RC, bool K1>
+__device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t unit, T &Treg,
+                                          int lane, T *stage, T *wsm)
+{
+    using F = typename Tr<T>::F;
+    constexpr int V = Tr<T>::V;
+    constexpr int G = S / V;
+    constexpr int LOGV = ilog2c(V);
+    constexpr int LOGG = ilog2c(G);
+    constexpr int B = LOGV + 5 + LOGG;
+    constexpr int NB = 1 << B;
+    constexpr int BODY = 1 << (RC + 1);
+    const int n = d.n, L = d.L, k = d.k, BL = B + L;
+    InstState *st = a.state + inst;
+    const F *W = field_matrix<T>(d);
+
+    // Fields of the set fixed bits on every other variable and c(x_f) (Sec. 3.3.1).
+    F f0, cx;
+    unit_fields<T>(W, n, k, BL, unit, lane, f0, cx);
+    // Walked-row couplings w_r, read at every flip of a row >= RC.
+    __syncwarp();
+    if (lane >= B && lane < BL)
+        wsm[lane - B] = (T)f0;
+    __syncwarp();
+
+    // Column fields: lin(j) = sum_b j_b v_b; bits of j are [e | lane | g] (LOGV, 5, LOGG bits).
+    F lin_t, lin_e[V], lin_g[G];
+    column_fields<F, V, G>(f0, lane, lin_t, lin_e, lin_g);
+
+    // Initial suffix-dependent energies (walked bits all zero): E_s(j) + lin(j).
+    const T *Es = (const T *)d.Es;
+    T E[S];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        T ev[V];
+        vload<T>(Es + (g * 32 + lane) * V, ev);
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+            E[g * V + e] = (T)((F)ev[e] + (lin_e[e] + lin_t + lin_g[g]));
+    }
+
+    // Register rows r < RC: M_r[j] + w_r, the walked-fixed coupling of row r folded in.
+    const T *Mt = (const T *)d.M;
+    T Mr[RC][S];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+        const F wr = __shfl_sync(kFull, f0, B + r);
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            T mv[V];
+            vload<T>(Mt + (size_t)r * NB + (g * 32 + lane) * V, mv);
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                Mr[r][g * V + e] = (T)((F)mv[e] + wr);
+        }
+    }
+
+    // Threshold: a state is recorded when its energy is <= Treg (+ margin for float scans).
+    {
+        const T tg = Tr<T>::thr_load(st);
+        Treg = K1 ? Tr<T>::tmin(Treg, tg) : tg;
+    }
+    const T mu = (T)a.margin;
+    T P = (T)cx;  // c(x_f) + coupling of the walked rows >= RC that are set
+    T u = Treg + mu - P;
+
+    // Flip of a walked row kk >= RC (row from memory, runtime sign).
+    auto high_flip = [&](int kk, T sg) {
+        const T *row = Mt + (size_t)kk * NB;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            T mv[V];
+            vload<T>(row + (g * 32 + lane) * V, mv);
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                E[g * V + e] = E[g * V + e] + sg * mv[e];
+        }
+        P = P + sg * wsm[kk];
+        u = Treg + mu - P;
+    };
+
+    const T *ELp = (const T *)d.EL;
+    const int nblk = 1 << (L - RC - 1);
+    const uint64_t cbase = unit << BL;
+
+    for (int blk = 0; blk < nblk; ++blk) {
+        const int i0 = blk * BODY;
+        T elv[V];
+        static_for<BODY>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            if constexpr (p > 0) {
+                constexpr int kk = ctzc(p);
+                if constexpr (kk < RC) {
+                    constexpr bool neg = (p >> (kk + 1)) & 1;
+#pragma unroll
+                    for (int q = 0; q < S; ++q)
+                        E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
+                } else {
+                    high_flip(RC, (blk & 1) ? (T)-1 : (T)1);
+                }
+            }
+            if constexpr (p % V == 0)
+                vload<T>(ELp + i0 + p, elv);
+            const T el = elv[p % V];
+            T t = u - el;
+            const T m = tree_min<T, S>(E);
+            if (m <= t) {
+                // Slow path: record every column at or below the threshold.
+#pragma unroll
+                for (int q = 0; q < S; ++q)
+                    stage[q * 32 + lane] = E[q];
+                const int i = i0 + p;
+                const uint64_t cb = cbase | ((uint64_t)(i ^ (i >> 1)) << B);
+                const T Ep = P + el;
+#pragma unroll 1
+                for (int q = 0; q < S; ++q) {
+                    const T ev = stage[q * 32 + lane];
+                    if (ev <= t) {
+                        const T Et = ev + Ep;
+                        const uint32_t j = (uint32_t)(((q / V) * 32 + lane) * V + (q % V));
+                        record<T>(a, inst, Et, cb | j);
+                        if (K1 && Et < Treg) {
+                            Treg = Et;
+                            u = Treg + mu - P;
+                            t = u - el;
+                            Tr<T>::thr_min(st, Et);
+                        }
+                    }
+                }
+            }
+        });
+        if (blk + 1 < nblk) {
+            const int ip = (blk + 1) * BODY;
+            const int kk = __ffs(ip) - 1;
+            high_flip(kk, ((ip >> (kk + 1)) & 1) ? (T)-1 : (T)1);
+        }
+    }
+
+    if (lane == 0)
+        atomicAdd(&st->scanned, 1ull << BL);
+
+    if constexpr (Tr<T>::kFloat) {
+        // Re-anchoring check: the walk ends at g = 2^(L-1); recompute those energies from the
+        // tables and compare with the incrementally updated ones.
+        F f0r, cxr, lt, le[V], lg[G];
+        unit_fields<T>(W, n, k, BL, unit, lane, f0r, cxr);
+        column_fields<F, V, G>(f0r, lane, lt, le, lg);
+        const T *rowL = Mt + (size_t)(L - 1) * NB;
+        double dmax = 0.0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            T ev[V], mv[V];
+            vload<T>(Es + (g * 32 + lane) * V, ev);
+            vload<T>(rowL + (g * 32 + lane) * V, mv);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const T fresh = (T)((F)ev[e] + (le[e] + lt + lg[g])) + mv[e];
+                dmax = fmax(dmax, fabs((double)E[g * V + e] - (double)fresh));
+            }
+        }
+        const F wl = __shfl_sync(kFull, f0r, B + L - 1);
+        dmax = fmax(dmax, fabs((double)P - (double)(T)(cxr + wl)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
+        if (lane == 0)
+            atomicMax(&st->drift, (unsigned long long)__double_as_longlong(dmax));
+    }
+}
+
+template <class T, int S, int RC, bool K1, int MINB>
+__global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs a)
+{
+    __shared__ T stage_all[kScanThreads / 32][S * 32];
+    __shared__ T wsm_all[kScanThreads / 32][kMaxWalkBits];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *stage = stage_all[warp];
+    T *wsm = wsm_all[warp];
+    int cur = -1;
+    T Treg = (T)0;
+    for (;;) {
+        unsigned long long item = 0;
+        int stop = 0;
+        if (lane == 0) {
+            stop = *a.abort_flag != 0;
+            if (!stop)
+                item = atomicAdd(a.queue, 1ull);
+        }
+        stop = __shfl_sync(kFull, stop, 0);
+        item = __shfl_sync(kFull, item, 0);
+        if (stop || item >= a.total_items)
+            break;
+        int inst = 0;
+        if (a.n_inst > 1) {
+            int lo = 0, hi = a.n_inst;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (a.item_base[mid] <= item)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            inst = lo;
+        }
+        if (inst != cur) {
+            cur = inst;
+            Treg = Tr<T>::thr_load(a.state + inst);
+        }
+        const Inst d = a.inst[inst];
+        const uint64_t off = item - a.item_base[inst];
+        if (d.small)
+            small_unit<T>(a, d, inst, lane);
+        else
+            scan_unit<T, S, RC, K1>(a, d, inst, d.unit_begin + off, Treg, lane, stage, wsm);
+    }
+}
+
+}  // namespace qubo

@@ -1,0 +1,90 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every entry point that
+include/qubo.h declares, and its host-only logic (status strings, result merge, argument
+checks) behaves."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_04857_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2607_04857_gb300 import build as qbuild
+
+    qbuild.build()
+    import paper_2607_04857_gb300 as q
+
+    q.load_library()
+    return q
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "qubo.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qubo_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_list(q):
+    assert declared_functions() == sorted(q.EXPORTS)
+
+
+def test_every_declared_symbol_is_exported(q):
+    import ctypes
+
+    lib = ctypes.CDLL(q.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_library_is_the_in_tree_build(q):
+    assert os.path.dirname(q.LIB_PATH) == os.path.join(ROOT, "paper_2607_04857_gb300")
+
+
+def test_strerror_and_version(q):
+    assert q.strerror(0) == "ok"
+    assert "argument" in q.strerror(-1)
+    assert "sm_103a" in q.version()
+
+
+def test_bad_arguments_are_rejected_before_any_device_work(q):
+    lib = q.load_library()
+    Q = np.zeros((4, 4), dtype=np.int32)
+    out = np.zeros(1, dtype=np.int64)
+    # n out of range, bad dtype, null Q, topk beyond the cap
+    assert lib.qubo_solve(Q.ctypes.data, 0, 2, 0, 0, out.ctypes.data, None, 0, None, None, None, None) == -1
+    assert lib.qubo_solve(Q.ctypes.data, 65, 2, 0, 0, out.ctypes.data, None, 0, None, None, None, None) == -1
+    assert lib.qubo_solve(Q.ctypes.data, 4, 9, 0, 0, out.ctypes.data, None, 0, None, None, None, None) == -1
+    assert lib.qubo_solve(None, 4, 2, 0, 0, out.ctypes.data, None, 0, None, None, None, None) == -1
+    assert lib.qubo_solve(Q.ctypes.data, 4, 2, 0, 5000, out.ctypes.data, None, 0, None, None, None, None) == -1
+
+
+def _as_result(q, o, scanned):
+    return q.Result(o.min, o.n_ties, o.ties, o.topk, o.topk_E, 0, {"states_scanned": scanned})
+
+
+@pytest.mark.parametrize("kind", ["int", "float", "degenerate"])
+def test_merge_of_subcube_results_equals_full_solve(q, kind):
+    """qubo_merge (the reduce of Sec. 3.3) applied to oracle results of disjoint sub-cubes gives
+    the oracle result of the whole cube."""
+    n, f, K, cap = 16, 3, 8, 100
+    if kind == "int":
+        Q = wl.upper_int(n, -20, 20, seed=5)
+    elif kind == "float":
+        Q = wl.sk_float32(n, seed=6)
+    else:
+        Q = wl.diagonal(n, seed=7, zeros=9)
+    full = oracle.solve(Q, topk=K, cap=cap)
+    acc = None
+    for v in range(1 << f):
+        part = _as_result(q, oracle.solve(Q, topk=K, cap=cap, fix_bits=f, fix_value=v), 1 << (n - f))
+        acc = part if acc is None else q.merge(acc, part, cap, K)
+    assert acc.min == full.min and acc.n_ties == full.n_ties
+    assert np.array_equal(acc.ties, full.ties)
+    assert np.array_equal(acc.topk, full.topk) and np.array_equal(acc.topk_E, full.topk_E)
+    assert acc.info["states_scanned"] == 1 << n

@@ -1,0 +1,266 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integer Q: minimum, exact tie count, tie codes and K lowest states must be bit-exact.
+Float Q: the tie set and the K lowest codes must be identical and the minimum within 1e-9
+relative of the oracle's FP64 value (both sides evaluate the final energies with the same
+fixed-order FP64 sum, so in practice they are equal).
+"""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_04857_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FLOAT_RTOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_04857_gb300 import build as qbuild
+
+    qbuild.build()
+    import paper_2607_04857_gb300 as q
+
+    q.load_library()
+    return q
+
+
+def check_int(r, o, cap=None):
+    assert r.min == o.min, (r.min, o.min)
+    assert r.n_ties == o.n_ties, (r.n_ties, o.n_ties)
+    assert np.array_equal(r.ties, o.ties), (r.ties[:8], o.ties[:8])
+    assert np.array_equal(r.topk, o.topk), (r.topk, o.topk)
+    assert np.array_equal(r.topk_E, o.topk_E), (r.topk_E, o.topk_E)
+
+
+def check_float(r, o):
+    assert abs(r.min - o.min) <= FLOAT_RTOL * max(1.0, abs(o.min)), (r.min, o.min)
+    assert r.n_ties == o.n_ties
+    assert np.array_equal(r.ties, o.ties)
+    assert np.array_equal(r.topk, o.topk), (r.topk, o.topk)
+    assert np.allclose(r.topk_E, o.topk_E, rtol=FLOAT_RTOL, atol=FLOAT_RTOL)
+
+
+# --- integers -----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 5, 9, 13])
+def test_direct_path_small_n(q, n):
+    for seed in range(3):
+        Q = wl.upper_int(n, -9, 9, seed=seed)
+        K = min(1 << n, 16)
+        check_int(q.solve(Q, topk=K), oracle.solve(Q, method=oracle.DIRECT, topk=K))
+
+
+@pytest.mark.parametrize("n", [14, 15, 16, 19, 22, 26])
+@pytest.mark.parametrize("topk", [0, 1, 16])
+def test_int_parity(q, n, topk):
+    for seed in range(2):
+        Q = wl.upper_int(n, -30, 30, seed=1000 * n + seed)
+        check_int(q.solve(Q, topk=topk), oracle.solve(Q, topk=topk))
+
+
+def test_full_nonsymmetric_int_q(q):
+    rng = np.random.default_rng(3)
+    Q = rng.integers(-50, 50, size=(21, 21)).astype(np.int32)
+    check_int(q.solve(Q, topk=8), oracle.solve(Q, topk=8))
+
+
+def test_config1_n24(q):
+    Q = wl.config1()
+    r = q.solve(Q)
+    check_int(r, oracle.solve(Q, method=oracle.DIRECT))
+    assert r.info["states_scanned"] == 1 << 24 and r.info["acc"] == "i32"
+
+
+@pytest.mark.parametrize("walk_bits", [4, 5, 8, 11, 13])
+def test_plan_shapes_agree(q, walk_bits):
+    Q = wl.upper_int(27, -200, 200, seed=77)
+    o = oracle.solve(Q, topk=16)
+    r = q.solve(Q, topk=16, walk_bits=walk_bits)
+    check_int(r, o)
+    assert r.info["walk_bits"] == walk_bits
+
+
+def test_int64_accumulator_for_wide_range(q):
+    Q = wl.upper_int(20, -2**31, 2**31 - 1, seed=5)
+    r = q.solve(Q, topk=4)
+    assert r.info["acc"] == "i64"
+    check_int(r, oracle.solve(Q, topk=4))
+
+
+def test_plain_int64_scan_matches(q):
+    Q = wl.upper_int(23, -1000, 1000, seed=6)
+    r = q.solve(Q, topk=16, plain=True)
+    assert r.info["acc"] == "i64"
+    check_int(r, oracle.solve(Q, topk=16))
+
+
+def test_int16_input(q):
+    Q = wl.upper_int(20, -127, 127, seed=8, dtype=np.int16)
+    check_int(q.solve(Q, topk=3), oracle.solve(Q.astype(np.int32), topk=3))
+
+
+# --- special instances --------------------------------------------------------------------
+
+def test_zero_matrix_truncation(q):
+    n = 18
+    Q = np.zeros((n, n), dtype=np.int32)
+    r = q.solve(Q, topk=5, states_cap=1000)
+    assert r.min == 0 and r.n_ties == 1 << n and r.truncated and r.status == q.QUBO_TRUNCATED
+    assert np.array_equal(r.ties, np.arange(1000, dtype=np.uint64))
+    assert np.array_equal(r.topk, np.arange(5, dtype=np.uint64))
+
+
+def test_diagonal_tie_set(q):
+    Q = wl.diagonal(24, seed=3, zeros=7)
+    check_int(q.solve(Q, states_cap=1 << 10), oracle.solve(Q, cap=1 << 10))
+
+
+def test_planted(q):
+    Q, xs = wl.planted(30, seed=4)
+    r = q.solve(Q)
+    assert r.n_ties == 1 and int(r.ties[0]) == xs
+
+
+def test_maxcut_complement_pairs(q):
+    Q = wl.maxcut_qubo(24, 0.5, seed=9)
+    r = q.solve(Q, topk=6)
+    check_int(r, oracle.solve(Q, topk=6))
+    full = (1 << 24) - 1
+    ties = set(int(t) for t in r.ties)
+    assert all((full ^ t) in ties for t in ties)
+
+
+def test_relabelled_instance_same_minimum(q):
+    Q = wl.upper_int(25, -100, 100, seed=10)
+    perm = np.random.default_rng(2).permutation(25)
+    a, b = q.solve(Q), q.solve(Q[np.ix_(perm, perm)])
+    assert a.min == b.min and a.n_ties == b.n_ties
+
+
+# --- sub-cubes, merge, device-resident problems ------------------------------------------
+
+def test_subcubes_merge_to_whole(q):
+    Q = wl.upper_int(28, -64, 64, seed=12)
+    whole = q.solve(Q, topk=16)
+    acc = None
+    for v in range(8):
+        part = q.solve(Q, topk=16, fix_bits=3, fix_value=v)
+        assert part.info["states_scanned"] == 1 << 25
+        acc = part if acc is None else q.merge(acc, part, 1 << 16, 16)
+    check_int(acc, whole)
+    check_int(whole, oracle.solve(Q, topk=16))
+
+
+def test_problem_run_fetch(q):
+    Q = wl.upper_int(26, -500, 500, seed=13)
+    p = q.Problem(Q, topk=16)
+    parts = []
+    for v in range(4):
+        p.run(2, v)
+        parts.append(p.fetch())
+    p.close()
+    acc = parts[0]
+    for r in parts[1:]:
+        acc = q.merge(acc, r, 1 << 16, 16)
+    check_int(acc, oracle.solve(Q, topk=16))
+
+
+def test_overflow_splits_and_stays_exact(q):
+    """A tiny candidate buffer forces the split-and-merge path; results stay exact."""
+    code = (
+        "import numpy as np, oracle, paper_2607_04857_gb300 as q;"
+        "from paper_2607_04857_gb300 import workloads as wl;"
+        "Q = wl.diagonal(20, seed=3, zeros=12);"
+        "r = q.solve(Q, topk=4, states_cap=500); o = oracle.solve(Q, topk=4, cap=500);"
+        "assert r.min == o.min and r.n_ties == o.n_ties == 4096, (r.n_ties, o.n_ties);"
+        "assert np.array_equal(r.ties, o.ties) and np.array_equal(r.topk, o.topk);"
+        "assert r.info['passes'] > 1, r.info; print('passes', r.info['passes'])"
+    )
+    env = dict(os.environ, QUBO_MAX_RECORDS="1000")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stdout + res.stderr
+
+
+# --- floats ---------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [6, 14, 18, 22, 25])
+def test_float_parity(q, n):
+    for seed in range(2):
+        Q = wl.sk_float32(n, seed=500 + n + seed)
+        r = q.solve(Q, topk=8)
+        check_float(r, oracle.solve(Q, topk=8))
+        assert r.info["acc"] == "f32" or n < 14
+
+
+def test_float64_input_and_plain_fp64(q):
+    Q = wl.sk_float32(21, seed=44).astype(np.float64)
+    o = oracle.solve(Q, topk=8)
+    check_float(q.solve(Q, topk=8), o)
+    rp = q.solve(Q, topk=8, plain=True)
+    assert rp.info["acc"] == "f64"
+    check_float(rp, o)
+
+
+def test_float_drift_within_margin(q):
+    Q = wl.config3()[:30, :30].copy()
+    r = q.solve(Q, topk=4)
+    assert r.info["acc"] == "f32"
+    assert 2 * r.info["fp32_max_drift"] < 1e-3
+    assert r.info["fp32_max_abs_err"] < 1e-3
+    check_float(r, oracle.solve(Q, topk=4))
+
+
+# --- batched ----------------------------------------------------------------------------------
+
+def test_batched_matches_per_instance(q):
+    insts = wl.config4(count=96, seed=4)
+    insts = [Q for Q in insts if Q.shape[0] <= 24][:40]
+    insts += [wl.upper_int(n, -127, 127, seed=n, dtype=np.int16) for n in (3, 8, 12, 13)]
+    rs = q.solve_batched(insts, topk=4, states_cap=64)
+    for Q, r in zip(insts, rs):
+        o = oracle.solve(Q.astype(np.int32), topk=4, cap=64)
+        check_int(r, o)
+        assert r.info["states_scanned"] == 1 << Q.shape[0]
+
+
+def test_batched_float(q):
+    insts = [wl.sk_float32(n, seed=n) for n in (10, 15, 18, 20, 16)]
+    rs = q.solve_batched(insts, topk=2)
+    for Q, r in zip(insts, rs):
+        check_float(r, oracle.solve(Q, topk=2))
+
+
+# --- the n=50 configuration, sampled ---------------------------------------------------------
+
+def test_n50_sampled_subcubes(q):
+    """The n=50 instance with the plan the benchmark uses (walk 12, suffix 10 bits): sub-cubes
+    of 2^24 states at sampled prefixes, each checked against the oracle."""
+    Q = wl.config5()
+    rng = np.random.default_rng(50)
+    for v in rng.integers(0, 1 << 26, size=6):
+        r = q.solve(Q, topk=16, fix_bits=26, fix_value=int(v), walk_bits=12)
+        assert r.info["split_k"] == 28 and r.info["acc"] == "i32"
+        check_int(r, oracle.solve(Q, topk=16, fix_bits=26, fix_value=int(v)))
+
+
+# --- time limit ------------------------------------------------------------------------------
+
+def test_time_limit_returns_timeout(q):
+    Q = wl.upper_int(46, -1000, 1000, seed=1)
+    with pytest.raises(q.QuboError) as e:
+        q.solve(Q, time_limit=0.2)
+    assert e.value.status == q.QUBO_ERR_TIMEOUT
+    # the context stays usable
+    Q2 = wl.upper_int(20, -10, 10, seed=2)
+    check_int(q.solve(Q2), oracle.solve(Q2))
