@@ -1,0 +1,441 @@
+#!/usr/bin/env python
+"""Benchmark of the exhaustive dense-QUBO scan on GB300.
+
+Default workload: the n=50 dense QUBO with int32 entries uniform in [-32768, 32767] (seed 5),
+int32 energies, tie set and the 16 lowest states.  One step is one full pass of the path
+(table build, Gray-walk enumeration, reduction and extraction) over one sub-cube of that
+instance with its top `--fix-bits` code bits fixed (2^(50-fix_bits) states); consecutive steps
+take consecutive sub-cubes, so 2^fix_bits steps cover the whole instance.  The rate is states
+per second (2^n / total time, the paper's convention, Sec. 5.3).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n50_int32|n44_fp32|batched]
+  python bench.py --impl reference ...   (the CPU oracle on the host cores, same workload)
+
+Under torchrun every rank takes disjoint sub-cubes (no data-path collective; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2607_04857_gb300 import workloads as wl  # noqa: E402
+
+LANES_PER_SM = 128          # FP32/INT32 lanes per Blackwell SM
+ALG_OPS_PER_STATE = 2       # one add and one min per state (Sec. 3.2; Sec. 4.2 on the min)
+PAPER_CONTEXT = "7.47e12 states/s, int16 energies, 1x H100 (paper Tab. 1); other machine and dtype"
+PROFILE_JSON = os.path.join(ROOT, "profiles", "scan_kernel_counters.json")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------------------------
+
+def make_workload(name: str, fix_bits: int | None):
+    if name == "n50_int32":
+        fb = 7 if fix_bits is None else fix_bits
+        return dict(name=name, Q=wl.config5(), n=50, topk=16, fix_bits=fb, metric="states/s (n=50 int32 dense QUBO)",
+                    unit="states/s", dtype="int32",
+                    config={"workload": "n50_int32_top16", "n": 50, "topk": 16, "seed": 5,
+                            "entries": "upper-triangular int32 uniform [-32768, 32767]",
+                            "step": f"one sub-cube of 2^{50 - fb} states (top {fb} code bits fixed)"})
+    if name == "n44_fp32":
+        fb = 2 if fix_bits is None else fix_bits
+        return dict(name=name, Q=wl.config3(), n=44, topk=0, fix_bits=fb, metric="states/s (n=44 FP32 SK-like QUBO)",
+                    unit="states/s", dtype="f32",
+                    config={"workload": "n44_fp32_sk", "n": 44, "seed": 3, "margin": 1e-3,
+                            "entries": "symmetric FP32, off-diagonal N(0,1)/sqrt(44), diagonal N(0,1)",
+                            "anchor": "every unit walk (<= 2^16 Gray steps)",
+                            "step": f"one sub-cube of 2^{44 - fb} states (top {fb} code bits fixed)"})
+    if name == "batched":
+        return dict(name=name, Qs=wl.config4(), topk=0, metric="instances/s (4096 QUBOs, n uniform in 16..32)",
+                    unit="instances/s", dtype="int32",
+                    config={"workload": "batched_4096_n16_32", "count": 4096, "seed": 4,
+                            "entries": "even: int16 uniform [-127,127]; odd: Max-Cut G(n,0.5) weights +-1",
+                            "step": "one persistent launch over all 4096 instances"})
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------------------------
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("scan_impl.cuh", "scan_i32.cu", "scan_f32.cu", "internal.h"):
+        with open(os.path.join(ROOT, "paper_2607_04857_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_counters(acc: str):
+    """ncu counters committed under profiles/ for the scan kernel, if they were taken on the
+    current kernel source; else None."""
+    try:
+        with open(PROFILE_JSON) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get(acc)
+    if not e or e.get("kernel_hash") != kernel_source_hash():
+        return None
+    return e
+
+
+def flush_l2(buf):
+    if buf is not None:
+        buf.add_(1)
+
+
+def cpu_oracle_rate(Q, n: int, target_s: float, fix_hint: int):
+    """Time the CPU oracle (Gray-walk, all host cores) on sub-cubes of the same instance."""
+    import oracle
+
+    fb = max(0, n - 28)
+    t = time.perf_counter()
+    oracle.solve(Q, method=oracle.GRAY, topk=16, fix_bits=fb, fix_value=1)
+    dt = time.perf_counter() - t
+    rate = (1 << (n - fb)) / dt
+    # grow the sample to about target_s seconds
+    free = n - fb
+    while free < n and (1 << (free + 1)) / rate < target_s:
+        free += 1
+    fb2 = n - free
+    t = time.perf_counter()
+    oracle.solve(Q, method=oracle.GRAY, topk=16, fix_bits=fb2, fix_value=2 if fb2 > 1 else 0)
+    dt = time.perf_counter() - t
+    return (1 << free) / dt, dt, fb2, oracle.max_threads()
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------------------------
+
+def run_reference(args, W):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    if W["name"] == "batched":
+        Qs = W["Qs"]
+        order = np.random.default_rng(0).permutation(len(Qs))
+        # bounded sample: instances solved one by one until each step takes ~2 s
+        per = []
+        t0 = time.perf_counter()
+        i = 0
+        times = []
+        for s in range(args.warmup + args.steps):
+            ts = time.perf_counter()
+            cnt = 0
+            while time.perf_counter() - ts < 2.0:
+                Q = Qs[order[i % len(Qs)]]
+                oracle.solve(Q.astype(np.int32), method=oracle.GRAY)
+                i += 1
+                cnt += 1
+            if s >= args.warmup:
+                times.append((cnt, time.perf_counter() - ts))
+        value = sum(c for c, _ in times) / sum(t for _, t in times)
+        sample = "instances of the 4096-instance batch, solved one by one on the host cores"
+        ms = 1000 * sum(t for _, t in times) / len(times)
+        del per, t0
+    else:
+        Q, n = W["Q"], W["n"]
+        # each step: one sub-cube of about 1 s of oracle work
+        fb = max(0, n - 28)
+        t = time.perf_counter()
+        oracle.solve(Q, method=oracle.GRAY, topk=W["topk"], fix_bits=fb, fix_value=3)
+        rate = (1 << (n - fb)) / (time.perf_counter() - t)
+        free = n - fb
+        while (1 << (free + 1)) / rate < 1.0:
+            free += 1
+        fb = n - free
+        times = []
+        for s in range(args.warmup + args.steps):
+            t = time.perf_counter()
+            oracle.solve(Q, method=oracle.GRAY, topk=W["topk"], fix_bits=fb, fix_value=s % (1 << fb))
+            if s >= args.warmup:
+                times.append(time.perf_counter() - t)
+        value = args.steps * (1 << free) / sum(times)
+        sample = f"sub-cubes of 2^{free} states (top {fb} bits fixed) of the same instance per step"
+        ms = 1000 * sum(times) / len(times)
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": W["metric"], "value": value, "unit": W["unit"], "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": W["dtype"], "data": "synthetic",
+            "config": W["config"],
+            "cpu_baseline": {"value": value, "unit": W["unit"], "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": W["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n50_int32", choices=["n50_int32", "n44_fp32", "batched"])
+    ap.add_argument("--fix-bits", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    W = make_workload(args.workload, args.fix_bits)
+    if args.impl == "reference":
+        return run_reference(args, W)
+
+    import torch
+
+    import paper_2607_04857_gb300 as q
+    from paper_2607_04857_gb300 import build as qbuild
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if rank == 0:
+        qbuild.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group(backend="nccl")
+        dist.barrier(device_ids=[local]) if torch.cuda.is_available() else dist.barrier()
+        if rank != 0:
+            qbuild.build()
+    torch.cuda.set_device(local)
+    q.load_library()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sms = q.device_sm_count()
+    l2buf = torch.zeros(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier(device_ids=[local])
+        torch.cuda.synchronize(dev)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and W["name"] != "batched":
+        # the oracle runs on the host cores before the GPU timing (it uses threads, no fork)
+        rate, dt, fb, cores = cpu_oracle_rate(W["Q"], W["n"], 12.0, W["fix_bits"])
+        cpu = {"value": rate, "unit": "states/s", "cores": cores, "kind": "oracle",
+               "sample": f"Gray-walk oracle on one sub-cube of 2^{W['n'] - fb} states of the same instance "
+                         f"({dt:.1f} s)"}
+        log(f"cpu oracle: {rate:.3e} states/s on {cores} threads")
+
+    launches = 0
+    scan_s = []
+    states_per_step = 0
+    sampler = ClockSampler(local)
+
+    if W["name"] == "batched":
+        Qs = W["Qs"]
+        mats = [q.as_qubo_matrix(Q)[0] for Q in Qs]
+
+        def step(_):
+            rs = q.solve_batched(mats, topk=0, states_cap=64, stream=stream)
+            return rs[0].info, len(rs)
+
+        for s in range(args.warmup):
+            step(s)
+        barrier()
+        sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        infos = []
+        for s in range(args.steps):
+            flush_l2(l2buf)
+            ev[s][0].record(stream)
+            info, cnt = step(s)
+            ev[s][1].record(stream)
+            infos.append(info)
+        barrier()
+        clocks = sampler.stop()
+        t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+        units = args.steps * len(Qs)
+        launches = sum(i["kernel_launches"] for i in infos)
+        scan_s = [i["seconds_scan"] for i in infos]
+        states_per_step = sum(1 << Q.shape[0] for Q in Qs)
+        e2e_val, h2d, d2h = units / t_dev, infos[0]["h2d_bytes"], infos[0]["d2h_bytes"]
+        e2e_note = "qubo_solve_batched from host buffers (copies inside every step)"
+    else:
+        Q, n, topk, fb = W["Q"], W["n"], W["topk"], W["fix_bits"]
+        nsub = 1 << fb
+        my = [v for v in range(nsub) if v % world == rank]
+
+        def sub(s):
+            return my[s % len(my)]
+
+        # value: device-resident problem, inputs uploaded before the timed region
+        prob = q.Problem(Q, topk=topk)
+        for s in range(args.warmup):
+            prob.run(fb, sub(s), stream)
+            prob.fetch()
+        barrier()
+        sampler.start()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        infos = []
+        for s in range(args.steps):
+            flush_l2(l2buf)
+            ev[s][0].record(stream)
+            prob.run(fb, sub(args.warmup + s), stream)
+            r = prob.fetch()
+            ev[s][1].record(stream)
+            infos.append(r.info)
+        barrier()
+        clocks = sampler.stop()
+        prob.close()
+        t_dev = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+        states_per_step = 1 << (n - fb)
+        units = args.steps * states_per_step
+        launches = sum(i["kernel_launches"] for i in infos)
+        scan_s = [i["seconds_scan"] for i in infos]
+        # e2e: the public call with host buffers, copies inside every step
+        q.solve(Q, topk=topk, fix_bits=fb, fix_value=sub(0), stream=stream)
+        barrier()
+        t = time.perf_counter()
+        for s in range(args.steps):
+            r = q.solve(Q, topk=topk, fix_bits=fb, fix_value=sub(args.warmup + s), stream=stream)
+        torch.cuda.synchronize(dev)
+        t_e2e = time.perf_counter() - t
+        e2e_val = units / t_e2e
+        h2d, d2h = r.info["h2d_bytes"], r.info["d2h_bytes"]
+        e2e_note = "qubo_solve_ex from host buffers (Q upload and result download inside every step)"
+
+    # max over ranks
+    t_max = t_dev
+    if dist is not None:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        ee = torch.tensor([e2e_val], dtype=torch.float64, device=dev)
+        dist.all_reduce(ee, op=dist.ReduceOp.SUM)
+        e2e_val = float(ee.item())
+    value = units * world / t_max
+
+    # roofline of the enumeration kernel: algorithmic ALU ops per launch / its event-timed duration
+    mean_scan = sum(scan_s) / len(scan_s)
+    if W["name"] == "batched":
+        per_launch_states = states_per_step
+    else:
+        per_launch_states = states_per_step
+    achieved = ALG_OPS_PER_STATE * per_launch_states / mean_scan / 1e9
+    clk_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = sms * LANES_PER_SM * clk_max * 1e6 / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "scan_kernel",
+            "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x {clk_max:.0f} MHz; 2 ops/state (add + min)"}
+    if clocks and clocks.get("sm_mhz"):
+        roof["frac_at_sampled_clock"] = achieved / (sms * LANES_PER_SM * clocks["sm_mhz"] * 1e-3)
+    acc = "i32" if W["dtype"] == "int32" else "f32"
+    prof = profile_counters(acc)
+    if prof:
+        roof["traffic"] = prof.get("dram_bytes_per_launch_scaled")
+        if prof.get("inst_per_state") and clocks:
+            ips = prof["inst_per_state"]
+            issue = sms * LANES_PER_SM * clocks["sm_mhz"] * 1e6 / ips
+            roof["issue_roofline"] = {"inst_per_state": ips, "states_per_s": issue,
+                                      "frac": (per_launch_states / mean_scan) / issue}
+
+    if rank == 0:
+        line = {"metric": W["metric"], "value": value, "unit": W["unit"], "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": W["dtype"], "data": "synthetic",
+                "config": dict(W["config"], parallelism=f"{world} GPU(s), disjoint sub-cubes per rank" if world > 1
+                               else "1 GPU", l2="256 MiB buffer written between timed steps (L2 is 129 MB)",
+                               states_per_step=states_per_step),
+                "e2e": {"value": e2e_val, "unit": W["unit"], "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "how": e2e_note},
+                "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+                "scan_kernel_ms_mean": mean_scan * 1000, "context": PAPER_CONTEXT}
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -97,10 +97,16 @@ typedef struct {
     uint64_t candidates;      /* states that passed the threshold and were recorded */
     double seconds;           /* wall time of the call */
     double seconds_gpu;       /* device time of tables + scan + finalize (CUDA events) */
+    double seconds_scan;      /* device time of the enumeration kernel alone (CUDA events on
+                                 the launching stream; summed over passes) */
     double states_per_s;      /* states_scanned / seconds */
     int32_t n, split_k, walk_bits, suffix_bits; /* plan: n = split_k + walk_bits + suffix_bits */
     int32_t cols_per_thread, threads, blocks, passes; /* launch shape; passes > 1 if the
                                  candidate buffer overflowed and the scan was repeated */
+    int32_t kernel_launches;  /* kernels this call launched (all passes) */
+    int32_t reserved1;
+    uint64_t h2d_bytes;       /* bytes copied host -> device by this call */
+    uint64_t d2h_bytes;       /* bytes copied device -> host by this call */
 } qubo_result;
 
 /*

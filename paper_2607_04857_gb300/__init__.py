@@ -55,10 +55,12 @@ class ResultInfo(ctypes.Structure):
         ("n_topk", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("fp32_max_abs_err", ctypes.c_double),
         ("fp32_max_drift", ctypes.c_double), ("n_near_ties", ctypes.c_uint64),
         ("states_scanned", ctypes.c_uint64), ("candidates", ctypes.c_uint64), ("seconds", ctypes.c_double),
-        ("seconds_gpu", ctypes.c_double), ("states_per_s", ctypes.c_double), ("n", ctypes.c_int32),
+        ("seconds_gpu", ctypes.c_double), ("seconds_scan", ctypes.c_double), ("states_per_s", ctypes.c_double),
+        ("n", ctypes.c_int32),
         ("split_k", ctypes.c_int32), ("walk_bits", ctypes.c_int32), ("suffix_bits", ctypes.c_int32),
         ("cols_per_thread", ctypes.c_int32), ("threads", ctypes.c_int32), ("blocks", ctypes.c_int32),
-        ("passes", ctypes.c_int32),
+        ("passes", ctypes.c_int32), ("kernel_launches", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:

@@ -25,6 +25,9 @@ constexpr unsigned long long kDefaultRecCap = 1ull << 22;  // candidate records 
 constexpr double kDefaultMargin = 1e-3;
 constexpr int kTargetUnitsLog2 = 15;   // aim for >= 2^15 work units per scan
 constexpr int kDefaultMaxWalkBits = 12;
+// FP32 scans re-anchor at every unit start, so the walk length is the anchoring period: 2^8
+// Gray steps keep the measured drift far below the default 1e-3 candidate margin.
+constexpr int kFloatMaxWalkBits = 8;
 
 double now_s()
 {
@@ -132,7 +135,8 @@ int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bi
     else if (walk_bits > 0)
         L = walk_bits;
     else
-        L = std::max(kRegRows + 1, std::min(kDefaultMaxWalkBits, free_bits - h.B - kTargetUnitsLog2));
+        L = std::max(kRegRows + 1, std::min(h.acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits,
+                                            free_bits - h.B - kTargetUnitsLog2));
     const int k = n - h.B - L;
     if (L < kRegRows + 1 || L > kMaxWalkBits || k < fix_bits || k > 63)
         return QUBO_ERR_ARG;
@@ -367,7 +371,7 @@ struct Workspace {
     size_t down_cap = 0;
     int *h_abort = nullptr;        // host-mapped flag read by the scan kernel
     const int *d_abort = nullptr;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // tables start, scan end, finalize end, scan start
     std::mutex mu;
 
     ~Workspace() { release(); }
@@ -561,6 +565,10 @@ struct Job {
     unsigned long long rec_cap = 0;
     double t_start = 0.0;
     bool aborted = false;
+    // accounting
+    int launches = 0;
+    uint64_t h2d = 0, d2h = 0;
+    double scan_seconds = 0.0;
 };
 
 int job_layout(Job &j)
@@ -584,7 +592,8 @@ int job_layout(Job &j)
         const HostInst &h = *j.insts[i];
         const size_t nn = (size_t)h.n * h.n;
         if (h.is_float) {
-            j.off_W[i] = 0;
+            j.off_W[i] = o;
+            o = align_up(o + (size_t)eb * nn, 256);
             j.off_W64[i] = o;
             o = align_up(o + 8 * nn, 256);
             j.off_U64[i] = o;
@@ -664,10 +673,15 @@ int job_launch(Workspace &ws, Job &j)
             for (int a = 0; a < h.n; ++a)
                 for (int b = 0; b < h.n; ++b) {
                     const int lo = std::min(a, b), hi2 = std::max(a, b);
-                    W64[(size_t)a * h.n + b] = h.Uf[(size_t)lo * h.n + hi2];
+                    const double w = h.Uf[(size_t)lo * h.n + hi2];
+                    W64[(size_t)a * h.n + b] = w;
                     U64[(size_t)a * h.n + b] = h.Uf[(size_t)a * h.n + b];
+                    if (j.acc == ACC_F32)
+                        ((float *)(up + j.off_W[i]))[(size_t)a * h.n + b] = (float)w;
+                    else
+                        ((double *)(up + j.off_W[i]))[(size_t)a * h.n + b] = w;
                 }
-            d.W = nullptr;
+            d.W = dev + j.off_W[i];
             d.W64 = (const double *)(dev + j.off_W64[i]);
             d.U64 = (const double *)(dev + j.off_U64[i]);
         } else {
@@ -707,6 +721,7 @@ int job_launch(Workspace &ws, Job &j)
     CK(cudaMemsetAsync(dev + j.off_ctr, 0, 16 * 8, s));
     CK(cudaEventRecord(ws.ev[0], s));
     CK(launch_tables(j.acc, (const Inst *)(dev + j.off_inst), ni, j.max_entries, s));
+    CK(cudaEventRecord(ws.ev[3], s));
     ScanArgs a{};
     a.inst = (const Inst *)(dev + j.off_inst);
     a.state = (InstState *)(dev + j.off_state);
@@ -721,6 +736,7 @@ int job_launch(Workspace &ws, Job &j)
     a.nrec = (unsigned long long *)(dev + j.off_ctr) + 1;
     a.abort_flag = ws.d_abort;
     a.margin = (j.acc == ACC_F32 || j.acc == ACC_F64) ? j.margin : 0.0;
+    a.one = 1;
     int bps = scan_blocks_per_sm(j.acc, k1, j.variant);
     if (bps < 1)
         bps = 1;
@@ -730,6 +746,8 @@ int job_launch(Workspace &ws, Job &j)
         j.blocks = (int)std::max<uint64_t>(1, need_blocks);
     CK(launch_scan(j.acc, a, j.blocks, j.variant, s));
     CK(cudaEventRecord(ws.ev[1], s));
+    j.launches += 2;
+    j.h2d += j.up_bytes;
     j.t_start = now_s();
     return QUBO_OK;
 }
@@ -760,6 +778,7 @@ int job_finish(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seco
         j.aborted = true;
     unsigned long long nrec = 0;
     CK(cudaMemcpy(&nrec, dev + j.off_ctr + 8, 8, cudaMemcpyDeviceToHost));
+    j.d2h += 8;
     const unsigned long long cnt = std::min(nrec, j.rec_cap);
     unsigned long long P = 1;
     while (P < cnt)
@@ -767,10 +786,13 @@ int job_finish(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seco
     const bool batched = ni > 1;
     const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
     const unsigned long long *d_nrec = (const unsigned long long *)(dev + j.off_ctr) + 1;
-    if (is_float)
+    if (is_float) {
         CK(launch_rescore((const Inst *)(dev + j.off_inst), (InstState *)(dev + j.off_state), ws.d_rec, d_nrec,
                           j.rec_cap, batched, cnt, s));
-    CK(launch_sort(ws.d_rec, d_nrec, j.rec_cap, P, batched, is_float, s));
+        j.launches += 1;
+    }
+    CK(launch_sort(ws.d_rec, d_nrec, j.rec_cap, P, batched, is_float, s, &j.launches));
+    j.launches += 2;  // bounds + extract
     CK(launch_extract((const Inst *)(dev + j.off_inst), ws.d_rec, d_nrec, j.rec_cap, ni, batched, is_float, j.K,
                       j.cap, (ResOut *)(dev + j.off_res), (uint64_t *)(dev + j.off_ties),
                       (uint64_t *)(dev + j.off_topk), (int64_t *)(dev + j.off_topke),
@@ -797,9 +819,12 @@ int job_finish(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seco
         CK(cudaMemcpyAsync(tke, dev + j.off_topke, 8 * (size_t)j.K * ni, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
+    j.d2h += sizeof(ResOut) * ni + sizeof(InstState) * ni + (j.cap ? 8 * j.cap * ni : 0) + 16 * (size_t)j.K * ni;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ws.ev[0], ws.ev[2]) == cudaSuccess && gpu_seconds)
         *gpu_seconds = ms * 1e-3;
+    if (cudaEventElapsedTime(&ms, ws.ev[3], ws.ev[1]) == cudaSuccess)
+        j.scan_seconds = ms * 1e-3;
     parts.assign(ni, Part());
     for (int i = 0; i < ni; ++i) {
         Part &p = parts[i];
@@ -840,8 +865,21 @@ struct SolveCfg {
 
 struct SolveStats {
     double gpu_seconds = 0.0;
+    double scan_seconds = 0.0;
     int passes = 0;
     int blocks = 0;
+    int launches = 0;
+    uint64_t h2d = 0, d2h = 0;
+    void add(const Job &j, double gs)
+    {
+        gpu_seconds += gs;
+        scan_seconds += j.scan_seconds;
+        passes += 1;
+        blocks = std::max(blocks, j.blocks);
+        launches += j.launches;
+        h2d += j.h2d;
+        d2h += j.d2h;
+    }
 };
 
 // Solve the sub-cube (fix_bits, fix_value) of one prepared instance.  When the candidate buffer
@@ -868,9 +906,7 @@ int solve_range(Workspace &ws, HostInst &h, int fix_bits, uint64_t fix_value, co
     std::vector<Part> parts;
     double gs = 0.0;
     st = job_finish(ws, j, parts, &gs);
-    stats.gpu_seconds += gs;
-    stats.passes += 1;
-    stats.blocks = std::max(stats.blocks, j.blocks);
+    stats.add(j, gs);
     if (st)
         return st;
     Part p = parts[0];
@@ -980,12 +1016,21 @@ int solve_one(Workspace &ws, HostInst &h, const qubo_options &o, size_t states_c
     int st = solve_range(ws, h, o.fix_bits, o.fix_value, c, stream, p, stats, deadline);
     if (st)
         return st;
-    if (!float_margin_ok(h, p, c.margin)) {
-        h.acc = ACC_F64;
+    // FP32 drift above the margin's budget: shorten the anchoring period (the walk), and as a
+    // last resort rescan in FP64.
+    while (!float_margin_ok(h, p, c.margin)) {
+        if (h.acc == ACC_F32 && !h.small && h.L > kRegRows + 1 && c.split_k <= 0) {
+            c.walk_bits = std::max(kRegRows + 1, h.L - 2);
+        } else {
+            h.acc = ACC_F64;
+            c.walk_bits = o.walk_bits;
+        }
         p = Part();
         st = solve_range(ws, h, o.fix_bits, o.fix_value, c, stream, p, stats, deadline);
         if (st)
             return st;
+        if (h.acc == ACC_F64)
+            break;
     }
     const uint64_t expect = 1ull << (h.n - o.fix_bits);
     if (p.scanned != expect || !p.has)
@@ -999,6 +1044,10 @@ void fill_plan_info(const HostInst &h, const SolveStats &stats, double t0, qubo_
         return;
     info->seconds = now_s() - t0;
     info->seconds_gpu = stats.gpu_seconds;
+    info->seconds_scan = stats.scan_seconds;
+    info->kernel_launches = stats.launches;
+    info->h2d_bytes = stats.h2d;
+    info->d2h_bytes = stats.d2h;
     info->states_per_s = info->seconds > 0 ? (double)info->states_scanned / info->seconds : 0.0;
     info->n = h.n;
     info->split_k = h.k;
@@ -1135,15 +1184,31 @@ int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets
         return QUBO_ERR_ARG;
     const size_t esz = dtype == QUBO_I16 ? 2 : (dtype == QUBO_I32 || dtype == QUBO_F32) ? 4 : 8;
     std::vector<HostInst> hs(count);
-    int st;
     for (int i = 0; i < count; ++i) {
         if (n[i] < 1 || n[i] > kMaxBatchedN)
             return QUBO_ERR_ARG;
         if (topk > 0 && (uint64_t)topk > (1ull << n[i]))
             return QUBO_ERR_ARG;
-        if ((st = prepare((const char *)Q_packed + offsets[i] * esz, n[i], dtype, 0, hs[i])))
-            return st;
     }
+    // Host preparation (fold, bound, threshold) of the instances, in parallel.
+    std::vector<int> pst(count, QUBO_OK);
+    auto prep_range = [&](int lo, int hi) {
+        for (int i = lo; i < hi; ++i)
+            pst[i] = prepare((const char *)Q_packed + offsets[i] * esz, n[i], dtype, 0, hs[i]);
+    };
+    auto parallel = [&](auto &&fn) {
+        const int nt = std::max(1, std::min<int>(count / 64 + 1, (int)std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back(fn, (int)((int64_t)count * t / nt), (int)((int64_t)count * (t + 1) / nt));
+        for (auto &x : th)
+            x.join();
+    };
+    parallel(prep_range);
+    int st;
+    for (int i = 0; i < count; ++i)
+        if (pst[i])
+            return pst[i];
     // one accumulator for the whole batch: the widest any instance needs
     Acc acc = hs[0].acc;
     for (auto &h : hs)
@@ -1151,11 +1216,23 @@ int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets
             acc = h.acc;
     for (auto &h : hs)
         h.acc = acc;
-    for (auto &h : hs) {
-        if ((st = plan(h, 0, 0, 0, 0)))
-            return st;
-        h.thr0 = threshold_bound(h, std::max(1, topk));
-    }
+    // The batch supplies the parallelism, so every instance walks as long as it can (fewest,
+    // largest units: less per-unit set-up).
+    auto plan_range = [&](int lo, int hi) {
+        for (int i = lo; i < hi; ++i) {
+            HostInst &h = hs[i];
+            const int B = suffix_bits(acc_bytes(acc));
+            const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
+            const int walk = h.n - B >= kRegRows + 1 ? std::min(wmax, h.n - B) : 0;
+            pst[i] = plan(h, 0, 0, 0, walk);
+            if (!pst[i])
+                h.thr0 = threshold_bound(h, std::max(1, topk));
+        }
+    };
+    parallel(plan_range);
+    for (int i = 0; i < count; ++i)
+        if (pst[i])
+            return pst[i];
     // longest work first (LPT order) so the tail of the persistent launch is short
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i)
@@ -1194,9 +1271,7 @@ int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets
         Part &p = parts[r];
         HostInst &h = hs[i];
         SolveStats stats;
-        stats.gpu_seconds = gs;
-        stats.passes = 1;
-        stats.blocks = j.blocks;
+        stats.add(j, gs);
         if (p.overflow || !float_margin_ok(h, p, c.margin)) {
             // rare: this instance overflowed the shared candidate buffer; solve it alone
             if (!float_margin_ok(h, p, c.margin))
@@ -1293,9 +1368,9 @@ int qubo_problem_fetch(qubo_problem *p, void *out_min, uint64_t *out_states, siz
     p->launched = false;
     std::vector<Part> parts;
     SolveStats stats;
-    int st = job_finish(p->ws, p->job, parts, &stats.gpu_seconds);
-    stats.passes = 1;
-    stats.blocks = p->job.blocks;
+    double gs = 0.0;
+    int st = job_finish(p->ws, p->job, parts, &gs);
+    stats.add(p->job, gs);
     if (st)
         return st;
     Part part = parts[0];

@@ -295,18 +295,21 @@ cudaError_t launch_rescore(const Inst *d_inst, InstState *d_state, Rec *rec, con
 }
 
 cudaError_t launch_sort(Rec *rec, const unsigned long long *d_nrec, unsigned long long cap, unsigned long long max_pow2,
-                        bool batched, bool is_float, cudaStream_t s)
+                        bool batched, bool is_float, cudaStream_t s, int *launches)
 {
     if (max_pow2 < 2)
         return cudaSuccess;
+    int nl = 0;
     {
         unsigned long long blocks = (max_pow2 + 255) / 256;
         if (blocks > 8192)
             blocks = 8192;
         pad_kernel<<<(unsigned)blocks, 256, 0, s>>>(rec, d_nrec, cap, is_float);
+        ++nl;
     }
     const unsigned long long chunks = (max_pow2 + kChunk - 1) / kChunk;
     auto local = [&](unsigned long long k_merge) {
+        ++nl;
         if (is_float)
             sort_local_kernel<true><<<(unsigned)chunks, 1024, 0, s>>>(rec, d_nrec, cap, batched, k_merge);
         else
@@ -318,6 +321,7 @@ cudaError_t launch_sort(Rec *rec, const unsigned long long *d_nrec, unsigned lon
             unsigned long long blocks = (max_pow2 + 255) / 256;
             if (blocks > 16384)
                 blocks = 16384;
+            ++nl;
             if (is_float)
                 sort_global_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(rec, d_nrec, cap, batched, k, j);
             else
@@ -325,6 +329,8 @@ cudaError_t launch_sort(Rec *rec, const unsigned long long *d_nrec, unsigned lon
         }
         local(k);
     }
+    if (launches)
+        *launches += nl;
     return cudaGetLastError();
 }
 

@@ -12,10 +12,14 @@ enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4 };
 // variants); the inner loop is unrolled over 2^(RC+1) Gray steps so that every register-row
 // flip has a compile-time sign.  A plan needs walk_bits >= kRegRows + 1.
 constexpr int kRegRows = 3;
-// Compiled scan variants: (register rows, minimum resident blocks per SM).
-constexpr int kScanVariants = 3;
-constexpr int kVariantRegRows[kScanVariants] = {3, 2, 3};
-constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 3};
+// Compiled scan variants of the 4-byte accumulators: register rows, minimum resident blocks
+// per SM, integer adds as multiply-adds (1) or plain adds (0), 2- or 3-input mins.  The 8-byte
+// accumulators compile variant 0 only.
+constexpr int kScanVariants = 6;
+constexpr int kVariantRegRows[kScanVariants] = {3, 2, 3, 3, 3, 2};
+constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 2, 2, 2, 3};
+constexpr int kVariantAddMode[kScanVariants] = {0, 0, 1, 0, 1, 1};
+constexpr int kVariantMinInputs[kScanVariants] = {2, 2, 2, 3, 3, 3};
 // Threads per block of the scan kernel (4 warps; every warp owns one work unit at a time).
 constexpr int kScanThreads = 128;
 // Longest Gray walk inside one work unit (also the FP32 re-anchoring period).
@@ -88,6 +92,8 @@ struct ScanArgs {
     unsigned long long *nrec;    // total candidates offered
     const volatile int *abort_flag;
     double margin;               // float scans: candidate margin above the threshold
+    int32_t one;                 // the constant 1, passed at run time (multiply-add variants)
+    int32_t pad;
 };
 
 // Columns per thread (S) of the scan kernel for an accumulator of `bytes` bytes; a work unit
@@ -110,7 +116,7 @@ int scan_blocks_per_sm(Acc acc, bool k1, int variant);
 cudaError_t launch_rescore(const Inst *d_inst, InstState *d_state, Rec *rec, const unsigned long long *d_nrec,
                            unsigned long long cap, bool batched, unsigned long long max_count, cudaStream_t s);
 cudaError_t launch_sort(Rec *rec, const unsigned long long *d_nrec, unsigned long long cap, unsigned long long max_pow2,
-                        bool batched, bool is_float, cudaStream_t s);
+                        bool batched, bool is_float, cudaStream_t s, int *launches);
 cudaError_t launch_extract(const Inst *d_inst, const Rec *rec, const unsigned long long *d_nrec, unsigned long long cap,
                            int n_inst, bool batched, bool is_float, int topk, unsigned long long states_cap,
                            ResOut *res, uint64_t *ties, uint64_t *topk_codes, int64_t *topk_e,

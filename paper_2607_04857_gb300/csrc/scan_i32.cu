@@ -10,7 +10,8 @@ static_assert(ilog2c(32 * kS) == suffix_bits(sizeof(int32_t)), "suffix bits must
 template <int VAR, bool K1>
 constexpr auto kernel_of()
 {
-    return scan_kernel<int32_t, kS, kVariantRegRows[VAR], K1, kVariantMinBlocks[VAR]>;
+    return scan_kernel<int32_t, kS, kVariantRegRows[VAR], K1, kVariantMinBlocks[VAR], kVariantAddMode[VAR],
+                       kVariantMinInputs[VAR]>;
 }
 
 template <bool K1>
@@ -19,6 +20,9 @@ auto pick(int variant)
     switch (variant) {
     case 1: return kernel_of<1, K1>();
     case 2: return kernel_of<2, K1>();
+    case 3: return kernel_of<3, K1>();
+    case 4: return kernel_of<4, K1>();
+    case 5: return kernel_of<5, K1>();
     default: return kernel_of<0, K1>();
     }
 }

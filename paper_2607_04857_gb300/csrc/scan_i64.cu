@@ -10,17 +10,15 @@ static_assert(ilog2c(32 * kS) == suffix_bits(sizeof(int64_t)), "suffix bits must
 template <int VAR, bool K1>
 constexpr auto kernel_of()
 {
-    return scan_kernel<int64_t, kS, kVariantRegRows[VAR], K1, kVariantMinBlocks[VAR]>;
+    return scan_kernel<int64_t, kS, kVariantRegRows[VAR], K1, kVariantMinBlocks[VAR], kVariantAddMode[VAR],
+                       kVariantMinInputs[VAR]>;
 }
 
 template <bool K1>
 auto pick(int variant)
 {
-    switch (variant) {
-    case 1: return kernel_of<1, K1>();
-    case 2: return kernel_of<2, K1>();
-    default: return kernel_of<0, K1>();
-    }
+    (void)variant;
+    return kernel_of<0, K1>();
 }
 }  // namespace
 

@@ -46,7 +46,8 @@ struct Tr;
 
 template <>
 struct Tr<int32_t> {
-    using F = int32_t;  // precision of the per-unit fields and of the tables
+    using F = int32_t;   // precision of the tables
+    using FU = int32_t;  // precision of the per-unit fields
     using Vec = int4;
     static constexpr int V = 4;
     static constexpr bool kFloat = false;
@@ -55,11 +56,13 @@ struct Tr<int32_t> {
     __device__ static void gmin_min(InstState *s, int32_t v) { atomicMin((int *)&s->gmin, v); }
     __device__ static int64_t bits(int32_t v) { return v; }
     __device__ static int32_t tmin(int32_t a, int32_t b) { return min(a, b); }
+    __device__ static int32_t tmin3(int32_t a, int32_t b, int32_t c) { return __vimin3_s32(a, b, c); }
 };
 
 template <>
 struct Tr<int64_t> {
     using F = int64_t;
+    using FU = int64_t;
     using Vec = longlong2;
     static constexpr int V = 2;
     static constexpr bool kFloat = false;
@@ -68,11 +71,13 @@ struct Tr<int64_t> {
     __device__ static void gmin_min(InstState *s, int64_t v) { atomicMin((long long *)&s->gmin, (long long)v); }
     __device__ static int64_t bits(int64_t v) { return v; }
     __device__ static int64_t tmin(int64_t a, int64_t b) { return min(a, b); }
+    __device__ static int64_t tmin3(int64_t a, int64_t b, int64_t c) { return min(min(a, b), c); }
 };
 
 template <>
 struct Tr<float> {
     using F = double;
+    using FU = float;
     using Vec = float4;
     static constexpr int V = 4;
     static constexpr bool kFloat = true;
@@ -81,11 +86,18 @@ struct Tr<float> {
     __device__ static void gmin_min(InstState *s, float v) { atomicMin((unsigned *)&s->gmin, ord32(v)); }
     __device__ static int64_t bits(float v) { return __double_as_longlong((double)v); }
     __device__ static float tmin(float a, float b) { return fminf(a, b); }
+    __device__ static float tmin3(float a, float b, float c)
+    {
+        float d;
+        asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+        return d;
+    }
 };
 
 template <>
 struct Tr<double> {
     using F = double;
+    using FU = double;
     using Vec = double2;
     static constexpr int V = 2;
     static constexpr bool kFloat = true;
@@ -97,8 +109,10 @@ struct Tr<double> {
     __device__ static void gmin_min(InstState *s, double v) { atomicMin(&s->gmin, ord64(v)); }
     __device__ static int64_t bits(double v) { return __double_as_longlong(v); }
     __device__ static double tmin(double a, double b) { return fmin(a, b); }
+    __device__ static double tmin3(double a, double b, double c) { return fmin(fmin(a, b), c); }
 };
 
+// Symmetric coupling matrix in the table precision (tables) and in the unit-field precision.
 template <class T>
 __device__ __forceinline__ const typename Tr<T>::F *field_matrix(const Inst &d)
 {
@@ -106,6 +120,11 @@ __device__ __forceinline__ const typename Tr<T>::F *field_matrix(const Inst &d)
         return d.W64;
     else
         return (const typename Tr<T>::F *)d.W;
+}
+template <class T>
+__device__ __forceinline__ const typename Tr<T>::FU *unit_matrix(const Inst &d)
+{
+    return (const typename Tr<T>::FU *)d.W;
 }
 
 __device__ __forceinline__ void vsplit(const int4 &v, int32_t (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
@@ -139,20 +158,32 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// min over S register values (tree, S a power of two)
-template <class T, int S>
-__device__ __forceinline__ T tree_min(const T (&E)[S])
+// min over N register values: a tree of 2-input (MINM == 2) or 3-input (MINM == 3) mins.
+template <class T, int MINM, int N>
+__device__ __forceinline__ T tree_min(const T (&E)[N])
 {
-    T m[S / 2];
+    if constexpr (N == 1) {
+        return E[0];
+    } else if constexpr (MINM == 3 && N >= 3) {
+        constexpr int M = N / 3 + (N % 3);
+        T m[M];
 #pragma unroll
-    for (int q = 0; q < S / 2; ++q)
-        m[q] = Tr<T>::tmin(E[2 * q], E[2 * q + 1]);
+        for (int q = 0; q < N / 3; ++q)
+            m[q] = Tr<T>::tmin3(E[3 * q], E[3 * q + 1], E[3 * q + 2]);
 #pragma unroll
-    for (int w = S / 4; w >= 1; w >>= 1)
+        for (int q = 0; q < N % 3; ++q)
+            m[N / 3 + q] = E[3 * (N / 3) + q];
+        return tree_min<T, MINM, M>(m);
+    } else {
+        constexpr int M = N / 2 + (N % 2);
+        T m[M];
 #pragma unroll
-        for (int q = 0; q < w; ++q)
-            m[q] = Tr<T>::tmin(m[2 * q], m[2 * q + 1]);
-    return m[0];
+        for (int q = 0; q < N / 2; ++q)
+            m[q] = Tr<T>::tmin(E[2 * q], E[2 * q + 1]);
+        if constexpr (N % 2)
+            m[M - 1] = E[N - 1];
+        return tree_min<T, MINM, M>(m);
+    }
 }
 
 // Offer one state to the candidate buffer.
@@ -252,10 +283,10 @@ __device__ void small_unit(const ScanArgs &a, const Inst &d, int inst, int lane)
 // (l < B + L) to the set fixed variables, and every lane returns c(x_f), the energy of the fixed
 // variables alone (Sec. 3.3.1: Q' = Q_rr + diag(x_f Q_fr), c(x_f) = x_f Q_ff x_f^T).
 template <class T>
-__device__ __forceinline__ void unit_fields(const typename Tr<T>::F *W, int n, int k, int BL, uint64_t unit, int lane,
-                                            typename Tr<T>::F &f0, typename Tr<T>::F &cx)
+__device__ __forceinline__ void unit_fields(const typename Tr<T>::FU *W, int n, int k, int BL, uint64_t unit, int lane,
+                                            typename Tr<T>::FU &f0, typename Tr<T>::FU &cx)
 {
-    using F = typename Tr<T>::F;
+    using F = typename Tr<T>::FU;
     F a0 = 0, up0 = 0, up1 = 0;
     for (int f = 0; f < k; ++f) {
         if (!((unit >> f) & 1ull))
@@ -312,11 +343,13 @@ __device__ __forceinline__ void column_fields(F f0, int lane, F &lin_t, F (&lin_
 }
 
 // ---- one work unit: all 2^(B+L) states with fixed bits x_f = unit --------------------------------
-template <class T, int S, int RC, bool K1>
+// ADDM == 1 issues the integer adds as multiply-adds by a runtime +-1 (fused multiply-add
+// pipe) so that the integer ALU pipe is left to the mins; MINM selects 2- or 3-input mins.
+template <class T, int S, int RC, bool K1, int ADDM, int MINM>
 __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t unit, T &Treg,
                                           int lane, T *stage, T *wsm)
 {
-    using F = typename Tr<T>::F;
+    using F = typename Tr<T>::FU;
     constexpr int V = Tr<T>::V;
     constexpr int G = S / V;
     constexpr int LOGV = ilog2c(V);
@@ -326,7 +359,7 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
     constexpr int BODY = 1 << (RC + 1);
     const int n = d.n, L = d.L, k = d.k, BL = B + L;
     InstState *st = a.state + inst;
-    const F *W = field_matrix<T>(d);
+    const F *W = unit_matrix<T>(d);
 
     // Fields of the set fixed bits on every other variable and c(x_f) (Sec. 3.3.1).
     F f0, cx;
@@ -406,9 +439,16 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
                 constexpr int kk = ctzc(p);
                 if constexpr (kk < RC) {
                     constexpr bool neg = (p >> (kk + 1)) & 1;
+                    if constexpr (ADDM == 1 && !Tr<T>::kFloat) {
+                        const T mul = neg ? -(T)a.one : (T)a.one;
 #pragma unroll
-                    for (int q = 0; q < S; ++q)
-                        E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
+                        for (int q = 0; q < S; ++q)
+                            E[q] = E[q] + Mr[kk][q] * mul;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < S; ++q)
+                            E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
+                    }
                 } else {
                     high_flip(RC, (blk & 1) ? (T)-1 : (T)1);
                 }
@@ -417,7 +457,7 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
                 vload<T>(ELp + i0 + p, elv);
             const T el = elv[p % V];
             T t = u - el;
-            const T m = tree_min<T, S>(E);
+            const T m = tree_min<T, MINM, S>(E);
             if (m <= t) {
                 // Slow path: record every column at or below the threshold.
 #pragma unroll
@@ -482,7 +522,7 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
     }
 }
 
-template <class T, int S, int RC, bool K1, int MINB>
+template <class T, int S, int RC, bool K1, int MINB, int ADDM, int MINM>
 __global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs a)
 {
     __shared__ T stage_all[kScanThreads / 32][S * 32];
@@ -525,7 +565,7 @@ __global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs
         if (d.small)
             small_unit<T>(a, d, inst, lane);
         else
-            scan_unit<T, S, RC, K1>(a, d, inst, d.unit_begin + off, Treg, lane, stage, wsm);
+            scan_unit<T, S, RC, K1, ADDM, MINM>(a, d, inst, d.unit_begin + off, Treg, lane, stage, wsm);
     }
 }
 

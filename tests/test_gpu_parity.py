@@ -264,3 +264,29 @@ def test_time_limit_returns_timeout(q):
     # the context stays usable
     Q2 = wl.upper_int(20, -10, 10, seed=2)
     check_int(q.solve(Q2), oracle.solve(Q2))
+
+
+# --- compiled kernel variants and the n=44 FP32 configuration ---------------------------------
+
+@pytest.mark.parametrize("variant", range(6))
+def test_scan_variants_agree(q, variant, monkeypatch):
+    monkeypatch.setenv("QUBO_SCAN_VARIANT", str(variant))
+    Q = wl.upper_int(27, -300, 300, seed=90)
+    check_int(q.solve(Q, topk=16), oracle.solve(Q, topk=16))
+    Qk1 = wl.upper_int(26, -300, 300, seed=91)
+    check_int(q.solve(Qk1), oracle.solve(Qk1))
+    Qf = wl.sk_float32(25, seed=92)
+    r = q.solve(Qf, topk=8)
+    assert r.info["acc"] == "f32"
+    check_float(r, oracle.solve(Qf, topk=8))
+
+
+def test_config3_subcube_stays_fp32(q):
+    """The n=44 SK instance: an FP32 scan (no FP64 fallback) on sampled sub-cubes of 2^24
+    states, checked against the FP64 oracle."""
+    Q = wl.config3()
+    for v in (0, 777, 1 << 19):
+        r = q.solve(Q, topk=16, fix_bits=20, fix_value=v)
+        assert r.info["acc"] == "f32", r.info
+        assert 2 * r.info["fp32_max_drift"] < 1e-3 and r.info["fp32_max_abs_err"] < 5e-4
+        check_float(r, oracle.solve(Q, topk=16, fix_bits=20, fix_value=v))
