@@ -190,6 +190,44 @@ typedef struct {
 int qubo_merge(const qubo_partial *a, const qubo_partial *b, size_t cap, int topk, qubo_partial *out);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Solving without allocating.                                                               */
+/* ---------------------------------------------------------------------------------------- */
+
+/*
+ * qubo_solve_noalloc has no counterpart in the paper.  It is for callers that must not allocate
+ * device memory when they ask for a solve: a process whose device memory is owned by its own
+ * pool allocator (a cudaMalloc behind its back would escape its accounting, or fail because the
+ * pool already holds the free memory), or a latency-sensitive caller that cannot accept the
+ * device-wide synchronisation and unbounded time that cudaMalloc and cudaFree may cost.
+ *
+ * Every byte of device scratch this call needs (tables, candidate records, counters) comes from
+ * one fixed array of QUBO_NOALLOC_SCRATCH_BYTES compiled into the library; each GPU that loads
+ * the library holds that array until the process exits.  The call itself allocates nothing, on
+ * the device or the host: no cudaMalloc, cudaFree, pinned buffers or heap.
+ *
+ *   Q_host      n x n row-major host matrix, QUBO_I16 or QUBO_I32 (same energy as qubo_solve).
+ *   out_min     host: the exact minimum energy.
+ *   out_states  host array of states_cap codes: the smallest min(n_ties, states_cap) tie codes in
+ *               ascending order (unused entries are set to 0).  May be NULL if states_cap == 0.
+ *   out_n_ties  host: the exact number of minimisers.
+ *   stream      cudaStream_t as void* (NULL = legacy default stream); the call waits for it.
+ * Limits: 1 <= n <= QUBO_NOALLOC_MAX_N, states_cap <= QUBO_NOALLOC_MAX_TIES, int32 energies
+ * (sum |U_ij| < 2^30), no K-lowest output.  Beyond them it returns QUBO_ERR_ARG
+ * (QUBO_ERR_OVERFLOW for the energy bound); an instance with more than 65536 states at or below
+ * the running minimum (massive ties) returns QUBO_ERR_NOMEM instead of results.
+ * The first call on each device performs a one-time set-up (it looks up the device address of
+ * the array); make that first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents; each call clears what must start at zero.  Calls that overlap
+ * on the GPU (concurrent streams, threads or processes sharing the context) race on the array:
+ * serialise them.  Returns QUBO_OK, QUBO_TRUNCATED or a negative qubo_status.
+ */
+#define QUBO_NOALLOC_SCRATCH_BYTES (2u << 20)
+#define QUBO_NOALLOC_MAX_N 40
+#define QUBO_NOALLOC_MAX_TIES 4096
+int qubo_solve_noalloc(const void *Q_host, int n, qubo_dtype dtype, int64_t *out_min, uint64_t *out_states,
+                       size_t states_cap, uint64_t *out_n_ties, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Utilities.                                                                                 */
 /* ---------------------------------------------------------------------------------------- */
 

@@ -30,8 +30,10 @@ MAX_TOPK = 1024
 EXPORTS = (
     "qubo_solve", "qubo_solve_ex", "qubo_solve_batched", "qubo_problem_create", "qubo_problem_run",
     "qubo_problem_fetch", "qubo_problem_destroy", "qubo_merge", "qubo_strerror", "qubo_abort",
-    "qubo_abort_clear", "qubo_device_sm_count", "qubo_version",
+    "qubo_abort_clear", "qubo_device_sm_count", "qubo_version", "qubo_solve_noalloc",
 )
+NOALLOC_MAX_N = 40
+NOALLOC_MAX_TIES = 4096
 
 
 class QuboError(RuntimeError):
@@ -99,13 +101,14 @@ def load_library(path: str = LIB_PATH):
     lib.qubo_problem_destroy.argtypes = [P]
     lib.qubo_problem_destroy.restype = None
     lib.qubo_merge.argtypes = [P, P, SZ, I, P]
+    lib.qubo_solve_noalloc.argtypes = [P, I, I, P, P, SZ, P, P]
     lib.qubo_strerror.argtypes = [I]
     lib.qubo_strerror.restype = ctypes.c_char_p
     lib.qubo_version.restype = ctypes.c_char_p
     lib.qubo_abort.restype = None
     lib.qubo_abort_clear.restype = None
     for name in ("qubo_solve", "qubo_solve_ex", "qubo_solve_batched", "qubo_problem_create", "qubo_problem_run",
-                 "qubo_problem_fetch", "qubo_merge", "qubo_device_sm_count"):
+                 "qubo_problem_fetch", "qubo_merge", "qubo_device_sm_count", "qubo_solve_noalloc"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -253,6 +256,24 @@ def solve_batched(Qs, topk: int = 0, states_cap: int = 64, stream=None) -> list[
                           tk[i * topk: i * topk + k].copy(), tkE[i * topk: i * topk + k].copy(),
                           QUBO_TRUNCATED if inf.n_ties > states_cap else QUBO_OK, inf.as_dict()))
     return out
+
+
+def solve_noalloc(Q, states_cap: int = 64, stream=None) -> Result:
+    """Minimum and tie set through qubo_solve_noalloc, which takes all its device scratch from a
+    fixed array inside the library and allocates nothing (for callers that must not allocate;
+    integer Q, n <= 40, states_cap <= 4096, no K lowest)."""
+    lib = load_library()
+    Qm, dt = as_qubo_matrix(Q)
+    if dt not in (QUBO_I16, QUBO_I32):
+        raise ValueError("solve_noalloc takes an integer Q")
+    n = Qm.shape[0]
+    mn = np.zeros(1, dtype=np.int64)
+    nt = np.zeros(1, dtype=np.uint64)
+    ties = np.zeros(max(states_cap, 1), dtype=np.uint64)
+    st = _check(lib.qubo_solve_noalloc(_ptr(Qm), n, dt, _ptr(mn), _ptr(ties) if states_cap else None, states_cap,
+                                       _ptr(nt), _stream_ptr(stream)), "qubo_solve_noalloc")
+    k = min(int(nt[0]), states_cap)
+    return Result(int(mn[0]), int(nt[0]), ties[:k].copy(), np.zeros(0, np.uint64), np.zeros(0, np.int64), st, {})
 
 
 class Problem:
