@@ -60,7 +60,7 @@ def make_workload(name: str, fix_bits: int | None):
                     unit="states/s", dtype="f32",
                     config={"workload": "n44_fp32_sk", "n": 44, "seed": 3, "margin": 1e-3,
                             "entries": "symmetric FP32, off-diagonal N(0,1)/sqrt(44), diagonal N(0,1)",
-                            "anchor": "every unit walk (<= 2^16 Gray steps)",
+                            "anchor": "re-anchored at every unit start: 2^10 Gray steps per walk",
                             "step": f"one sub-cube of 2^{44 - fb} states (top {fb} code bits fixed)"})
     if name == "batched":
         return dict(name=name, Qs=wl.config4(), topk=0, metric="instances/s (4096 QUBOs, n uniform in 16..32)",
@@ -411,7 +411,10 @@ def main():
     acc = "i32" if W["dtype"] == "int32" else "f32"
     prof = profile_counters(acc)
     if prof:
-        roof["traffic"] = prof.get("dram_bytes_per_launch_scaled")
+        # DRAM bytes per launch, scaled from the captured launch by the states it processed
+        roof["traffic"] = prof["dram_bytes_per_state"] * per_launch_states
+        roof["traffic_basis"] = (f"ncu capture of {prof['captured_states']} states scaled to "
+                                 f"{per_launch_states} states per launch")
         if prof.get("inst_per_state") and clocks:
             ips = prof["inst_per_state"]
             issue = sms * LANES_PER_SM * clocks["sm_mhz"] * 1e6 / ips

@@ -25,9 +25,10 @@ constexpr unsigned long long kDefaultRecCap = 1ull << 22;  // candidate records 
 constexpr double kDefaultMargin = 1e-3;
 constexpr int kTargetUnitsLog2 = 15;   // aim for >= 2^15 work units per scan
 constexpr int kDefaultMaxWalkBits = 12;
-// FP32 scans re-anchor at every unit start, so the walk length is the anchoring period: 2^8
-// Gray steps keep the measured drift far below the default 1e-3 candidate margin.
-constexpr int kFloatMaxWalkBits = 8;
+// FP32 scans re-anchor at every unit start, so the walk length is the anchoring period: 2^10
+// Gray steps keep the measured drift (2.4e-4 on the n=44 SK instance) well inside the budget
+// of the default 1e-3 candidate margin; the drift guard shortens it when it does not.
+constexpr int kFloatMaxWalkBits = 10;
 
 double now_s()
 {
@@ -46,6 +47,7 @@ struct HostInst {
     std::vector<double> Uf;   // folded upper-triangular (float Q), FP64
     double beta = 0.0;        // sum |U_ij|
     // plan of the current run
+    int variant = 0;  // compiled scan variant (fixes the columns per thread)
     int B = 0, L = 0, k = 0, small = 0;
     int fix_bits = 0;
     uint64_t fix_value = 0;
@@ -118,7 +120,7 @@ int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bi
     if (free_bits > 63)
         return QUBO_ERR_ARG;
     h.states = 1ull << free_bits;
-    h.B = suffix_bits(acc_bytes(h.acc));
+    h.B = suffix_bits(acc_bytes(h.acc), h.variant);
     if (free_bits < h.B + kRegRows + 1) {
         h.small = 1;
         h.L = h.k = 0;
@@ -522,13 +524,16 @@ unsigned long long record_capacity()
     return kDefaultRecCap;
 }
 
-int scan_variant()
+// Compiled scan variant: QUBO_SCAN_VARIANT overrides the measured default of the accumulator.
+int scan_variant(Acc acc = ACC_I32)
 {
     const char *v = std::getenv("QUBO_SCAN_VARIANT");
-    if (!v)
-        return 0;
-    const int x = std::atoi(v);
-    return (x >= 0 && x < kScanVariants) ? x : 0;
+    if (v) {
+        const int x = std::atoi(v);
+        if (x >= 0 && x < kScanVariants)
+            return x;
+    }
+    return acc == ACC_F32 ? kDefaultVariantF32 : kDefaultVariantI32;
 }
 
 #define CK(call)                                                                                   \
@@ -737,6 +742,7 @@ int job_launch(Workspace &ws, Job &j)
     a.abort_flag = ws.d_abort;
     a.margin = (j.acc == ACC_F32 || j.acc == ACC_F64) ? j.margin : 0.0;
     a.one = 1;
+    a.zero = 0;
     int bps = scan_blocks_per_sm(j.acc, k1, j.variant);
     if (bps < 1)
         bps = 1;
@@ -888,6 +894,7 @@ struct SolveStats {
 int solve_range(Workspace &ws, HostInst &h, int fix_bits, uint64_t fix_value, const SolveCfg &c,
                 cudaStream_t stream, Part &out, SolveStats &stats, double t_deadline)
 {
+    h.variant = acc_bytes(h.acc) == 4 ? c.variant : 0;
     int st = plan(h, fix_bits, fix_value, c.split_k, c.walk_bits);
     if (st)
         return st;
@@ -1011,7 +1018,7 @@ int solve_one(Workspace &ws, HostInst &h, const qubo_options &o, size_t states_c
     c.time_limit = o.time_limit_s;
     c.split_k = o.split_k;
     c.walk_bits = o.walk_bits;
-    c.variant = scan_variant();
+    c.variant = scan_variant(h.acc);
     const double deadline = o.time_limit_s > 0 ? now_s() + o.time_limit_s : 0.0;
     int st = solve_range(ws, h, o.fix_bits, o.fix_value, c, stream, p, stats, deadline);
     if (st)
@@ -1053,7 +1060,7 @@ void fill_plan_info(const HostInst &h, const SolveStats &stats, double t0, qubo_
     info->split_k = h.k;
     info->walk_bits = h.L;
     info->suffix_bits = h.small ? 0 : h.B;
-    info->cols_per_thread = h.small ? 0 : cols_per_thread(acc_bytes(h.acc));
+    info->cols_per_thread = h.small ? 0 : cols_per_thread(acc_bytes(h.acc), h.variant);
     info->threads = kScanThreads;
     info->blocks = stats.blocks;
     info->passes = stats.passes;
@@ -1218,10 +1225,12 @@ int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets
         h.acc = acc;
     // The batch supplies the parallelism, so every instance walks as long as it can (fewest,
     // largest units: less per-unit set-up).
+    const int variant = scan_variant(acc);
     auto plan_range = [&](int lo, int hi) {
         for (int i = lo; i < hi; ++i) {
             HostInst &h = hs[i];
-            const int B = suffix_bits(acc_bytes(acc));
+            h.variant = acc_bytes(acc) == 4 ? variant : 0;
+            const int B = suffix_bits(acc_bytes(acc), h.variant);
             const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
             const int walk = h.n - B >= kRegRows + 1 ? std::min(wmax, h.n - B) : 0;
             pst[i] = plan(h, 0, 0, 0, walk);
@@ -1253,7 +1262,7 @@ int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets
     j.K = topk;
     j.cap = states_cap_per_inst;
     j.margin = kDefaultMargin;
-    j.variant = scan_variant();
+    j.variant = variant;
     j.stream = (cudaStream_t)stream;
     if ((st = job_launch(*ws, j)))
         return st;
@@ -1339,6 +1348,7 @@ int qubo_problem_run(qubo_problem *p, int fix_bits, uint64_t fix_value, void *st
     p->fix_bits = fix_bits;
     p->fix_value = fix_value;
     p->stream = (cudaStream_t)stream;
+    p->h.variant = acc_bytes(p->h.acc) == 4 ? scan_variant(p->h.acc) : 0;
     int st = plan(p->h, fix_bits, fix_value, p->opt.split_k, p->opt.walk_bits);
     if (st)
         return st;
@@ -1350,7 +1360,7 @@ int qubo_problem_run(qubo_problem *p, int fix_bits, uint64_t fix_value, void *st
     p->job.cap = 1 << 16;
     p->job.margin = p->opt.margin > 0 ? p->opt.margin : kDefaultMargin;
     p->job.time_limit = p->opt.time_limit_s;
-    p->job.variant = scan_variant();
+    p->job.variant = p->h.variant;
     p->job.stream = p->stream;
     st = job_launch(p->ws, p->job);
     p->launched = st == QUBO_OK;

@@ -12,14 +12,20 @@ enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4 };
 // variants); the inner loop is unrolled over 2^(RC+1) Gray steps so that every register-row
 // flip has a compile-time sign.  A plan needs walk_bits >= kRegRows + 1.
 constexpr int kRegRows = 3;
-// Compiled scan variants of the 4-byte accumulators: register rows, minimum resident blocks
-// per SM, integer adds as multiply-adds (1) or plain adds (0), 2- or 3-input mins.  The 8-byte
-// accumulators compile variant 0 only.
-constexpr int kScanVariants = 6;
-constexpr int kVariantRegRows[kScanVariants] = {3, 2, 3, 3, 3, 2};
-constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 2, 2, 2, 3};
-constexpr int kVariantAddMode[kScanVariants] = {0, 0, 1, 0, 1, 1};
-constexpr int kVariantMinInputs[kScanVariants] = {2, 2, 2, 3, 3, 3};
+// Compiled scan variants of the 4-byte accumulators: columns per thread S, register rows,
+// minimum resident blocks per SM, how integer adds are issued (0: compiler's choice, 1: all as
+// multiply-adds by a runtime 1 on the FMA pipe, 2: a quarter as 3-input adds with a runtime 0 on
+// the ALU pipe and the rest as multiply-adds), 2- or 3-input mins.  The 8-byte accumulators
+// compile one variant: S = 16 with variant 0's register rows, blocks and min inputs.
+constexpr int kScanVariants = 8;
+constexpr int kVariantCols[kScanVariants] = {32, 32, 32, 16, 16, 32, 32, 16};
+constexpr int kVariantRegRows[kScanVariants] = {3, 2, 2, 3, 3, 2, 3, 2};
+constexpr int kVariantMinBlocks[kScanVariants] = {2, 2, 2, 3, 3, 3, 2, 3};
+constexpr int kVariantAddMode[kScanVariants] = {0, 0, 2, 0, 2, 0, 0, 0};
+constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 2, 3};
+// Default variant per 4-byte accumulator (measured on GB300; see the profiles).
+constexpr int kDefaultVariantI32 = 3;
+constexpr int kDefaultVariantF32 = 0;
 // Threads per block of the scan kernel (4 warps; every warp owns one work unit at a time).
 constexpr int kScanThreads = 128;
 // Longest Gray walk inside one work unit (also the FP32 re-anchoring period).
@@ -93,13 +99,19 @@ struct ScanArgs {
     const volatile int *abort_flag;
     double margin;               // float scans: candidate margin above the threshold
     int32_t one;                 // the constant 1, passed at run time (multiply-add variants)
-    int32_t pad;
+    int32_t zero;                // the constant 0, passed at run time (3-input-add variants)
 };
 
-// Columns per thread (S) of the scan kernel for an accumulator of `bytes` bytes; a work unit
-// covers 32*S columns, so the suffix has log2(32*S) bits.
-constexpr int cols_per_thread(int bytes) { return bytes == 4 ? 32 : 16; }
-constexpr int suffix_bits(int bytes) { return bytes == 4 ? 10 : 9; }
+// Columns per thread (S) of the scan kernel for an accumulator of `bytes` bytes and a variant;
+// a work unit covers 32*S columns, so the suffix has log2(32*S) bits.
+constexpr int cols_per_thread(int bytes, int variant = 0)
+{
+    return bytes == 4 ? kVariantCols[(variant >= 0 && variant < kScanVariants) ? variant : 0] : 16;
+}
+constexpr int suffix_bits(int bytes, int variant = 0)
+{
+    return cols_per_thread(bytes, variant) == 32 ? 10 : 9;
+}
 
 // ---- launchers (scan_*.cu, one translation unit per accumulator type) -------------------------
 template <class T>

@@ -17,7 +17,7 @@ namespace {
 
 constexpr size_t kScratchBytes = 2u << 20;  // QUBO_NOALLOC_SCRATCH_BYTES
 constexpr unsigned long long kRecords = 1ull << 16;  // candidate records (a power of two)
-constexpr int kB = suffix_bits(4);           // int32 accumulator: 10 suffix bits
+constexpr int kB = suffix_bits(4, 0);        // int32 accumulator, scan variant 0: 10 suffix bits
 constexpr int kMaxWalk = 12;
 
 static_assert(QUBO_NOALLOC_SCRATCH_BYTES == kScratchBytes, "header and implementation must agree");
@@ -261,6 +261,7 @@ extern "C" int qubo_solve_noalloc(const void *Q_host, int n, qubo_dtype dtype, i
     a.abort_flag = (const volatile int *)(base + lo.abort);
     a.margin = 0.0;
     a.one = 1;
+    a.zero = 0;
     int sms = 0;
     NA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int bps = scan_blocks_per_sm(ACC_I32, true, 0);

@@ -4,12 +4,11 @@
 namespace qubo {
 
 namespace {
-constexpr int kS = cols_per_thread(sizeof(float));
-static_assert(ilog2c(32 * kS) == suffix_bits(sizeof(float)), "suffix bits must match the column layout");
-
 template <int VAR, bool K1>
 constexpr auto kernel_of()
 {
+    constexpr int kS = cols_per_thread(sizeof(float), VAR);
+    static_assert(ilog2c(32 * kS) == suffix_bits(sizeof(float), VAR), "suffix bits must match the column layout");
     return scan_kernel<float, kS, kVariantRegRows[VAR], K1, kVariantMinBlocks[VAR], kVariantAddMode[VAR],
                        kVariantMinInputs[VAR]>;
 }
@@ -23,6 +22,8 @@ auto pick(int variant)
     case 3: return kernel_of<3, K1>();
     case 4: return kernel_of<4, K1>();
     case 5: return kernel_of<5, K1>();
+    case 6: return kernel_of<6, K1>();
+    case 7: return kernel_of<7, K1>();
     default: return kernel_of<0, K1>();
     }
 }

@@ -4,12 +4,11 @@
 namespace qubo {
 
 namespace {
-constexpr int kS = cols_per_thread(sizeof(double));
-static_assert(ilog2c(32 * kS) == suffix_bits(sizeof(double)), "suffix bits must match the column layout");
-
 template <int VAR, bool K1>
 constexpr auto kernel_of()
 {
+    constexpr int kS = cols_per_thread(sizeof(double), VAR);
+    static_assert(ilog2c(32 * kS) == suffix_bits(sizeof(double), VAR), "suffix bits must match the column layout");
     return scan_kernel<double, kS, kVariantRegRows[VAR], K1, kVariantMinBlocks[VAR], kVariantAddMode[VAR],
                        kVariantMinInputs[VAR]>;
 }

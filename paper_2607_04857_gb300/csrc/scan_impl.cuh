@@ -433,6 +433,10 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
     for (int blk = 0; blk < nblk; ++blk) {
         const int i0 = blk * BODY;
         T elv[V];
+        bool hit = false;
+        T Pmid = P;
+        // Fast path: per step one add per column, a min over the columns and one compare whose
+        // outcome is only OR-ed into `hit`, so consecutive steps can overlap freely.
         static_for<BODY>([&](auto pc) {
             constexpr int p = decltype(pc)::value;
             if constexpr (p > 0) {
@@ -444,45 +448,84 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
 #pragma unroll
                         for (int q = 0; q < S; ++q)
                             E[q] = E[q] + Mr[kk][q] * mul;
+                    } else if constexpr (ADDM == 2 && !Tr<T>::kFloat) {
+                        const T mul = neg ? -(T)a.one : (T)a.one;
+                        const T z = (T)a.zero;
+#pragma unroll
+                        for (int q = 0; q < S; ++q) {
+                            if (q % 4 == 0)
+                                E[q] = neg ? (E[q] - Mr[kk][q]) + z : (E[q] + Mr[kk][q]) + z;
+                            else
+                                E[q] = E[q] + Mr[kk][q] * mul;
+                        }
                     } else {
 #pragma unroll
                         for (int q = 0; q < S; ++q)
                             E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
                     }
                 } else {
+                    Pmid = P;
                     high_flip(RC, (blk & 1) ? (T)-1 : (T)1);
                 }
             }
             if constexpr (p % V == 0)
                 vload<T>(ELp + i0 + p, elv);
-            const T el = elv[p % V];
-            T t = u - el;
-            const T m = tree_min<T, MINM, S>(E);
-            if (m <= t) {
-                // Slow path: record every column at or below the threshold.
-#pragma unroll
-                for (int q = 0; q < S; ++q)
-                    stage[q * 32 + lane] = E[q];
+            const T t = u - elv[p % V];
+            hit |= tree_min<T, MINM, S>(E) <= t;
+        });
+        if (hit) {
+            // Slow path (rare): rebuild every step of this body from the body-end registers and
+            // record each column at or below the threshold.  Step p differs from the last step
+            // by the register rows and row RC whose Gray bits differ.
+            const int iend = i0 + BODY - 1;
+            const int gend = iend ^ (iend >> 1);
+            const T *rowRC = Mt + (size_t)RC * NB;
+#pragma unroll 1
+            for (int p = 0; p < BODY; ++p) {
                 const int i = i0 + p;
-                const uint64_t cb = cbase | ((uint64_t)(i ^ (i >> 1)) << B);
-                const T Ep = P + el;
+                const int gp = i ^ (i >> 1);
+                T sr[RC];
+#pragma unroll
+                for (int r = 0; r < RC; ++r)
+                    sr[r] = (T)(((gp >> r) & 1) - ((gend >> r) & 1));
+                const int dRC = ((gp >> RC) & 1) - ((gend >> RC) & 1);
+                const T sRC = (T)dRC;
+                const T Pp = dRC == 0 ? P : Pmid;
+                const T elp = ELp[i];
+                T tp = (Treg + mu - Pp) - elp;
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    T mv[V];
+                    vload<T>(rowRC + (g * 32 + lane) * V, mv);
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const int q = g * V + e;
+                        T ev = E[q];
+#pragma unroll
+                        for (int r = 0; r < RC; ++r)
+                            ev = ev + sr[r] * Mr[r][q];
+                        stage[q * 32 + lane] = ev + sRC * mv[e];
+                    }
+                }
+                const uint64_t cb = cbase | ((uint64_t)gp << B);
+                const T Ep = Pp + elp;
 #pragma unroll 1
                 for (int q = 0; q < S; ++q) {
                     const T ev = stage[q * 32 + lane];
-                    if (ev <= t) {
+                    if (ev <= tp) {
                         const T Et = ev + Ep;
                         const uint32_t j = (uint32_t)(((q / V) * 32 + lane) * V + (q % V));
                         record<T>(a, inst, Et, cb | j);
                         if (K1 && Et < Treg) {
                             Treg = Et;
-                            u = Treg + mu - P;
-                            t = u - el;
+                            tp = (Treg + mu - Pp) - elp;
                             Tr<T>::thr_min(st, Et);
                         }
                     }
                 }
             }
-        });
+            u = Treg + mu - P;
+        }
         if (blk + 1 < nblk) {
             const int ip = (blk + 1) * BODY;
             const int kk = __ffs(ip) - 1;
