@@ -341,8 +341,7 @@ def main():
         e2e_note = "qubo_solve_batched from host buffers (copies inside every step)"
     else:
         Q, n, topk, fb = W["Q"], W["n"], W["topk"], W["fix_bits"]
-        nsub = 1 << fb
-        my = [v for v in range(nsub) if v % world == rank]
+        my = q.shard_subcubes(fb, world, rank)
 
         def sub(s):
             return my[s % len(my)]

@@ -318,6 +318,20 @@ class Problem:
         self.close()
 
 
+def shard_subcubes(fix_bits: int, world: int, rank: int) -> list[int]:
+    """Sub-cubes (values of the top fix_bits code bits) scanned by `rank` of `world` ranks: a
+    round-robin split of the 2^fix_bits independent parts (Sec. 3.3.1)."""
+    return [v for v in range(1 << fix_bits) if v % world == rank]
+
+
+def merge_all(results, states_cap: int, topk: int) -> Result:
+    """Fold qubo_merge over results of disjoint state sets."""
+    acc = None
+    for r in results:
+        acc = r if acc is None else merge(acc, r, states_cap, topk)
+    return acc
+
+
 def merge(a: Result, b: Result, states_cap: int, topk: int) -> Result:
     """Merge the results of two disjoint state sets (qubo_merge)."""
     lib = load_library()

@@ -1,0 +1,58 @@
+"""Write the stored expected results of the benchmark configurations, using only the CPU oracle.
+
+    python tests/golden/make_golden.py cfg2      # n=36 int32, min + ties + 16 lowest (~2 min, 8 cores)
+    python tests/golden/make_golden.py cfg4      # 4096 batched instances (~1 h, 8 cores)
+
+The inputs come from the seeded generators in paper_2607_04857_gb300/workloads.py; the paper's
+benchmark matrices are uniformly random (Sec. 5.3), so the instances are synthetic stand-ins of
+the stated shapes.  Every value written here is computed by oracle/ (Gray-walk exhaustive search
+with the direct evaluator defining float energies); nothing comes from the CUDA path.
+"""
+from __future__ import annotations
+
+import json
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+from paper_2607_04857_gb300 import workloads as wl  # noqa: E402
+
+
+def cfg2():
+    Q = wl.config2()
+    t = time.time()
+    r = oracle.solve(Q, method=oracle.GRAY, topk=16, cap=1 << 16)
+    out = {"config": 2, "generator": "workloads.config2()", "n": 36, "seed": 2, "oracle": "gray",
+           "seconds": round(time.time() - t, 1), "min": r.min, "n_ties": r.n_ties,
+           "ties": [int(c) for c in r.ties], "topk": [int(c) for c in r.topk],
+           "topk_E": [int(e) for e in r.topk_E]}
+    with open(os.path.join(HERE, "cfg2_n36_top16.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
+def cfg4():
+    insts = wl.config4()
+    rows = []
+    t = time.time()
+    for i, Q in enumerate(insts):
+        r = oracle.solve(Q.astype(np.int32), method=oracle.GRAY, cap=64)
+        rows.append({"i": i, "n": int(Q.shape[0]), "min": r.min, "n_ties": r.n_ties,
+                     "ties": [int(c) for c in r.ties]})
+        if i % 256 == 0:
+            print(f"{i} {time.time() - t:.0f}s", file=sys.stderr, flush=True)
+    out = {"config": 4, "generator": "workloads.config4()", "count": len(insts), "seed": 4, "oracle": "gray",
+           "cap": 64, "seconds": round(time.time() - t, 1), "instances": rows}
+    with open(os.path.join(HERE, "cfg4_batched.json"), "w") as fh:
+        json.dump(out, fh, separators=(",", ":"))
+
+
+if __name__ == "__main__":
+    for what in sys.argv[1:]:
+        {"cfg2": cfg2, "cfg4": cfg4}[what]()
