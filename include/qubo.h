@@ -145,6 +145,30 @@ int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets
                        qubo_result *info, void *stream);
 
 /* ---------------------------------------------------------------------------------------- */
+/* Device-resident batches, replayed as one CUDA graph.                                      */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct qubo_batch qubo_batch;
+
+/* Prepare a batch (same inputs as qubo_solve_batched: fold, bound, plan, thresholds on the
+ * host), upload it once, and capture the whole device sequence (table build, one persistent
+ * scan over every (instance, unit) item in longest-first order, FP64 rescoring for floats,
+ * candidate sort, extraction, result download into pinned memory) as one CUDA graph.  The
+ * batch owns its device memory until qubo_batch_destroy. */
+int qubo_batch_create(const void *Q_packed, const int *n, const size_t *offsets, int count, qubo_dtype dtype,
+                      int topk, size_t states_cap_per_inst, qubo_batch **out);
+
+/* Replay the graph on `stream`; returns without waiting. */
+int qubo_batch_run(qubo_batch *b, void *stream);
+
+/* Wait for the last run and write the per-instance results (same layout as qubo_solve_batched).
+ * An instance whose candidates overflowed the buffer is solved again on its own. */
+int qubo_batch_fetch(qubo_batch *b, void *out_min, uint64_t *out_states, uint64_t *out_topk, void *out_topk_E,
+                     qubo_result *info);
+
+void qubo_batch_destroy(qubo_batch *b);
+
+/* ---------------------------------------------------------------------------------------- */
 /* Device-resident problems: upload once, run many times (sub-cube by sub-cube), fetch.       */
 /* ---------------------------------------------------------------------------------------- */
 
@@ -226,6 +250,34 @@ int qubo_merge(const qubo_partial *a, const qubo_partial *b, size_t cap, int top
 #define QUBO_NOALLOC_MAX_TIES 4096
 int qubo_solve_noalloc(const void *Q_host, int n, qubo_dtype dtype, int64_t *out_min, uint64_t *out_states,
                        size_t states_cap, uint64_t *out_n_ties, void *stream);
+
+/* ---------------------------------------------------------------------------------------- */
+/* Autotuning (the paper's launch configuration was found empirically, Sec. 4.2.8 and 6.2;    */
+/* these calls do that search on the running GPU).                                           */
+/* ---------------------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t variant;        /* compiled scan variant (columns per thread, register rows, blocks/SM, mins) */
+    int32_t walk_bits;      /* Gray-walked prefix bits per work unit (0 for batches: per instance) */
+    double states_per_s;    /* scan-kernel rate of the winning trial */
+    int32_t trials;         /* plans timed */
+    int32_t reserved;
+} qubo_plan;
+
+/* Time every compiled kernel variant and walk lengths around the default on sub-cubes of Q_host
+ * (top fix_bits code bits fixed, two values, each trial run twice) and install the fastest plan
+ * for (current device, accumulator, n): later solves of that size that set neither split_k nor
+ * walk_bits use it.  *best receives the winner.  QUBO_SCAN_VARIANT, when set, overrides any
+ * installed plan. */
+int qubo_autotune(const void *Q_host, int n, qubo_dtype dtype, int fix_bits, qubo_plan *best);
+
+/* Time every compiled variant on a whole batch (inputs as qubo_solve_batched) and install the
+ * fastest for later batches of this accumulator on the current device. */
+int qubo_autotune_batched(const void *Q_packed, const int *n, const size_t *offsets, int count, qubo_dtype dtype,
+                          qubo_plan *best);
+
+/* Forget every installed plan. */
+void qubo_autotune_clear(void);
 
 /* ---------------------------------------------------------------------------------------- */
 /* Utilities.                                                                                 */

@@ -31,6 +31,8 @@ EXPORTS = (
     "qubo_solve", "qubo_solve_ex", "qubo_solve_batched", "qubo_problem_create", "qubo_problem_run",
     "qubo_problem_fetch", "qubo_problem_destroy", "qubo_merge", "qubo_strerror", "qubo_abort",
     "qubo_abort_clear", "qubo_device_sm_count", "qubo_version", "qubo_solve_noalloc",
+    "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_batch_destroy",
+    "qubo_autotune", "qubo_autotune_batched", "qubo_autotune_clear",
 )
 NOALLOC_MAX_N = 40
 NOALLOC_MAX_TIES = 4096
@@ -71,6 +73,11 @@ class ResultInfo(ctypes.Structure):
         return d
 
 
+class Plan(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("walk_bits", ctypes.c_int32), ("states_per_s", ctypes.c_double),
+                ("trials", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class Partial(ctypes.Structure):
     _fields_ = [
         ("is_float", ctypes.c_int32), ("n_topk", ctypes.c_int32), ("min_i", ctypes.c_int64),
@@ -102,13 +109,23 @@ def load_library(path: str = LIB_PATH):
     lib.qubo_problem_destroy.restype = None
     lib.qubo_merge.argtypes = [P, P, SZ, I, P]
     lib.qubo_solve_noalloc.argtypes = [P, I, I, P, P, SZ, P, P]
+    lib.qubo_batch_create.argtypes = [P, P, P, I, I, I, SZ, P]
+    lib.qubo_batch_run.argtypes = [P, P]
+    lib.qubo_batch_fetch.argtypes = [P, P, P, P, P, P]
+    lib.qubo_batch_destroy.argtypes = [P]
+    lib.qubo_batch_destroy.restype = None
+    lib.qubo_autotune.argtypes = [P, I, I, I, P]
+    lib.qubo_autotune_batched.argtypes = [P, P, P, I, I, P]
+    lib.qubo_autotune_clear.restype = None
     lib.qubo_strerror.argtypes = [I]
     lib.qubo_strerror.restype = ctypes.c_char_p
     lib.qubo_version.restype = ctypes.c_char_p
     lib.qubo_abort.restype = None
     lib.qubo_abort_clear.restype = None
     for name in ("qubo_solve", "qubo_solve_ex", "qubo_solve_batched", "qubo_problem_create", "qubo_problem_run",
-                 "qubo_problem_fetch", "qubo_merge", "qubo_device_sm_count", "qubo_solve_noalloc"):
+                 "qubo_problem_fetch", "qubo_merge", "qubo_device_sm_count", "qubo_solve_noalloc",
+                 "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_autotune",
+                 "qubo_autotune_batched"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -223,10 +240,7 @@ def solve(Q, topk: int = 0, states_cap: int = 1 << 16, split_k: int = 0, walk_bi
                   tkE[:k].copy(), st, info.as_dict())
 
 
-def solve_batched(Qs, topk: int = 0, states_cap: int = 64, stream=None) -> list[Result]:
-    """Solve many instances in one persistent launch (qubo_solve_batched).  All matrices must
-    share one dtype."""
-    lib = load_library()
+def _pack(Qs):
     mats = [as_qubo_matrix(Q) for Q in Qs]
     dts = {d for _, d in mats}
     if len(dts) != 1:
@@ -236,17 +250,17 @@ def solve_batched(Qs, topk: int = 0, states_cap: int = 64, stream=None) -> list[
     offs = np.zeros(len(mats), dtype=np.uint64)
     offs[1:] = np.cumsum(ns[:-1].astype(np.uint64) ** 2)
     packed = np.concatenate([m.ravel() for m, _ in mats])
-    count = len(mats)
+    return packed, ns, offs, dt
+
+
+def _batch_outputs(count, dt, topk, states_cap):
+    edt = np.float64 if dt in (QUBO_F32, QUBO_F64) else np.int64
+    return (np.zeros(count, dtype=edt), np.zeros(count * states_cap, dtype=np.uint64),
+            np.zeros(count * topk, dtype=np.uint64), np.zeros(count * topk, dtype=edt), (ResultInfo * count)())
+
+
+def _batch_results(count, dt, topk, states_cap, mn, ties, tk, tkE, infos):
     isf = dt in (QUBO_F32, QUBO_F64)
-    edt = np.float64 if isf else np.int64
-    mn = np.zeros(count, dtype=edt)
-    ties = np.zeros(count * states_cap, dtype=np.uint64)
-    tk = np.zeros(count * topk, dtype=np.uint64)
-    tkE = np.zeros(count * topk, dtype=edt)
-    infos = (ResultInfo * count)()
-    st = lib.qubo_solve_batched(_ptr(packed), _ptr(ns), _ptr(offs), count, dt, topk, _ptr(mn), _ptr(ties),
-                                states_cap, _ptr(tk), _ptr(tkE), infos, _stream_ptr(stream))
-    _check(st, "qubo_solve_batched")
     out = []
     for i in range(count):
         inf = infos[i]
@@ -256,6 +270,74 @@ def solve_batched(Qs, topk: int = 0, states_cap: int = 64, stream=None) -> list[
                           tk[i * topk: i * topk + k].copy(), tkE[i * topk: i * topk + k].copy(),
                           QUBO_TRUNCATED if inf.n_ties > states_cap else QUBO_OK, inf.as_dict()))
     return out
+
+
+def autotune(Q, fix_bits: int) -> dict:
+    """Time the compiled variants and walk lengths on sub-cubes of Q (top fix_bits fixed) and
+    install the fastest plan for this size (qubo_autotune)."""
+    lib = load_library()
+    Qm, dt = as_qubo_matrix(Q)
+    p = Plan()
+    _check(lib.qubo_autotune(_ptr(Qm), Qm.shape[0], dt, fix_bits, ctypes.byref(p)), "qubo_autotune")
+    return {"variant": p.variant, "walk_bits": p.walk_bits, "states_per_s": p.states_per_s, "trials": p.trials}
+
+
+def autotune_batched(Qs) -> dict:
+    """Time the compiled variants on a whole batch and install the fastest (qubo_autotune_batched)."""
+    lib = load_library()
+    packed, ns, offs, dt = _pack(Qs)
+    p = Plan()
+    _check(lib.qubo_autotune_batched(_ptr(packed), _ptr(ns), _ptr(offs), len(ns), dt, ctypes.byref(p)),
+           "qubo_autotune_batched")
+    return {"variant": p.variant, "walk_bits": p.walk_bits, "states_per_s": p.states_per_s, "trials": p.trials}
+
+
+def autotune_clear() -> None:
+    load_library().qubo_autotune_clear()
+
+
+class Batch:
+    """Device-resident batch replayed as one CUDA graph (qubo_batch_*)."""
+
+    def __init__(self, Qs, topk: int = 0, states_cap: int = 64):
+        self._lib = load_library()
+        packed, ns, offs, dt = _pack(Qs)
+        self.count, self.dt, self.topk, self.states_cap = len(ns), dt, topk, states_cap
+        h = ctypes.c_void_p()
+        _check(self._lib.qubo_batch_create(_ptr(packed), _ptr(ns), _ptr(offs), self.count, dt, topk, states_cap,
+                                           ctypes.byref(h)), "qubo_batch_create")
+        self._h = h
+        self._out = _batch_outputs(self.count, dt, topk, states_cap)
+
+    def run(self, stream=None) -> None:
+        _check(self._lib.qubo_batch_run(self._h, _stream_ptr(stream)), "qubo_batch_run")
+
+    def fetch(self) -> list[Result]:
+        mn, ties, tk, tkE, infos = self._out
+        _check(self._lib.qubo_batch_fetch(self._h, _ptr(mn), _ptr(ties), _ptr(tk), _ptr(tkE), infos),
+               "qubo_batch_fetch")
+        return _batch_results(self.count, self.dt, self.topk, self.states_cap, mn, ties, tk, tkE, infos)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.qubo_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+def solve_batched(Qs, topk: int = 0, states_cap: int = 64, stream=None) -> list[Result]:
+    """Solve many instances in one persistent launch (qubo_solve_batched).  All matrices must
+    share one dtype."""
+    lib = load_library()
+    packed, ns, offs, dt = _pack(Qs)
+    count = len(ns)
+    mn, ties, tk, tkE, infos = _batch_outputs(count, dt, topk, states_cap)
+    st = lib.qubo_solve_batched(_ptr(packed), _ptr(ns), _ptr(offs), count, dt, topk, _ptr(mn), _ptr(ties),
+                                states_cap, _ptr(tk), _ptr(tkE), infos, _stream_ptr(stream))
+    _check(st, "qubo_solve_batched")
+    return _batch_results(count, dt, topk, states_cap, mn, ties, tk, tkE, infos)
 
 
 def solve_noalloc(Q, states_cap: int = 64, stream=None) -> Result:

@@ -6,7 +6,10 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <memory>
 #include <mutex>
+#include <tuple>
 #include <new>
 #include <random>
 #include <thread>
@@ -22,6 +25,7 @@ using namespace qubo;
 namespace {
 
 constexpr unsigned long long kDefaultRecCap = 1ull << 22;  // candidate records per job (64 MiB)
+constexpr unsigned long long kBatchGraphRecords = 1ull << 18;  // candidate records of a replayed batch
 constexpr double kDefaultMargin = 1e-3;
 constexpr int kTargetUnitsLog2 = 15;   // aim for >= 2^15 work units per scan
 constexpr int kDefaultMaxWalkBits = 12;
@@ -536,6 +540,53 @@ int scan_variant(Acc acc = ACC_I32)
     return acc == ACC_F32 ? kDefaultVariantF32 : kDefaultVariantI32;
 }
 
+// Plans installed by the autotuner: (device, accumulator, n) -> (variant, walk bits); n = 0 is
+// the entry used by batches.  Consulted when the caller fixes neither split_k nor walk_bits and
+// QUBO_SCAN_VARIANT is unset.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;
+
+bool tuned_plan(Acc acc, int n, int *variant, int *walk)
+{
+    if (std::getenv("QUBO_SCAN_VARIANT"))
+        return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find({dev, (int)acc, n});
+    if (it == g_tuned.end())
+        return false;
+    *variant = it->second.first;
+    *walk = it->second.second;
+    return true;
+}
+
+void install_plan(Acc acc, int n, int variant, int walk)
+{
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[{dev, (int)acc, n}] = {variant, walk};
+}
+
+// Timing events: recorded as event nodes of the graph while the stream is being captured,
+// plainly otherwise.
+cudaError_t record_event(cudaEvent_t e, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t q = cudaStreamIsCapturing(s, &cs);
+    if (q != cudaSuccess)
+        return q;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                               : cudaEventRecord(e, s);
+}
+
 #define CK(call)                                                                                   \
     do {                                                                                           \
         cudaError_t e_ = (call);                                                                   \
@@ -574,6 +625,7 @@ struct Job {
     int launches = 0;
     uint64_t h2d = 0, d2h = 0;
     double scan_seconds = 0.0;
+    uint64_t total_items = 0;
 };
 
 int job_layout(Job &j)
@@ -643,14 +695,15 @@ int job_layout(Job &j)
     return QUBO_OK;
 }
 
-// Stage, upload and launch tables + scan.  Does not wait.
-int job_launch(Workspace &ws, Job &j)
+// Lay out the job, size the workspace and fill the host staging buffer (descriptors, initial
+// thresholds, item bases, coupling matrices).
+int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
 {
     const int ni = (int)j.insts.size();
     int st;
     if ((st = job_layout(j)))
         return st;
-    if ((st = ws.ensure(j.arena_bytes, kDefaultRecCap, j.up_bytes, j.down_bytes)))
+    if ((st = ws.ensure(j.arena_bytes + extra_arena, kDefaultRecCap, j.up_bytes, j.down_bytes)))
         return st;
     char *up = (char *)ws.h_up;
     char *dev = (char *)ws.d_arena;
@@ -658,7 +711,6 @@ int job_launch(Workspace &ws, Job &j)
     InstState *hs = (InstState *)(up + j.off_state);
     uint64_t *items = (uint64_t *)(up + j.off_items);
     uint64_t total = 0;
-    const bool k1 = j.K <= 1;
     for (int i = 0; i < ni; ++i) {
         HostInst &h = *j.insts[i];
         const size_t nn = (size_t)h.n * h.n;
@@ -719,54 +771,76 @@ int job_launch(Workspace &ws, Job &j)
         total += h.items;
     }
     items[ni] = total;
-
-    cudaStream_t s = j.stream;
-    *ws.h_abort = g_abort_all.load() ? 1 : 0;
-    CK(cudaMemcpyAsync(dev, up, j.up_bytes, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(dev + j.off_ctr, 0, 16 * 8, s));
-    CK(cudaEventRecord(ws.ev[0], s));
-    CK(launch_tables(j.acc, (const Inst *)(dev + j.off_inst), ni, j.max_entries, s));
-    CK(cudaEventRecord(ws.ev[3], s));
-    ScanArgs a{};
-    a.inst = (const Inst *)(dev + j.off_inst);
-    a.state = (InstState *)(dev + j.off_state);
-    a.item_base = (const uint64_t *)(dev + j.off_items);
-    a.n_inst = ni;
-    a.k1 = k1 ? 1 : 0;
-    a.total_items = total;
-    a.queue = (unsigned long long *)(dev + j.off_ctr);
-    a.rec = ws.d_rec;
-    a.rec_cap = std::min(ws.rec_cap, record_capacity());
-    j.rec_cap = a.rec_cap;
-    a.nrec = (unsigned long long *)(dev + j.off_ctr) + 1;
-    a.abort_flag = ws.d_abort;
-    a.margin = (j.acc == ACC_F32 || j.acc == ACC_F64) ? j.margin : 0.0;
-    a.one = 1;
-    a.zero = 0;
-    int bps = scan_blocks_per_sm(j.acc, k1, j.variant);
+    j.total_items = total;
+    j.rec_cap = std::min(ws.rec_cap, record_capacity());
+    int bps = scan_blocks_per_sm(j.acc, j.K <= 1, j.variant);
     if (bps < 1)
         bps = 1;
     j.blocks = ws.sms * bps;
     const uint64_t need_blocks = (total * 32 + kScanThreads - 1) / kScanThreads;
     if ((uint64_t)j.blocks > need_blocks)
         j.blocks = (int)std::max<uint64_t>(1, need_blocks);
+    return QUBO_OK;
+}
+
+// Enqueue the run's inputs and the table build and scan on j.stream.  With state_init set, the
+// descriptors are already on the device and the per-run state is copied from state_init
+// (device to device), so the sequence can be captured and replayed as a graph.
+int job_enqueue_scan(Workspace &ws, Job &j, const void *state_init = nullptr)
+{
+    const int ni = (int)j.insts.size();
+    char *up = (char *)ws.h_up;
+    char *dev = (char *)ws.d_arena;
+    cudaStream_t s = j.stream;
+    if (state_init) {
+        CK(cudaMemcpyAsync(dev + j.off_state, state_init, sizeof(InstState) * ni, cudaMemcpyDeviceToDevice, s));
+    } else {
+        CK(cudaMemcpyAsync(dev, up, j.up_bytes, cudaMemcpyHostToDevice, s));
+        j.h2d += j.up_bytes;
+    }
+    CK(cudaMemsetAsync(dev + j.off_ctr, 0, 16 * 8, s));
+    CK(record_event(ws.ev[0], s));
+    CK(launch_tables(j.acc, (const Inst *)(dev + j.off_inst), ni, j.max_entries, s));
+    CK(record_event(ws.ev[3], s));
+    ScanArgs a{};
+    a.inst = (const Inst *)(dev + j.off_inst);
+    a.state = (InstState *)(dev + j.off_state);
+    a.item_base = (const uint64_t *)(dev + j.off_items);
+    a.n_inst = ni;
+    a.k1 = j.K <= 1 ? 1 : 0;
+    a.total_items = j.total_items;
+    a.queue = (unsigned long long *)(dev + j.off_ctr);
+    a.rec = ws.d_rec;
+    a.rec_cap = j.rec_cap;
+    a.nrec = (unsigned long long *)(dev + j.off_ctr) + 1;
+    a.abort_flag = ws.d_abort;
+    a.margin = (j.acc == ACC_F32 || j.acc == ACC_F64) ? j.margin : 0.0;
+    a.one = 1;
+    a.zero = 0;
     CK(launch_scan(j.acc, a, j.blocks, j.variant, s));
-    CK(cudaEventRecord(ws.ev[1], s));
+    CK(record_event(ws.ev[1], s));
     j.launches += 2;
-    j.h2d += j.up_bytes;
+    return QUBO_OK;
+}
+
+// Stage, upload and launch tables + scan.  Does not wait.
+int job_launch(Workspace &ws, Job &j)
+{
+    int st;
+    if ((st = job_stage(ws, j)))
+        return st;
+    *ws.h_abort = g_abort_all.load() ? 1 : 0;
+    if ((st = job_enqueue_scan(ws, j)))
+        return st;
     j.t_start = now_s();
     return QUBO_OK;
 }
 
-// Wait for the scan (honouring the time limit and qubo_abort), then finalize and download.
-int job_finish(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seconds)
+// Wait for `ev` (the scan's end), honouring the time limit and qubo_abort.
+int job_wait(Workspace &ws, Job &j, cudaEvent_t ev)
 {
-    const int ni = (int)j.insts.size();
-    char *dev = (char *)ws.d_arena;
-    cudaStream_t s = j.stream;
-    // watchdog: poll the scan's completion event
     for (;;) {
-        const cudaError_t q = cudaEventQuery(ws.ev[1]);
+        const cudaError_t q = cudaEventQuery(ev);
         if (q == cudaSuccess)
             break;
         if (q != cudaErrorNotReady) {
@@ -782,6 +856,116 @@ int job_finish(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seco
     }
     if (*(volatile int *)ws.h_abort)
         j.aborted = true;
+    return QUBO_OK;
+}
+
+// Host-side view of the download staging buffer.
+struct Down {
+    ResOut *res;
+    InstState *sts;
+    uint64_t *ties, *tk;
+    int64_t *tke;
+};
+
+Down down_view(Workspace &ws, const Job &j)
+{
+    const int ni = (int)j.insts.size();
+    char *down = (char *)ws.h_down;
+    Down d;
+    size_t o = 0;
+    d.res = (ResOut *)(down + o);
+    o += sizeof(ResOut) * ni;
+    d.sts = (InstState *)(down + o);
+    o += sizeof(InstState) * ni;
+    d.ties = (uint64_t *)(down + o);
+    o += 8 * j.cap * ni;
+    d.tk = (uint64_t *)(down + o);
+    o += 8 * (size_t)j.K * ni;
+    d.tke = (int64_t *)(down + o);
+    return d;
+}
+
+// Enqueue rescoring (floats), the sort of the candidate records, extraction and the download
+// of the results.  max_pow2 bounds the sort network; the kernels read the record count on the
+// device, so a larger bound only costs empty launches (this is what a captured graph uses).
+int job_enqueue_finalize(Workspace &ws, Job &j, unsigned long long max_count, unsigned long long max_pow2)
+{
+    const int ni = (int)j.insts.size();
+    char *dev = (char *)ws.d_arena;
+    cudaStream_t s = j.stream;
+    const bool batched = ni > 1;
+    const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
+    const unsigned long long *d_nrec = (const unsigned long long *)(dev + j.off_ctr) + 1;
+    if (is_float) {
+        CK(launch_rescore((const Inst *)(dev + j.off_inst), (InstState *)(dev + j.off_state), ws.d_rec, d_nrec,
+                          j.rec_cap, batched, max_count, s));
+        j.launches += 1;
+    }
+    CK(launch_sort(ws.d_rec, d_nrec, j.rec_cap, max_pow2, batched, is_float, s, &j.launches));
+    j.launches += 2;  // bounds + extract
+    CK(launch_extract((const Inst *)(dev + j.off_inst), ws.d_rec, d_nrec, j.rec_cap, ni, batched, is_float, j.K,
+                      j.cap, (ResOut *)(dev + j.off_res), (uint64_t *)(dev + j.off_ties),
+                      (uint64_t *)(dev + j.off_topk), (int64_t *)(dev + j.off_topke),
+                      (unsigned long long *)(dev + j.off_starts), s));
+    CK(record_event(ws.ev[2], s));
+    const Down d = down_view(ws, j);
+    CK(cudaMemcpyAsync(d.res, dev + j.off_res, sizeof(ResOut) * ni, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(d.sts, dev + j.off_state, sizeof(InstState) * ni, cudaMemcpyDeviceToHost, s));
+    if (j.cap)
+        CK(cudaMemcpyAsync(d.ties, dev + j.off_ties, 8 * j.cap * ni, cudaMemcpyDeviceToHost, s));
+    if (j.K) {
+        CK(cudaMemcpyAsync(d.tk, dev + j.off_topk, 8 * (size_t)j.K * ni, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(d.tke, dev + j.off_topke, 8 * (size_t)j.K * ni, cudaMemcpyDeviceToHost, s));
+    }
+    j.d2h += sizeof(ResOut) * ni + sizeof(InstState) * ni + (j.cap ? 8 * j.cap * ni : 0) + 16 * (size_t)j.K * ni;
+    return QUBO_OK;
+}
+
+// After the stream has finished: timings and per-instance results from the staging buffer.
+void job_unpack(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seconds)
+{
+    const int ni = (int)j.insts.size();
+    const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ws.ev[0], ws.ev[2]) == cudaSuccess && gpu_seconds)
+        *gpu_seconds = ms * 1e-3;
+    if (cudaEventElapsedTime(&ms, ws.ev[3], ws.ev[1]) == cudaSuccess)
+        j.scan_seconds = ms * 1e-3;
+    const Down d = down_view(ws, j);
+    parts.assign(ni, Part());
+    for (int i = 0; i < ni; ++i) {
+        Part &p = parts[i];
+        const ResOut &r = d.res[i];
+        p.is_float = is_float;
+        p.has = r.has != 0;
+        p.min_i = r.min_i;
+        p.min_f = is_float ? r.min_f : (double)r.min_i;
+        p.n_ties = r.n_ties;
+        p.n_near = r.n_near;
+        p.ties.assign(d.ties + (size_t)i * j.cap, d.ties + (size_t)i * j.cap + r.n_written);
+        for (int t = 0; t < r.nk; ++t) {
+            const uint64_t c = d.tk[(size_t)i * j.K + t];
+            const int64_t e = d.tke[(size_t)i * j.K + t];
+            if (is_float)
+                p.topf.emplace_back(bits_to_double(e), c);
+            else
+                p.topi.emplace_back(e, c);
+        }
+        p.scanned = d.sts[i].scanned;
+        p.candidates = d.sts[i].nrec;
+        p.drift = ubits_to_double(d.sts[i].drift);
+        p.err = ubits_to_double(d.sts[i].err);
+        p.overflow = d.sts[i].dropped > 0;
+    }
+}
+
+// Wait for the scan, finalize with the exact record count, download and unpack.
+int job_finish(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seconds)
+{
+    char *dev = (char *)ws.d_arena;
+    int st;
+    if ((st = job_wait(ws, j, ws.ev[1])))
+        return st;
     unsigned long long nrec = 0;
     CK(cudaMemcpy(&nrec, dev + j.off_ctr + 8, 8, cudaMemcpyDeviceToHost));
     j.d2h += 8;
@@ -789,73 +973,10 @@ int job_finish(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seco
     unsigned long long P = 1;
     while (P < cnt)
         P <<= 1;
-    const bool batched = ni > 1;
-    const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
-    const unsigned long long *d_nrec = (const unsigned long long *)(dev + j.off_ctr) + 1;
-    if (is_float) {
-        CK(launch_rescore((const Inst *)(dev + j.off_inst), (InstState *)(dev + j.off_state), ws.d_rec, d_nrec,
-                          j.rec_cap, batched, cnt, s));
-        j.launches += 1;
-    }
-    CK(launch_sort(ws.d_rec, d_nrec, j.rec_cap, P, batched, is_float, s, &j.launches));
-    j.launches += 2;  // bounds + extract
-    CK(launch_extract((const Inst *)(dev + j.off_inst), ws.d_rec, d_nrec, j.rec_cap, ni, batched, is_float, j.K,
-                      j.cap, (ResOut *)(dev + j.off_res), (uint64_t *)(dev + j.off_ties),
-                      (uint64_t *)(dev + j.off_topk), (int64_t *)(dev + j.off_topke),
-                      (unsigned long long *)(dev + j.off_starts), s));
-    CK(cudaEventRecord(ws.ev[2], s));
-    // download
-    char *down = (char *)ws.h_down;
-    size_t o = 0;
-    ResOut *res = (ResOut *)(down + o);
-    o += sizeof(ResOut) * ni;
-    InstState *sts = (InstState *)(down + o);
-    o += sizeof(InstState) * ni;
-    uint64_t *ties = (uint64_t *)(down + o);
-    o += 8 * j.cap * ni;
-    uint64_t *tk = (uint64_t *)(down + o);
-    o += 8 * (size_t)j.K * ni;
-    int64_t *tke = (int64_t *)(down + o);
-    CK(cudaMemcpyAsync(res, dev + j.off_res, sizeof(ResOut) * ni, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(sts, dev + j.off_state, sizeof(InstState) * ni, cudaMemcpyDeviceToHost, s));
-    if (j.cap)
-        CK(cudaMemcpyAsync(ties, dev + j.off_ties, 8 * j.cap * ni, cudaMemcpyDeviceToHost, s));
-    if (j.K) {
-        CK(cudaMemcpyAsync(tk, dev + j.off_topk, 8 * (size_t)j.K * ni, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(tke, dev + j.off_topke, 8 * (size_t)j.K * ni, cudaMemcpyDeviceToHost, s));
-    }
-    CK(cudaStreamSynchronize(s));
-    j.d2h += sizeof(ResOut) * ni + sizeof(InstState) * ni + (j.cap ? 8 * j.cap * ni : 0) + 16 * (size_t)j.K * ni;
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, ws.ev[0], ws.ev[2]) == cudaSuccess && gpu_seconds)
-        *gpu_seconds = ms * 1e-3;
-    if (cudaEventElapsedTime(&ms, ws.ev[3], ws.ev[1]) == cudaSuccess)
-        j.scan_seconds = ms * 1e-3;
-    parts.assign(ni, Part());
-    for (int i = 0; i < ni; ++i) {
-        Part &p = parts[i];
-        const ResOut &r = res[i];
-        p.is_float = is_float;
-        p.has = r.has != 0;
-        p.min_i = r.min_i;
-        p.min_f = is_float ? r.min_f : (double)r.min_i;
-        p.n_ties = r.n_ties;
-        p.n_near = r.n_near;
-        p.ties.assign(ties + (size_t)i * j.cap, ties + (size_t)i * j.cap + r.n_written);
-        for (int t = 0; t < r.nk; ++t) {
-            const uint64_t c = tk[(size_t)i * j.K + t];
-            const int64_t e = tke[(size_t)i * j.K + t];
-            if (is_float)
-                p.topf.emplace_back(bits_to_double(e), c);
-            else
-                p.topi.emplace_back(e, c);
-        }
-        p.scanned = sts[i].scanned;
-        p.candidates = sts[i].nrec;
-        p.drift = ubits_to_double(sts[i].drift);
-        p.err = ubits_to_double(sts[i].err);
-        p.overflow = sts[i].dropped > 0;
-    }
+    if ((st = job_enqueue_finalize(ws, j, cnt, P)))
+        return st;
+    CK(cudaStreamSynchronize(j.stream));
+    job_unpack(ws, j, parts, gpu_seconds);
     return j.aborted ? QUBO_ERR_TIMEOUT : QUBO_OK;
 }
 
@@ -1019,6 +1140,16 @@ int solve_one(Workspace &ws, HostInst &h, const qubo_options &o, size_t states_c
     c.split_k = o.split_k;
     c.walk_bits = o.walk_bits;
     c.variant = scan_variant(h.acc);
+    if (o.split_k <= 0 && o.walk_bits <= 0 && acc_bytes(h.acc) == 4) {
+        int tv = 0, tw = 0;
+        if (tuned_plan(h.acc, h.n, &tv, &tw)) {
+            c.variant = tv;
+            HostInst probe = h;
+            probe.variant = tv;
+            if (plan(probe, o.fix_bits, o.fix_value, 0, tw) == QUBO_OK)
+                c.walk_bits = tw;
+        }
+    }
     const double deadline = o.time_limit_s > 0 ? now_s() + o.time_limit_s : 0.0;
     int st = solve_range(ws, h, o.fix_bits, o.fix_value, c, stream, p, stats, deadline);
     if (st)
@@ -1066,11 +1197,108 @@ void fill_plan_info(const HostInst &h, const SolveStats &stats, double t0, qubo_
     info->passes = stats.passes;
 }
 
+// Fold, bound, plan and threshold every instance of a batch (in parallel on the host), one
+// accumulator for all, and the launch order (longest work first, so the persistent launch's
+// tail is short).
+int batch_prepare(const void *Q_packed, const int *n, const size_t *offsets, int count, qubo_dtype dtype, int topk,
+                  std::vector<HostInst> &hs, std::vector<int> &order)
+{
+    const size_t esz = dtype == QUBO_I16 ? 2 : (dtype == QUBO_I32 || dtype == QUBO_F32) ? 4 : 8;
+    hs.assign(count, HostInst());
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 1 || n[i] > kMaxBatchedN)
+            return QUBO_ERR_ARG;
+        if (topk > 0 && (uint64_t)topk > (1ull << n[i]))
+            return QUBO_ERR_ARG;
+    }
+    // Host preparation (fold, bound, threshold) of the instances, in parallel.
+    std::vector<int> pst(count, QUBO_OK);
+    auto prep_range = [&](int lo, int hi) {
+        for (int i = lo; i < hi; ++i)
+            pst[i] = prepare((const char *)Q_packed + offsets[i] * esz, n[i], dtype, 0, hs[i]);
+    };
+    auto parallel = [&](auto &&fn) {
+        const int nt = std::max(1, std::min<int>(count / 64 + 1, (int)std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back(fn, (int)((int64_t)count * t / nt), (int)((int64_t)count * (t + 1) / nt));
+        for (auto &x : th)
+            x.join();
+    };
+    parallel(prep_range);
+    for (int i = 0; i < count; ++i)
+        if (pst[i])
+            return pst[i];
+    // one accumulator for the whole batch: the widest any instance needs
+    Acc acc = hs[0].acc;
+    for (auto &h : hs)
+        if (acc_bytes(h.acc) > acc_bytes(acc))
+            acc = h.acc;
+    for (auto &h : hs)
+        h.acc = acc;
+    // The batch supplies the parallelism, so every instance walks as long as it can (fewest,
+    // largest units: less per-unit set-up).
+    int variant = scan_variant(acc);
+    {
+        int tv = 0, tw = 0;
+        if (tuned_plan(acc, 0, &tv, &tw))
+            variant = tv;
+    }
+    auto plan_range = [&](int lo, int hi) {
+        for (int i = lo; i < hi; ++i) {
+            HostInst &h = hs[i];
+            h.variant = acc_bytes(acc) == 4 ? variant : 0;
+            const int B = suffix_bits(acc_bytes(acc), h.variant);
+            const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
+            const int walk = h.n - B >= kRegRows + 1 ? std::min(wmax, h.n - B) : 0;
+            pst[i] = plan(h, 0, 0, 0, walk);
+            if (!pst[i])
+                h.thr0 = threshold_bound(h, std::max(1, topk));
+        }
+    };
+    parallel(plan_range);
+    for (int i = 0; i < count; ++i)
+        if (pst[i])
+            return pst[i];
+    // longest work first (LPT order) so the tail of the persistent launch is short
+    order.resize(count);
+    for (int i = 0; i < count; ++i)
+        order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a].states > hs[b].states; });
+    return QUBO_OK;
+}
+
 }  // namespace
 
 // ================================================================================================
 // C ABI
 // ================================================================================================
+
+struct qubo_batch {
+    std::vector<HostInst> hs;
+    std::vector<int> order;   // launch order (longest first) -> caller index
+    Job job;
+    Workspace ws;
+    int count = 0;
+    int topk = 0;
+    size_t cap = 0;
+    bool is_float = false;
+    size_t off_state_init = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    bool launched = false;
+    double t0 = 0.0;
+    ~qubo_batch()
+    {
+        if (exec)
+            cudaGraphExecDestroy(exec);
+        if (graph)
+            cudaGraphDestroy(graph);
+        if (cap_stream)
+            cudaStreamDestroy(cap_stream);
+    }
+};
 
 struct qubo_problem {
     HostInst h;
@@ -1189,64 +1417,13 @@ int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets
         return QUBO_ERR_ARG;
     if (topk < 0 || topk > QUBO_MAX_TOPK || (topk > 0 && !out_topk) || (states_cap_per_inst > 0 && !out_states))
         return QUBO_ERR_ARG;
-    const size_t esz = dtype == QUBO_I16 ? 2 : (dtype == QUBO_I32 || dtype == QUBO_F32) ? 4 : 8;
-    std::vector<HostInst> hs(count);
-    for (int i = 0; i < count; ++i) {
-        if (n[i] < 1 || n[i] > kMaxBatchedN)
-            return QUBO_ERR_ARG;
-        if (topk > 0 && (uint64_t)topk > (1ull << n[i]))
-            return QUBO_ERR_ARG;
-    }
-    // Host preparation (fold, bound, threshold) of the instances, in parallel.
-    std::vector<int> pst(count, QUBO_OK);
-    auto prep_range = [&](int lo, int hi) {
-        for (int i = lo; i < hi; ++i)
-            pst[i] = prepare((const char *)Q_packed + offsets[i] * esz, n[i], dtype, 0, hs[i]);
-    };
-    auto parallel = [&](auto &&fn) {
-        const int nt = std::max(1, std::min<int>(count / 64 + 1, (int)std::thread::hardware_concurrency()));
-        std::vector<std::thread> th;
-        for (int t = 0; t < nt; ++t)
-            th.emplace_back(fn, (int)((int64_t)count * t / nt), (int)((int64_t)count * (t + 1) / nt));
-        for (auto &x : th)
-            x.join();
-    };
-    parallel(prep_range);
-    int st;
-    for (int i = 0; i < count; ++i)
-        if (pst[i])
-            return pst[i];
-    // one accumulator for the whole batch: the widest any instance needs
-    Acc acc = hs[0].acc;
-    for (auto &h : hs)
-        if (acc_bytes(h.acc) > acc_bytes(acc))
-            acc = h.acc;
-    for (auto &h : hs)
-        h.acc = acc;
-    // The batch supplies the parallelism, so every instance walks as long as it can (fewest,
-    // largest units: less per-unit set-up).
-    const int variant = scan_variant(acc);
-    auto plan_range = [&](int lo, int hi) {
-        for (int i = lo; i < hi; ++i) {
-            HostInst &h = hs[i];
-            h.variant = acc_bytes(acc) == 4 ? variant : 0;
-            const int B = suffix_bits(acc_bytes(acc), h.variant);
-            const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
-            const int walk = h.n - B >= kRegRows + 1 ? std::min(wmax, h.n - B) : 0;
-            pst[i] = plan(h, 0, 0, 0, walk);
-            if (!pst[i])
-                h.thr0 = threshold_bound(h, std::max(1, topk));
-        }
-    };
-    parallel(plan_range);
-    for (int i = 0; i < count; ++i)
-        if (pst[i])
-            return pst[i];
-    // longest work first (LPT order) so the tail of the persistent launch is short
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i)
-        order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a].states > hs[b].states; });
+    std::vector<HostInst> hs;
+    std::vector<int> order;
+    int st = batch_prepare(Q_packed, n, offsets, count, dtype, topk, hs, order);
+    if (st)
+        return st;
+    const int variant = hs[0].variant;
+    const Acc acc = hs[0].acc;
     Workspace *ws = nullptr;
     if ((st = resolve_device(&ws)))
         return st;
@@ -1410,6 +1587,323 @@ void qubo_problem_destroy(qubo_problem *p)
         return;
     unregister_ws(&p->ws);
     delete p;
+}
+
+int qubo_batch_create(const void *Q_packed, const int *n, const size_t *offsets, int count, qubo_dtype dtype, int topk,
+                      size_t states_cap_per_inst, qubo_batch **out)
+{
+    if (!out || !Q_packed || !n || !offsets || count < 1 || count > 65535 || !dtype_ok(dtype))
+        return QUBO_ERR_ARG;
+    if (topk < 0 || topk > QUBO_MAX_TOPK)
+        return QUBO_ERR_ARG;
+    *out = nullptr;
+    qubo_batch *b = new (std::nothrow) qubo_batch();
+    if (!b)
+        return QUBO_ERR_NOMEM;
+    std::unique_ptr<qubo_batch> guard(b);
+    b->count = count;
+    b->topk = topk;
+    b->cap = states_cap_per_inst;
+    b->is_float = dtype_float(dtype);
+    int st = batch_prepare(Q_packed, n, offsets, count, dtype, topk, b->hs, b->order);
+    if (st)
+        return st;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return QUBO_ERR_CUDA;
+    }
+    if ((st = b->ws.init(dev)))
+        return st;
+    Job &j = b->job;
+    for (int i : b->order)
+        j.insts.push_back(&b->hs[i]);
+    j.acc = b->hs[0].acc;
+    j.K = topk;
+    j.cap = states_cap_per_inst;
+    j.margin = kDefaultMargin;
+    j.variant = b->hs[0].variant;
+    // the initial per-instance state lives after the job's arena and is copied in at every run
+    const size_t state_bytes = sizeof(InstState) * (size_t)count;
+    if ((st = job_stage(b->ws, j, state_bytes + 256)))
+        return st;
+    // A graph sorts with a fixed network sized by the buffer; batches produce few candidates per
+    // instance, so a smaller buffer keeps the replay short (an instance that overflows it is
+    // solved again on its own at fetch time).
+    j.rec_cap = std::min<unsigned long long>(j.rec_cap, kBatchGraphRecords);
+    b->off_state_init = align_up(j.arena_bytes, 256);
+    char *dev_arena = (char *)b->ws.d_arena;
+    CK(cudaMemcpy(dev_arena, b->ws.h_up, j.up_bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dev_arena + b->off_state_init, (char *)b->ws.h_up + j.off_state, state_bytes,
+                  cudaMemcpyHostToDevice));
+    j.h2d += j.up_bytes + state_bytes;
+    // capture tables -> scan -> (rescore) -> sort -> extract -> download as one graph
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return QUBO_ERR_CUDA;
+    }
+    j.stream = b->cap_stream;
+    unsigned long long P = 1;
+    while (P < j.rec_cap)
+        P <<= 1;
+    CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int st1 = job_enqueue_scan(b->ws, j, dev_arena + b->off_state_init);
+    int st2 = st1 ? st1 : job_enqueue_finalize(b->ws, j, j.rec_cap, P);
+    const cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &b->graph);
+    if (st1 || st2 || ce != cudaSuccess) {
+        cudaGetLastError();
+        return st1 ? st1 : (st2 ? st2 : QUBO_ERR_CUDA);
+    }
+    if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return QUBO_ERR_CUDA;
+    }
+    register_ws(&b->ws);
+    *out = guard.release();
+    return QUBO_OK;
+}
+
+int qubo_batch_run(qubo_batch *b, void *stream)
+{
+    if (!b)
+        return QUBO_ERR_ARG;
+    b->t0 = now_s();
+    Job &j = b->job;
+    j.stream = (cudaStream_t)stream;
+    j.aborted = false;
+    j.launches = 0;
+    j.h2d = j.d2h = 0;
+    *b->ws.h_abort = g_abort_all.load() ? 1 : 0;
+    if (cudaGraphLaunch(b->exec, j.stream) != cudaSuccess) {
+        cudaGetLastError();
+        b->launched = false;
+        return QUBO_ERR_CUDA;
+    }
+    j.t_start = now_s();
+    b->launched = true;
+    return QUBO_OK;
+}
+
+int qubo_batch_fetch(qubo_batch *b, void *out_min, uint64_t *out_states, uint64_t *out_topk, void *out_topk_E,
+                     qubo_result *info)
+{
+    if (!b || !out_min || (b->cap > 0 && !out_states) || (b->topk > 0 && !out_topk))
+        return QUBO_ERR_ARG;
+    if (!b->launched)
+        return QUBO_ERR_ARG;
+    b->launched = false;
+    Job &j = b->job;
+    int st;
+    if ((st = job_wait(b->ws, j, b->ws.ev[2])))
+        return st;
+    CK(cudaStreamSynchronize(j.stream));
+    std::vector<Part> parts;
+    double gs = 0.0;
+    job_unpack(b->ws, j, parts, &gs);
+    // the graph's launches: the same kernels a direct run makes, with every sort stage present
+    j.launches = 0;
+    {
+        const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
+        unsigned long long P = 1;
+        while (P < j.rec_cap)
+            P <<= 1;
+        int nl = 2 + (is_float ? 1 : 0) + 2 + (P >= 2 ? 2 : 0);
+        for (unsigned long long k = 4096; k <= P; k <<= 1) {
+            for (unsigned long long jj = k >> 1; jj >= 2048; jj >>= 1)
+                ++nl;
+            ++nl;
+        }
+        j.launches = nl;
+    }
+    j.d2h = sizeof(ResOut) * b->count + sizeof(InstState) * b->count + 8 * j.cap * b->count + 16 * (size_t)j.K * b->count;
+    if (j.aborted)
+        return QUBO_ERR_TIMEOUT;
+    int worst = QUBO_OK;
+    SolveCfg c;
+    c.K = b->topk;
+    c.cap = b->cap;
+    c.variant = j.variant;
+    for (int r = 0; r < b->count; ++r) {
+        const int i = b->order[r];
+        Part &p = parts[r];
+        HostInst &h = b->hs[i];
+        SolveStats stats;
+        stats.add(j, gs);
+        if (p.overflow || !float_margin_ok(h, p, c.margin)) {
+            // rare: solve this instance alone on the shared workspace (the graph's is fixed)
+            Workspace *sw = nullptr;
+            if ((st = resolve_device(&sw)))
+                return st;
+            std::lock_guard<std::mutex> lk(sw->mu);
+            int dev = -1;
+            cudaGetDevice(&dev);
+            if ((st = sw->init(dev)))
+                return st;
+            HostInst hc = h;
+            if (!float_margin_ok(hc, p, c.margin))
+                hc.acc = ACC_F64;
+            p = Part();
+            if ((st = solve_range(*sw, hc, 0, 0, c, j.stream, p, stats, 0.0)))
+                return st;
+        }
+        if (p.scanned != (1ull << h.n) || !p.has)
+            return QUBO_ERR_INTERNAL;
+        void *om = h.is_float ? (void *)((double *)out_min + i) : (void *)((int64_t *)out_min + i);
+        void *otke = nullptr;
+        if (out_topk_E)
+            otke = h.is_float ? (void *)((double *)out_topk_E + (size_t)i * b->topk)
+                              : (void *)((int64_t *)out_topk_E + (size_t)i * b->topk);
+        qubo_result *inf = info ? info + i : nullptr;
+        if (inf)
+            std::memset(inf, 0, sizeof(*inf));
+        fill_outputs(h, p, b->topk, b->cap, om, out_states ? out_states + (size_t)i * b->cap : nullptr,
+                     out_topk ? out_topk + (size_t)i * b->topk : nullptr, otke, inf);
+        fill_plan_info(h, stats, b->t0, inf);
+        if (p.n_ties > b->cap)
+            worst = std::max(worst, (int)QUBO_TRUNCATED);
+    }
+    return worst;
+}
+
+void qubo_batch_destroy(qubo_batch *b)
+{
+    if (!b)
+        return;
+    unregister_ws(&b->ws);
+    delete b;
+}
+
+int qubo_autotune(const void *Q_host, int n, qubo_dtype dtype, int fix_bits, qubo_plan *best)
+{
+    if (!best || fix_bits < 0)
+        return QUBO_ERR_ARG;
+    HostInst h;
+    int st = prepare(Q_host, n, dtype, 0, h);
+    if (st)
+        return st;
+    if (fix_bits > n)
+        return QUBO_ERR_ARG;
+    Workspace *ws = nullptr;
+    if ((st = resolve_device(&ws)))
+        return st;
+    std::lock_guard<std::mutex> lk(ws->mu);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if ((st = ws->init(dev)))
+        return st;
+    const int nvar = acc_bytes(h.acc) == 4 ? kScanVariants : 1;
+    std::memset(best, 0, sizeof(*best));
+    double best_rate = -1.0;
+    for (int v = 0; v < nvar; ++v) {
+        HostInst base = h;
+        base.variant = v;
+        if (plan(base, fix_bits, 0, 0, 0))
+            continue;
+        if (base.small)
+            break;  // nothing to tune: the sub-cube is evaluated directly
+        const int L0 = base.L;
+        for (int L = std::max(kRegRows + 1, L0 - 2); L <= std::min(kMaxWalkBits, L0 + 2); L += 2) {
+            SolveCfg c;
+            c.K = 0;
+            c.cap = 0;
+            c.variant = v;
+            c.walk_bits = L;
+            HostInst t = h;
+            t.variant = v;
+            if (plan(t, fix_bits, 0, 0, L) || kVariantRegRows[v] + 1 > L)
+                continue;
+            double rate = 0.0;
+            for (int rep = 0; rep < 2; ++rep) {  // the first run warms the workspace
+                Part p;
+                SolveStats stats;
+                HostInst r = h;
+                if ((st = solve_range(*ws, r, fix_bits, (uint64_t)rep, c, nullptr, p, stats, 0.0)))
+                    return st;
+                if (stats.scan_seconds > 0)
+                    rate = (double)p.scanned / stats.scan_seconds;
+            }
+            best->trials += 1;
+            if (rate > best_rate) {
+                best_rate = rate;
+                best->variant = v;
+                best->walk_bits = L;
+                best->states_per_s = rate;
+            }
+        }
+    }
+    if (best_rate > 0)
+        install_plan(h.acc, n, best->variant, best->walk_bits);
+    return QUBO_OK;
+}
+
+int qubo_autotune_batched(const void *Q_packed, const int *n, const size_t *offsets, int count, qubo_dtype dtype,
+                          qubo_plan *best)
+{
+    if (!best)
+        return QUBO_ERR_ARG;
+    std::memset(best, 0, sizeof(*best));
+    std::vector<HostInst> hs;
+    std::vector<int> order;
+    int st = batch_prepare(Q_packed, n, offsets, count, dtype, 0, hs, order);
+    if (st)
+        return st;
+    const Acc acc = hs[0].acc;
+    const int nvar = acc_bytes(acc) == 4 ? kScanVariants : 1;
+    Workspace *ws = nullptr;
+    if ((st = resolve_device(&ws)))
+        return st;
+    std::lock_guard<std::mutex> lk(ws->mu);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if ((st = ws->init(dev)))
+        return st;
+    double best_t = 0.0;
+    for (int v = 0; v < nvar; ++v) {
+        std::vector<HostInst> hv = hs;
+        bool ok = true;
+        for (auto &h : hv) {
+            h.variant = acc_bytes(acc) == 4 ? v : 0;
+            const int B = suffix_bits(acc_bytes(acc), h.variant);
+            const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
+            const int walk = h.n - B >= kVariantRegRows[v] + 1 ? std::min(wmax, h.n - B) : 0;
+            if (plan(h, 0, 0, 0, walk))
+                ok = false;
+        }
+        if (!ok)
+            continue;
+        double t = 0.0;
+        for (int rep = 0; rep < 2; ++rep) {
+            Job j;
+            for (int i : order)
+                j.insts.push_back(&hv[i]);
+            j.acc = acc;
+            j.variant = acc_bytes(acc) == 4 ? v : 0;
+            j.margin = kDefaultMargin;
+            std::vector<Part> parts;
+            double gs = 0.0;
+            if ((st = job_launch(*ws, j)) || (st = job_finish(*ws, j, parts, &gs)))
+                return st;
+            t = j.scan_seconds;
+        }
+        best->trials += 1;
+        if (t > 0 && (best_t == 0.0 || t < best_t)) {
+            best_t = t;
+            best->variant = v;
+            uint64_t states = 0;
+            for (auto &h : hv)
+                states += h.states;
+            best->states_per_s = (double)states / t;
+        }
+    }
+    if (best_t > 0)
+        install_plan(acc, 0, best->variant, 0);
+    return QUBO_OK;
+}
+
+void qubo_autotune_clear(void)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned.clear();
 }
 
 int qubo_merge(const qubo_partial *a, const qubo_partial *b, size_t cap, int topk, qubo_partial *out)

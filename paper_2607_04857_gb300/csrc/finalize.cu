@@ -319,8 +319,8 @@ cudaError_t launch_sort(Rec *rec, const unsigned long long *d_nrec, unsigned lon
     for (unsigned long long k = 2 * kChunk; k <= max_pow2; k <<= 1) {
         for (unsigned long long j = k >> 1; j >= (unsigned long long)kChunk; j >>= 1) {
             unsigned long long blocks = (max_pow2 + 255) / 256;
-            if (blocks > 16384)
-                blocks = 16384;
+            if (blocks > 2048)
+                blocks = 2048;  // grid-stride; keeps stages that the device count skips cheap
             ++nl;
             if (is_float)
                 sort_global_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(rec, d_nrec, cap, batched, k, j);

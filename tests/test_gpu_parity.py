@@ -244,13 +244,16 @@ def test_batched_float(q):
 # --- the n=50 configuration, sampled ---------------------------------------------------------
 
 def test_n50_sampled_subcubes(q):
-    """The n=50 instance with the plan the benchmark uses (walk 12, suffix 10 bits): sub-cubes
-    of 2^24 states at sampled prefixes, each checked against the oracle."""
+    """The n=50 instance with the plan the benchmark uses (the default variant, 12 walked bits):
+    sub-cubes of 2^24 states at sampled prefixes, each checked against the oracle."""
     Q = wl.config5()
     rng = np.random.default_rng(50)
     for v in rng.integers(0, 1 << 26, size=6):
         r = q.solve(Q, topk=16, fix_bits=26, fix_value=int(v), walk_bits=12)
-        assert r.info["split_k"] == 28 and r.info["acc"] == "i32"
+        i = r.info
+        # the benchmark's 2^43-state steps plan 12 walked bits with the default variant too
+        assert i["acc"] == "i32" and i["walk_bits"] == 12
+        assert i["split_k"] + i["walk_bits"] + i["suffix_bits"] == 50
         check_int(r, oracle.solve(Q, topk=16, fix_bits=26, fix_value=int(v)))
 
 
@@ -290,3 +293,81 @@ def test_config3_subcube_stays_fp32(q):
         assert r.info["acc"] == "f32", r.info
         assert 2 * r.info["fp32_max_drift"] < 1e-3 and r.info["fp32_max_abs_err"] < 5e-4
         check_float(r, oracle.solve(Q, topk=16, fix_bits=20, fix_value=v))
+
+
+# --- device-resident batch replayed as a CUDA graph -------------------------------------------
+
+def test_batch_graph_replays_match_oracle(q):
+    insts = wl.config4(count=64, seed=44)
+    insts = [Q for Q in insts if Q.shape[0] <= 24][:30] + [wl.upper_int(9, -50, 50, seed=9, dtype=np.int16)]
+    b = q.Batch(insts, topk=3, states_cap=32)
+    for rep in range(3):  # replays reuse the graph; thresholds and counters are reset each time
+        b.run()
+        rs = b.fetch()
+        for Q, r in zip(insts, rs):
+            check_int(r, oracle.solve(Q.astype(np.int32), topk=3, cap=32))
+    b.close()
+
+
+def test_batch_graph_float(q):
+    insts = [wl.sk_float32(n, seed=100 + n) for n in (12, 16, 19, 21)]
+    b = q.Batch(insts, topk=2)
+    b.run()
+    for Q, r in zip(insts, b.fetch()):
+        check_float(r, oracle.solve(Q, topk=2))
+    b.close()
+
+
+# --- stored oracle results and the autotuner --------------------------------------------------
+
+GOLDEN_DIR = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_config2_matches_golden(q):
+    import json
+
+    g = json.load(open(os.path.join(GOLDEN_DIR, "cfg2_n36_top16.json")))
+    r = q.solve(wl.config2(), topk=16)
+    assert r.min == g["min"] and r.n_ties == g["n_ties"]
+    assert [int(c) for c in r.ties] == g["ties"]
+    assert [int(c) for c in r.topk] == g["topk"] and [int(e) for e in r.topk_E] == g["topk_E"]
+
+
+def test_config4_matches_golden(q):
+    import json
+
+    path = os.path.join(GOLDEN_DIR, "cfg4_batched.json")
+    if not os.path.exists(path):
+        pytest.skip("cfg4 golden not generated")
+    g = json.load(open(path))
+    insts = wl.config4()
+    b = q.Batch(insts, topk=0, states_cap=g["cap"])
+    b.run()
+    rs = b.fetch()
+    b.close()
+    for row, r in zip(g["instances"], rs):
+        assert r.min == row["min"] and r.n_ties == row["n_ties"], row["i"]
+        assert [int(c) for c in r.ties] == row["ties"], row["i"]
+
+
+def test_autotune_installs_a_working_plan(q):
+    Q = wl.upper_int(34, -500, 500, seed=55)
+    p = q.autotune(Q, fix_bits=8)
+    try:
+        assert p["trials"] >= 2 and p["states_per_s"] > 0
+        r = q.solve(Q, topk=8, fix_bits=6, fix_value=3)
+        assert r.info["walk_bits"] == p["walk_bits"]
+        check_int(r, oracle.solve(Q, topk=8, fix_bits=6, fix_value=3))
+    finally:
+        q.autotune_clear()
+
+
+def test_autotune_batched(q):
+    insts = [wl.upper_int(n, -100, 100, seed=n, dtype=np.int16) for n in (14, 17, 20, 22, 23)]
+    p = q.autotune_batched(insts)
+    try:
+        assert p["trials"] >= 1
+        for Q, r in zip(insts, q.solve_batched(insts, topk=2)):
+            check_int(r, oracle.solve(Q.astype(np.int32), topk=2, cap=64))
+    finally:
+        q.autotune_clear()
