@@ -132,6 +132,21 @@ int qubo_solve_ex(const void *Q_host, int n, qubo_dtype dtype, const qubo_option
                   void *out_topk_E, qubo_result *info, void *stream);
 
 /*
+ * Low-energy spectrum (Sec. 6.2: the k lowest energies, Sec. 1.4: brute force yields the
+ * low-energy spectrum): every state with E <= E_min + window, in (E, code) ascending order.
+ *   window     >= 0, in energy units (integer Q: the integer part is used; < 2^30).
+ *   opt        as qubo_solve_ex (topk is ignored); may be NULL.
+ *   out_codes  host, cap codes; out_E host, cap energies (int64_t, or double for float Q).
+ *   out_count  host: the exact number of states in the window.
+ *   info       optional; info->min_i / min_f hold E_min, info->n_written the codes written.
+ * Returns QUBO_OK, QUBO_TRUNCATED (count > cap; the cap lowest are written) or an error.  Float
+ * instances apply the window to the FP64-rescored energies.
+ */
+int qubo_solve_window(const void *Q_host, int n, qubo_dtype dtype, double window, const qubo_options *opt,
+                      uint64_t *out_codes, void *out_E, size_t cap, uint64_t *out_count, qubo_result *info,
+                      void *stream);
+
+/*
  * Solve `count` independent instances of uneven size in one persistent launch (the map-reduce
  * of Sec. 3.3 across problems).  Instance i is the n[i] x n[i] row-major matrix starting
  * offsets[i] elements into Q_packed (host).  Per instance i the outputs are:

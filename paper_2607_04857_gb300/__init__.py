@@ -32,7 +32,7 @@ EXPORTS = (
     "qubo_problem_fetch", "qubo_problem_destroy", "qubo_merge", "qubo_strerror", "qubo_abort",
     "qubo_abort_clear", "qubo_device_sm_count", "qubo_version", "qubo_solve_noalloc",
     "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_batch_destroy",
-    "qubo_autotune", "qubo_autotune_batched", "qubo_autotune_clear",
+    "qubo_autotune", "qubo_autotune_batched", "qubo_autotune_clear", "qubo_solve_window",
 )
 NOALLOC_MAX_N = 40
 NOALLOC_MAX_TIES = 4096
@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH):
     lib.qubo_batch_destroy.argtypes = [P]
     lib.qubo_batch_destroy.restype = None
     lib.qubo_autotune.argtypes = [P, I, I, I, P]
+    lib.qubo_solve_window.argtypes = [P, I, I, ctypes.c_double, P, P, P, SZ, P, P, P]
     lib.qubo_autotune_batched.argtypes = [P, P, P, I, I, P]
     lib.qubo_autotune_clear.restype = None
     lib.qubo_strerror.argtypes = [I]
@@ -125,7 +126,7 @@ def load_library(path: str = LIB_PATH):
     for name in ("qubo_solve", "qubo_solve_ex", "qubo_solve_batched", "qubo_problem_create", "qubo_problem_run",
                  "qubo_problem_fetch", "qubo_merge", "qubo_device_sm_count", "qubo_solve_noalloc",
                  "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_autotune",
-                 "qubo_autotune_batched"):
+                 "qubo_autotune_batched", "qubo_solve_window"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -325,6 +326,24 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+def solve_window(Q, window: float, cap: int = 1 << 16, fix_bits: int = 0, fix_value: int = 0, plain: bool = False,
+                 stream=None):
+    """Every state with E <= E_min + window in (E, code) order (qubo_solve_window).
+    Returns (count, codes, energies, info)."""
+    lib = load_library()
+    Qm, dt = as_qubo_matrix(Q)
+    isf = dt in (QUBO_F32, QUBO_F64)
+    o = Options(fix_bits=fix_bits, fix_value=fix_value, flags=QUBO_FLAG_PLAIN if plain else 0)
+    codes = np.zeros(max(cap, 1), dtype=np.uint64)
+    E = np.zeros(max(cap, 1), dtype=np.float64 if isf else np.int64)
+    cnt = np.zeros(1, dtype=np.uint64)
+    info = ResultInfo()
+    _check(lib.qubo_solve_window(_ptr(Qm), Qm.shape[0], dt, float(window), ctypes.byref(o), _ptr(codes), _ptr(E), cap,
+                                 _ptr(cnt), ctypes.byref(info), _stream_ptr(stream)), "qubo_solve_window")
+    k = int(info.n_written)
+    return int(cnt[0]), codes[:k].copy(), E[:k].copy(), info.as_dict()
 
 
 def solve_batched(Qs, topk: int = 0, states_cap: int = 64, stream=None) -> list[Result]:

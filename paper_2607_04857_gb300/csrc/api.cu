@@ -308,6 +308,9 @@ struct Part {
     uint64_t scanned = 0, candidates = 0;
     double drift = 0.0, err = 0.0;
     bool overflow = false;
+    // energy-window mode: every state with E <= min + window, (E, code) ascending (energies as
+    // double; integer energies are exact in double below 2^53)
+    std::vector<std::pair<double, uint64_t>> win;
 };
 
 bool part_less_min(const Part &a, const Part &b)
@@ -356,6 +359,20 @@ Part merge_parts(const Part &a, const Part &b, size_t cap, int K)
     if ((int)o.topi.size() > K)
         o.topi.resize(K);
     return o;
+}
+
+// Window lists of disjoint parts: union, then keep E <= merged minimum + window.  Each part's list
+// holds every state of the part with E <= (its minimum) + window, a superset of its states within
+// the merged window because the merged minimum is not larger.
+void merge_windows(const Part &a, const Part &b, double window, Part &o)
+{
+    o.win.resize(a.win.size() + b.win.size());
+    std::merge(a.win.begin(), a.win.end(), b.win.begin(), b.win.end(), o.win.begin());
+    const double lim = o.min_f + window;
+    size_t k = 0;
+    while (k < o.win.size() && o.win[k].first <= lim)
+        ++k;
+    o.win.resize(k);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -626,6 +643,7 @@ struct Job {
     uint64_t h2d = 0, d2h = 0;
     double scan_seconds = 0.0;
     uint64_t total_items = 0;
+    double window = -1.0;  // >= 0: energy-window mode (single instance)
 };
 
 int job_layout(Job &j)
@@ -815,6 +833,8 @@ int job_enqueue_scan(Workspace &ws, Job &j, const void *state_init = nullptr)
     a.nrec = (unsigned long long *)(dev + j.off_ctr) + 1;
     a.abort_flag = ws.d_abort;
     a.margin = (j.acc == ACC_F32 || j.acc == ACC_F64) ? j.margin : 0.0;
+    if (j.window >= 0.0)  // record everything within the window of the running minimum
+        a.margin += (j.acc == ACC_F32 || j.acc == ACC_F64) ? j.window : std::floor(j.window);
     a.one = 1;
     a.zero = 0;
     CK(launch_scan(j.acc, a, j.blocks, j.variant, s));
@@ -975,12 +995,30 @@ int job_finish(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seco
         P <<= 1;
     if ((st = job_enqueue_finalize(ws, j, cnt, P)))
         return st;
+    std::vector<Rec> sorted;
+    if (j.window >= 0.0 && cnt) {
+        sorted.resize(cnt);
+        CK(cudaMemcpyAsync(sorted.data(), ws.d_rec, sizeof(Rec) * cnt, cudaMemcpyDeviceToHost, j.stream));
+        j.d2h += sizeof(Rec) * cnt;
+    }
     CK(cudaStreamSynchronize(j.stream));
     job_unpack(ws, j, parts, gpu_seconds);
+    if (j.window >= 0.0 && !parts.empty() && parts[0].has) {
+        Part &p = parts[0];
+        const bool fl = j.acc == ACC_F32 || j.acc == ACC_F64;
+        const double lim = p.min_f + j.window;
+        for (const Rec &r : sorted) {
+            const double e = fl ? bits_to_double(r.e) : (double)r.e;
+            if (e > lim)
+                break;
+            p.win.emplace_back(e, r.key);
+        }
+    }
     return j.aborted ? QUBO_ERR_TIMEOUT : QUBO_OK;
 }
 
 struct SolveCfg {
+    double window = -1.0;
     int K = 0;
     size_t cap = 0;
     uint32_t flags = 0;
@@ -1029,6 +1067,7 @@ int solve_range(Workspace &ws, HostInst &h, int fix_bits, uint64_t fix_value, co
     j.time_limit = t_deadline > 0 ? std::max(1e-3, t_deadline - now_s()) : 0.0;
     j.variant = c.variant;
     j.stream = stream;
+    j.window = c.window;
     if ((st = job_launch(ws, j)))
         return st;
     std::vector<Part> parts;
@@ -1050,6 +1089,8 @@ int solve_range(Workspace &ws, HostInst &h, int fix_bits, uint64_t fix_value, co
     if ((st = solve_range(ws, h, fix_bits + 1, (fix_value << 1) | 1, c, stream, b, stats, t_deadline)))
         return st;
     out = merge_parts(a, b, c.cap, c.K);
+    if (c.window >= 0.0)
+        merge_windows(a, b, c.window, out);
     return QUBO_OK;
 }
 
@@ -1129,9 +1170,10 @@ int check_opts(const qubo_options *o, size_t states_cap, const uint64_t *out_sta
 }
 
 int solve_one(Workspace &ws, HostInst &h, const qubo_options &o, size_t states_cap, cudaStream_t stream, Part &p,
-              SolveStats &stats)
+              SolveStats &stats, double window = -1.0)
 {
     SolveCfg c;
+    c.window = window;
     c.K = o.topk;
     c.cap = states_cap;
     c.flags = o.flags;
@@ -1396,6 +1438,57 @@ int qubo_solve_ex(const void *Q_host, int n, qubo_dtype dtype, const qubo_option
     fill_outputs(h, p, o.topk, states_cap, out_min, out_states, out_topk, out_topk_E, info);
     fill_plan_info(h, stats, t0, info);
     return p.n_ties > states_cap ? QUBO_TRUNCATED : QUBO_OK;
+}
+
+int qubo_solve_window(const void *Q_host, int n, qubo_dtype dtype, double window, const qubo_options *opt,
+                      uint64_t *out_codes, void *out_E, size_t cap, uint64_t *out_count, qubo_result *info,
+                      void *stream)
+{
+    const double t0 = now_s();
+    qubo_options o{};
+    if (opt)
+        o = *opt;
+    o.topk = 0;
+    if (!(window >= 0.0) || !std::isfinite(window) || !out_count || (cap > 0 && (!out_codes || !out_E)))
+        return QUBO_ERR_ARG;
+    HostInst h;
+    int st = prepare(Q_host, n, dtype, o.flags, h);
+    if (st)
+        return st;
+    if (o.fix_bits < 0 || o.fix_bits > n)
+        return QUBO_ERR_ARG;
+    if (!h.is_float && window >= 1073741824.0)
+        return QUBO_ERR_ARG;  // the int32 threshold arithmetic bounds the window
+    if (!h.is_float && h.acc == ACC_I32 && h.beta + window >= 1073741824.0)
+        h.acc = ACC_I64;
+    Workspace *ws = nullptr;
+    if ((st = resolve_device(&ws)))
+        return st;
+    std::lock_guard<std::mutex> lk(ws->mu);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if ((st = ws->init(dev)))
+        return st;
+    Part p;
+    SolveStats stats;
+    if ((st = solve_one(*ws, h, o, 0, (cudaStream_t)stream, p, stats, window)))
+        return st;
+    if (info)
+        std::memset(info, 0, sizeof(*info));
+    fill_outputs(h, p, 0, 0, nullptr, nullptr, nullptr, nullptr, info);
+    fill_plan_info(h, stats, t0, info);
+    *out_count = p.win.size();
+    const size_t nw = std::min(cap, p.win.size());
+    for (size_t t = 0; t < nw; ++t) {
+        out_codes[t] = p.win[t].second;
+        if (h.is_float)
+            ((double *)out_E)[t] = p.win[t].first;
+        else
+            ((int64_t *)out_E)[t] = (int64_t)p.win[t].first;
+    }
+    if (info)
+        info->n_written = nw;
+    return p.win.size() > cap ? QUBO_TRUNCATED : QUBO_OK;
 }
 
 int qubo_solve(const void *Q_host, int n, qubo_dtype dtype, int split_k, int topk, void *out_min,

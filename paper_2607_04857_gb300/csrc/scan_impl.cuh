@@ -262,6 +262,8 @@ __device__ void small_unit(const ScanArgs &a, const Inst &d, int inst, int lane)
     using F = typename Tr<T>::F;
     const int n = d.n;
     const F *W = field_matrix<T>(d);
+    // states above the run's threshold (plus margin) cannot be in the answer
+    const double lim = (double)Tr<T>::thr_load(a.state + inst) + a.margin;
     for (uint64_t s = lane; s < d.sub_count; s += 32) {
         const uint64_t x = d.sub_base + s;
         F acc = 0;
@@ -273,7 +275,8 @@ __device__ void small_unit(const ScanArgs &a, const Inst &d, int inst, int lane)
                 if ((x >> j) & 1)
                     acc += W[i * n + j];
         }
-        record<T>(a, inst, (T)acc, x);
+        if ((double)acc <= lim + (Tr<T>::kFloat ? 1e-6 * (1.0 + fabs(lim)) : 0.0))
+            record<T>(a, inst, (T)acc, x);
     }
     if (lane == 0)
         atomicAdd(&a.state[inst].scanned, (unsigned long long)d.sub_count);

@@ -371,3 +371,46 @@ def test_autotune_batched(q):
             check_int(r, oracle.solve(Q.astype(np.int32), topk=2, cap=64))
     finally:
         q.autotune_clear()
+
+
+# --- low-energy window (every state within a band above the minimum) --------------------------
+
+def oracle_window(Q, window):
+    o = oracle.solve(Q, topk=4096, cap=1)
+    sel = o.topk_E <= o.min + window
+    assert not sel.all() or len(sel) < 4096, "window too wide for the oracle check"
+    return int(sel.sum()), o.topk[sel], o.topk_E[sel]
+
+
+@pytest.mark.parametrize("n,window", [(12, 40), (16, 150), (21, 60), (24, 0)])
+def test_window_matches_oracle(q, n, window):
+    Q = wl.upper_int(n, -50, 50, seed=400 + n)
+    cnt, codes, E, info = q.solve_window(Q, window)
+    ocnt, ocodes, oE = oracle_window(Q, window)
+    assert cnt == ocnt and np.array_equal(codes, ocodes) and np.array_equal(E, oE)
+
+
+def test_window_float(q):
+    Q = wl.sk_float32(20, seed=41)
+    cnt, codes, E, info = q.solve_window(Q, 0.5)
+    ocnt, ocodes, oE = oracle_window(Q, 0.5)
+    assert cnt == ocnt and np.array_equal(codes, ocodes)
+    assert np.allclose(E, oE, rtol=FLOAT_RTOL, atol=FLOAT_RTOL)
+
+
+def test_window_through_overflow_split(q):
+    """175 states in the window and room for 128 candidates: the sub-cube splits and merges."""
+    code = (
+        "import numpy as np, oracle, paper_2607_04857_gb300 as q;"
+        "from paper_2607_04857_gb300 import workloads as wl;"
+        "Q = wl.upper_int(18, -20, 20, seed=5);"
+        "cnt, codes, E, info = q.solve_window(Q, 80, cap=5000);"
+        "o = oracle.solve(Q, topk=4096, cap=1); sel = o.topk_E <= o.min + 80;"
+        "assert sel.sum() < 4096 and cnt == sel.sum(), (cnt, sel.sum());"
+        "assert np.array_equal(codes, o.topk[sel]) and np.array_equal(E, o.topk_E[sel]);"
+        "assert info['passes'] > 1, info"
+    )
+    env = dict(os.environ, QUBO_MAX_RECORDS="128")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stdout + res.stderr
