@@ -137,7 +137,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("scan_impl.cuh", "scan_i32.cu", "scan_f32.cu", "internal.h"):
+    for f in ("scan_impl.cuh", "scan_i32.cu", "scan_f32.cu", "scan_i32f.cu", "internal.h"):
         with open(os.path.join(ROOT, "paper_2607_04857_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -426,7 +426,7 @@ def main():
             "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x {clk_max:.0f} MHz; 2 ops/state (add + min)"}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (sms * LANES_PER_SM * clocks["sm_mhz"] * 1e-3)
-    acc = "i32" if W["dtype"] == "int32" else "f32"
+    acc = infos[0].get("acc", "i32")
     prof = profile_counters(acc)
     if prof:
         # DRAM bytes per launch, scaled from the captured launch by the states it processed

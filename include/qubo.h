@@ -34,8 +34,10 @@ extern "C" {
 /* Element type of Q. */
 typedef enum { QUBO_I16 = 1, QUBO_I32 = 2, QUBO_F32 = 3, QUBO_F64 = 4 } qubo_dtype;
 
-/* Accumulator the scan ran in (reported in qubo_result.acc). */
-typedef enum { QUBO_ACC_I32 = 1, QUBO_ACC_I64 = 2, QUBO_ACC_F32 = 3, QUBO_ACC_F64 = 4 } qubo_acc;
+/* Accumulator the scan ran in (reported in qubo_result.acc).  QUBO_ACC_I32F: integer energies
+ * held exactly in FP32 lanes, chosen when every partial sum of the run's plan stays below 2^24
+ * in magnitude (results are exact integers, as with QUBO_ACC_I32). */
+typedef enum { QUBO_ACC_I32 = 1, QUBO_ACC_I64 = 2, QUBO_ACC_F32 = 3, QUBO_ACC_F64 = 4, QUBO_ACC_I32F = 5 } qubo_acc;
 
 typedef enum {
     QUBO_OK = 0,

@@ -58,6 +58,7 @@ struct HostInst {
     uint64_t unit_begin = 0, units = 0, sub_base = 0, sub_count = 0;
     uint64_t items = 0, states = 0;
     double thr0 = 0.0;  // initial threshold (a bound on the K-th lowest energy of the range)
+    int32_t clampC = 0; // ACC_I32F: threshold clamp
 };
 
 bool dtype_ok(qubo_dtype dt) { return dt == QUBO_I16 || dt == QUBO_I32 || dt == QUBO_F32 || dt == QUBO_F64; }
@@ -109,7 +110,7 @@ int prepare(const void *Q, int n, qubo_dtype dt, uint32_t flags, HostInst &h)
     return QUBO_OK;
 }
 
-int acc_bytes(Acc a) { return (a == ACC_I32 || a == ACC_F32) ? 4 : 8; }
+int acc_bytes(Acc a) { return (a == ACC_I32 || a == ACC_F32 || a == ACC_I32F) ? 4 : 8; }
 
 int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bits)
 {
@@ -152,6 +153,69 @@ int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bi
     h.unit_begin = fix_bits ? (fix_value << (k - fix_bits)) : 0;
     h.items = h.units;
     return QUBO_OK;
+}
+
+// Compiled scan variant: QUBO_SCAN_VARIANT overrides the measured default of the accumulator.
+int scan_variant(Acc acc = ACC_I32)
+{
+    const char *v = std::getenv("QUBO_SCAN_VARIANT");
+    if (v) {
+        const int x = std::atoi(v);
+        if (x >= 0 && x < kScanVariants)
+            return x;
+    }
+    return acc == ACC_F32 ? kDefaultVariantF32 : (acc == ACC_I32F ? kDefaultVariantI32F : kDefaultVariantI32);
+}
+
+// The variant a run uses: the caller's (tuned) choice, else the accumulator's default.
+int pick_variant(Acc acc, int requested) { return requested >= 0 ? requested : scan_variant(acc); }
+
+// Integer energies can be scanned exactly in FP32 lanes when every column energy, table row and
+// clamped threshold stays below 2^24 in magnitude.  With nf = B + L non-fixed variables, every
+// column value is a signed subset sum of the entries touching a non-fixed variable (S_nf bounds
+// it) and every E_L value one of the entries among walked variables (S_ww); the per-step
+// threshold is clamped to +-(S_nf + S_ww + 1), which leaves every decision unchanged, so
+// |threshold - E_L| <= S_nf + 2 S_ww + 1 must stay below 2^24.
+bool i32f_exact(const HostInst &h, int32_t *clampC)
+{
+    if (h.small || h.is_float)
+        return false;
+    const int n = h.n, nf = h.B + h.L;
+    double s_nf = 0.0, s_ww = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) {
+            const double a = std::fabs((double)h.Ui[(size_t)i * n + j]);
+            if (i < nf)
+                s_nf += a;
+            if (i >= h.B && j < nf)
+                s_ww += a;
+        }
+    if (s_nf + 2.0 * s_ww + 2.0 >= 16777216.0)
+        return false;
+    *clampC = (int32_t)(s_nf + s_ww + 1.0);
+    return true;
+}
+
+bool i32f_allowed()
+{
+    const char *v = std::getenv("QUBO_NO_I32F");
+    return !(v && v[0] == '1');
+}
+
+// Accumulator, kernel variant and plan of one run.  Integer instances scan in FP32 lanes when
+// the plan keeps every value exact (and the plain form was not asked for).
+int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bits, int variant_req,
+             uint32_t flags)
+{
+    if ((h.acc == ACC_I32 || h.acc == ACC_I32F) && !(flags & QUBO_FLAG_PLAIN)) {
+        h.acc = ACC_I32F;
+        h.variant = pick_variant(h.acc, variant_req);
+        if (!i32f_allowed() || plan(h, fix_bits, fix_value, split_k, walk_bits) != QUBO_OK ||
+            !i32f_exact(h, &h.clampC))
+            h.acc = ACC_I32;
+    }
+    h.variant = acc_bytes(h.acc) == 4 ? pick_variant(h.acc, variant_req) : 0;
+    return plan(h, fix_bits, fix_value, split_k, walk_bits);
 }
 
 // Upper bound on the K-th lowest energy (with multiplicity) of the run's sub-cube: the K-th lowest
@@ -268,7 +332,8 @@ double ubits_to_double(unsigned long long b)
 unsigned long long encode_thr(Acc acc, double t)
 {
     switch (acc) {
-    case ACC_I32: return (unsigned long long)(uint32_t)(int32_t)t;
+    case ACC_I32:
+    case ACC_I32F: return (unsigned long long)(uint32_t)(int32_t)t;
     case ACC_I64: return (unsigned long long)(int64_t)t;
     case ACC_F32: {
         float f = (float)t;
@@ -284,7 +349,8 @@ unsigned long long encode_thr(Acc acc, double t)
 unsigned long long encode_max(Acc acc)
 {
     switch (acc) {
-    case ACC_I32: return (unsigned long long)(uint32_t)INT32_MAX;
+    case ACC_I32:
+    case ACC_I32F: return (unsigned long long)(uint32_t)INT32_MAX;
     case ACC_I64: return (unsigned long long)INT64_MAX;
     case ACC_F32: return ord32h(INFINITY);
     case ACC_F64: return ord64h(INFINITY);
@@ -545,17 +611,7 @@ unsigned long long record_capacity()
     return kDefaultRecCap;
 }
 
-// Compiled scan variant: QUBO_SCAN_VARIANT overrides the measured default of the accumulator.
-int scan_variant(Acc acc = ACC_I32)
-{
-    const char *v = std::getenv("QUBO_SCAN_VARIANT");
-    if (v) {
-        const int x = std::atoi(v);
-        if (x >= 0 && x < kScanVariants)
-            return x;
-    }
-    return acc == ACC_F32 ? kDefaultVariantF32 : kDefaultVariantI32;
-}
+
 
 // Plans installed by the autotuner: (device, accumulator, n) -> (variant, walk bits); n = 0 is
 // the entry used by batches.  Consulted when the caller fixes neither split_k nor walk_bits and
@@ -738,6 +794,7 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
         d.L = h.L;
         d.k = h.k;
         d.small = h.small;
+        d.clampC = h.clampC;
         d.unit_begin = h.unit_begin;
         d.units = h.units;
         d.sub_base = h.sub_base;
@@ -760,7 +817,7 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
             d.W64 = (const double *)(dev + j.off_W64[i]);
             d.U64 = (const double *)(dev + j.off_U64[i]);
         } else {
-            if (j.acc == ACC_I32) {
+            if (j.acc == ACC_I32 || j.acc == ACC_I32F) {
                 int32_t *W = (int32_t *)(up + j.off_W[i]);
                 for (int a = 0; a < h.n; ++a)
                     for (int b = 0; b < h.n; ++b)
@@ -1025,7 +1082,7 @@ struct SolveCfg {
     double margin = kDefaultMargin;
     double time_limit = 0.0;
     int split_k = 0, walk_bits = 0;
-    int variant = 0;
+    int variant = -1;  // < 0: the accumulator's default (or QUBO_SCAN_VARIANT)
 };
 
 struct SolveStats {
@@ -1053,8 +1110,7 @@ struct SolveStats {
 int solve_range(Workspace &ws, HostInst &h, int fix_bits, uint64_t fix_value, const SolveCfg &c,
                 cudaStream_t stream, Part &out, SolveStats &stats, double t_deadline)
 {
-    h.variant = acc_bytes(h.acc) == 4 ? c.variant : 0;
-    int st = plan(h, fix_bits, fix_value, c.split_k, c.walk_bits);
+    int st = plan_run(h, fix_bits, fix_value, c.split_k, c.walk_bits, c.variant, c.flags);
     if (st)
         return st;
     h.thr0 = threshold_bound(h, std::max(1, c.K));
@@ -1065,7 +1121,7 @@ int solve_range(Workspace &ws, HostInst &h, int fix_bits, uint64_t fix_value, co
     j.cap = c.cap;
     j.margin = c.margin;
     j.time_limit = t_deadline > 0 ? std::max(1e-3, t_deadline - now_s()) : 0.0;
-    j.variant = c.variant;
+    j.variant = h.variant;
     j.stream = stream;
     j.window = c.window;
     if ((st = job_launch(ws, j)))
@@ -1181,7 +1237,8 @@ int solve_one(Workspace &ws, HostInst &h, const qubo_options &o, size_t states_c
     c.time_limit = o.time_limit_s;
     c.split_k = o.split_k;
     c.walk_bits = o.walk_bits;
-    c.variant = scan_variant(h.acc);
+    c.variant = std::getenv("QUBO_SCAN_VARIANT") ? scan_variant(h.acc) : -1;
+    c.flags = o.flags;
     if (o.split_k <= 0 && o.walk_bits <= 0 && acc_bytes(h.acc) == 4) {
         int tv = 0, tw = 0;
         if (tuned_plan(h.acc, h.n, &tv, &tw)) {
@@ -1302,6 +1359,28 @@ int batch_prepare(const void *Q_packed, const int *n, const size_t *offsets, int
     for (int i = 0; i < count; ++i)
         if (pst[i])
             return pst[i];
+    if (acc == ACC_I32 && i32f_allowed()) {
+        // one accumulator for the batch: FP32 lanes when every instance's plan is exact
+        std::vector<HostInst> alt = hs;
+        const int v2 = pick_variant(ACC_I32F, -1);
+        bool all = true;
+        for (auto &h : alt) {
+            h.acc = ACC_I32F;
+            h.variant = v2;
+            const int B = suffix_bits(4, v2);
+            const int walk = h.n - B >= kRegRows + 1 ? std::min(kDefaultMaxWalkBits, h.n - B) : 0;
+            if (plan(h, 0, 0, 0, walk) != QUBO_OK || (!h.small && !i32f_exact(h, &h.clampC))) {
+                all = false;
+                break;
+            }
+        }
+        if (all) {
+            for (size_t i = 0; i < hs.size(); ++i) {
+                alt[i].thr0 = hs[i].thr0;
+                hs[i] = std::move(alt[i]);
+            }
+        }
+    }
     // longest work first (LPT order) so the tail of the persistent launch is short
     order.resize(count);
     for (int i = 0; i < count; ++i)
@@ -1618,8 +1697,8 @@ int qubo_problem_run(qubo_problem *p, int fix_bits, uint64_t fix_value, void *st
     p->fix_bits = fix_bits;
     p->fix_value = fix_value;
     p->stream = (cudaStream_t)stream;
-    p->h.variant = acc_bytes(p->h.acc) == 4 ? scan_variant(p->h.acc) : 0;
-    int st = plan(p->h, fix_bits, fix_value, p->opt.split_k, p->opt.walk_bits);
+    int st = plan_run(p->h, fix_bits, fix_value, p->opt.split_k, p->opt.walk_bits,
+                      std::getenv("QUBO_SCAN_VARIANT") ? scan_variant(p->h.acc) : -1, p->opt.flags);
     if (st)
         return st;
     p->h.thr0 = threshold_bound(p->h, std::max(1, p->opt.topk));

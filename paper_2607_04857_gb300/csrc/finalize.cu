@@ -14,6 +14,7 @@ cudaError_t launch_tables(Acc acc, const Inst *d_inst, int n_inst, int max_entri
     case ACC_I64: return launch_tables_t<int64_t>(d_inst, n_inst, max_entries, s);
     case ACC_F32: return launch_tables_t<float>(d_inst, n_inst, max_entries, s);
     case ACC_F64: return launch_tables_t<double>(d_inst, n_inst, max_entries, s);
+    case ACC_I32F: return launch_tables_t<i32f>(d_inst, n_inst, max_entries, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -25,6 +26,7 @@ cudaError_t launch_scan(Acc acc, const ScanArgs &a, int blocks, int variant, cud
     case ACC_I64: return launch_scan_t<int64_t>(a, blocks, variant, s);
     case ACC_F32: return launch_scan_t<float>(a, blocks, variant, s);
     case ACC_F64: return launch_scan_t<double>(a, blocks, variant, s);
+    case ACC_I32F: return launch_scan_t<i32f>(a, blocks, variant, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -36,6 +38,7 @@ int scan_blocks_per_sm(Acc acc, bool k1, int variant)
     case ACC_I64: return scan_blocks_per_sm_t<int64_t>(k1, variant);
     case ACC_F32: return scan_blocks_per_sm_t<float>(k1, variant);
     case ACC_F64: return scan_blocks_per_sm_t<double>(k1, variant);
+    case ACC_I32F: return scan_blocks_per_sm_t<i32f>(k1, variant);
     }
     return -1;
 }

@@ -6,7 +6,8 @@
 
 namespace qubo {
 
-enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4 };
+// ACC_I32F: integer energies scanned exactly in FP32 lanes (partial sums below 2^24).
+enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4, ACC_I32F = 5 };
 
 // Walked prefix rows kept in registers by the scan kernel (the largest of the compiled
 // variants); the inner loop is unrolled over 2^(RC+1) Gray steps so that every register-row
@@ -26,6 +27,7 @@ constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 2, 3};
 // Default variant per 4-byte accumulator (measured on GB300; see the profiles).
 constexpr int kDefaultVariantI32 = 3;
 constexpr int kDefaultVariantF32 = 0;
+constexpr int kDefaultVariantI32F = 0;
 // Threads per block of the scan kernel (4 warps; every warp owns one work unit at a time).
 constexpr int kScanThreads = 128;
 // Longest Gray walk inside one work unit (also the FP32 re-anchoring period).
@@ -48,7 +50,7 @@ struct Inst {
     int32_t L;          // walked prefix bits
     int32_t k;          // fixed bits per unit (n = B + L + k on the tabled path)
     int32_t small;      // 1: no split, every state evaluated directly
-    int32_t pad0;
+    int32_t clampC;     // ACC_I32F: clamp of the per-step threshold (max |column| + max |E_L| + 1)
     uint64_t unit_begin;  // first unit (value of the fixed bits) of this run
     uint64_t units;       // units in this run
     uint64_t sub_base;    // small path: first code
@@ -112,6 +114,8 @@ constexpr int suffix_bits(int bytes, int variant = 0)
 {
     return cols_per_thread(bytes, variant) == 32 ? 10 : 9;
 }
+
+struct i32f;  // tag of the integer-in-FP32 accumulator (scan_impl.cuh)
 
 // ---- launchers (scan_*.cu, one translation unit per accumulator type) -------------------------
 template <class T>

@@ -13,6 +13,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <utility>
 
 #include "internal.h"
@@ -41,11 +42,21 @@ __device__ __forceinline__ double unord64(unsigned long long o)
 }
 
 // ---- accumulator traits ----------------------------------------------------------------------
+// TC: type of the column energies and table rows; TP: type of the prefix energy, thresholds and
+// recorded energies; F: table-build precision; FU: per-unit field precision.
 template <class T>
 struct Tr;
 
+// Integer instances whose partial sums stay below 2^24 in magnitude: columns and tables are FP32
+// holding exact integers (FP32 adds use both halves of the fused multiply-add pipe), while the
+// prefix energy and thresholds stay int32.
+struct i32f {};
+
 template <>
 struct Tr<int32_t> {
+    using TC = int32_t;
+    using TP = int32_t;
+    static constexpr bool kIntInFloat = false;
     using F = int32_t;   // precision of the tables
     using FU = int32_t;  // precision of the per-unit fields
     using Vec = int4;
@@ -61,6 +72,9 @@ struct Tr<int32_t> {
 
 template <>
 struct Tr<int64_t> {
+    using TC = int64_t;
+    using TP = int64_t;
+    static constexpr bool kIntInFloat = false;
     using F = int64_t;
     using FU = int64_t;
     using Vec = longlong2;
@@ -76,6 +90,9 @@ struct Tr<int64_t> {
 
 template <>
 struct Tr<float> {
+    using TC = float;
+    using TP = float;
+    static constexpr bool kIntInFloat = false;
     using F = double;
     using FU = float;
     using Vec = float4;
@@ -96,6 +113,9 @@ struct Tr<float> {
 
 template <>
 struct Tr<double> {
+    using TC = double;
+    using TP = double;
+    static constexpr bool kIntInFloat = false;
     using F = double;
     using FU = double;
     using Vec = double2;
@@ -113,6 +133,35 @@ struct Tr<double> {
 };
 
 // Symmetric coupling matrix in the table precision (tables) and in the unit-field precision.
+template <>
+struct Tr<i32f> {
+    using TC = float;
+    using TP = int32_t;
+    static constexpr bool kIntInFloat = true;
+    using F = int32_t;
+    using FU = int32_t;
+    using Vec = float4;
+    static constexpr int V = 4;
+    static constexpr bool kFloat = false;
+    __device__ static int32_t thr_load(const InstState *s) { return *(const volatile int32_t *)&s->thr; }
+    __device__ static void thr_min(InstState *s, int32_t v) { atomicMin((int *)&s->thr, v); }
+    __device__ static void gmin_min(InstState *s, int32_t v) { atomicMin((int *)&s->gmin, v); }
+    __device__ static int64_t bits(int32_t v) { return v; }
+    __device__ static int32_t tmin(int32_t a, int32_t b) { return min(a, b); }
+};
+
+// Column value of a prefix-type threshold.  For FP32 columns holding integers the threshold is
+// clamped to +-C first: beyond C every column (|column| <= C - 1 - max|E_L|) is decided the same
+// way, and within it the value is exact in FP32.
+template <class T>
+__device__ __forceinline__ typename Tr<T>::TC to_col(typename Tr<T>::TP v, int32_t clampC)
+{
+    if constexpr (Tr<T>::kIntInFloat)
+        return (float)max(-clampC, min(clampC, v));
+    else
+        return v;
+}
+
 template <class T>
 __device__ __forceinline__ const typename Tr<T>::F *field_matrix(const Inst &d)
 {
@@ -132,11 +181,22 @@ __device__ __forceinline__ void vsplit(const float4 &v, float (&o)[4]) { o[0] = 
 __device__ __forceinline__ void vsplit(const longlong2 &v, int64_t (&o)[2]) { o[0] = v.x; o[1] = v.y; }
 __device__ __forceinline__ void vsplit(const double2 &v, double (&o)[2]) { o[0] = v.x; o[1] = v.y; }
 
-// 16-byte read-only load of V consecutive table entries.
-template <class T>
-__device__ __forceinline__ void vload(const T *p, T (&o)[Tr<T>::V])
+// 16-byte read-only load of consecutive table entries (4 x 4 bytes or 2 x 8 bytes).
+template <class E>
+struct VecOf;
+template <>
+struct VecOf<int32_t> { using type = int4; static constexpr int V = 4; };
+template <>
+struct VecOf<float> { using type = float4; static constexpr int V = 4; };
+template <>
+struct VecOf<int64_t> { using type = longlong2; static constexpr int V = 2; };
+template <>
+struct VecOf<double> { using type = double2; static constexpr int V = 2; };
+
+template <class E>
+__device__ __forceinline__ void vload(const E *p, E (&o)[VecOf<E>::V])
 {
-    vsplit(__ldg((const typename Tr<T>::Vec *)p), o);
+    vsplit(__ldg((const typename VecOf<E>::type *)p), o);
 }
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
@@ -158,6 +218,20 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+__device__ __forceinline__ int32_t emin(int32_t a, int32_t b) { return min(a, b); }
+__device__ __forceinline__ int64_t emin(int64_t a, int64_t b) { return min(a, b); }
+__device__ __forceinline__ float emin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double emin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ int32_t emin3(int32_t a, int32_t b, int32_t c) { return __vimin3_s32(a, b, c); }
+__device__ __forceinline__ int64_t emin3(int64_t a, int64_t b, int64_t c) { return min(min(a, b), c); }
+__device__ __forceinline__ float emin3(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ double emin3(double a, double b, double c) { return fmin(fmin(a, b), c); }
+
 // min over N register values: a tree of 2-input (MINM == 2) or 3-input (MINM == 3) mins.
 template <class T, int MINM, int N>
 __device__ __forceinline__ T tree_min(const T (&E)[N])
@@ -169,7 +243,7 @@ __device__ __forceinline__ T tree_min(const T (&E)[N])
         T m[M];
 #pragma unroll
         for (int q = 0; q < N / 3; ++q)
-            m[q] = Tr<T>::tmin3(E[3 * q], E[3 * q + 1], E[3 * q + 2]);
+            m[q] = emin3(E[3 * q], E[3 * q + 1], E[3 * q + 2]);
 #pragma unroll
         for (int q = 0; q < N % 3; ++q)
             m[N / 3 + q] = E[3 * (N / 3) + q];
@@ -179,7 +253,7 @@ __device__ __forceinline__ T tree_min(const T (&E)[N])
         T m[M];
 #pragma unroll
         for (int q = 0; q < N / 2; ++q)
-            m[q] = Tr<T>::tmin(E[2 * q], E[2 * q + 1]);
+            m[q] = emin(E[2 * q], E[2 * q + 1]);
         if constexpr (N % 2)
             m[M - 1] = E[N - 1];
         return tree_min<T, MINM, M>(m);
@@ -188,7 +262,7 @@ __device__ __forceinline__ T tree_min(const T (&E)[N])
 
 // Offer one state to the candidate buffer.
 template <class T>
-__device__ __forceinline__ void record(const ScanArgs &a, int inst, T E, uint64_t code)
+__device__ __forceinline__ void record(const ScanArgs &a, int inst, typename Tr<T>::TP E, uint64_t code)
 {
     InstState *st = a.state + inst;
     atomicAdd(&st->nrec, 1ull);
@@ -229,7 +303,7 @@ __global__ void tables_kernel(const Inst *insts)
                     if ((j >> b2) & 1)
                         acc += W[b * n + b2];
             }
-            ((T *)d.Es)[j] = (T)acc;
+            ((typename Tr<T>::TC *)d.Es)[j] = (typename Tr<T>::TC)acc;
         } else if (idx < NB * (L + 1)) {  // M_int row r: coupling of walked variable r to pattern j
             const long r = (idx - NB) / NB, j = (idx - NB) % NB;
             const int vr = B + (int)r;
@@ -237,7 +311,7 @@ __global__ void tables_kernel(const Inst *insts)
             for (int b = 0; b < B; ++b)
                 if ((j >> b) & 1)
                     acc += W[vr * n + b];
-            ((T *)d.M)[r * NB + j] = (T)acc;
+            ((typename Tr<T>::TC *)d.M)[r * NB + j] = (typename Tr<T>::TC)acc;
         } else {  // E_L(g(i)): energy of the i-th walked pattern, stored in walk order
             const long i = idx - NB * (L + 1);
             const long g = i ^ (i >> 1);
@@ -250,7 +324,7 @@ __global__ void tables_kernel(const Inst *insts)
                     if ((g >> r2) & 1)
                         acc += W[(B + r) * n + (B + r2)];
             }
-            ((T *)d.EL)[i] = (T)acc;
+            ((typename Tr<T>::TC *)d.EL)[i] = (typename Tr<T>::TC)acc;
         }
     }
 }
@@ -276,7 +350,7 @@ __device__ void small_unit(const ScanArgs &a, const Inst &d, int inst, int lane)
                     acc += W[i * n + j];
         }
         if ((double)acc <= lim + (Tr<T>::kFloat ? 1e-6 * (1.0 + fabs(lim)) : 0.0))
-            record<T>(a, inst, (T)acc, x);
+            record<T>(a, inst, (typename Tr<T>::TP)acc, x);
     }
     if (lane == 0)
         atomicAdd(&a.state[inst].scanned, (unsigned long long)d.sub_count);
@@ -347,13 +421,18 @@ __device__ __forceinline__ void column_fields(F f0, int lane, F &lin_t, F (&lin_
 
 // ---- one work unit: all 2^(B+L) states with fixed bits x_f = unit --------------------------------
 // ADDM == 1 issues the integer adds as multiply-adds by a runtime +-1 (fused multiply-add
-// pipe) so that the integer ALU pipe is left to the mins; MINM selects 2- or 3-input mins.
+// pipe) so that the integer ALU pipe is left to the mins; ADDM == 2 sends a quarter of them to
+// the ALU pipe as 3-input adds; MINM selects 2- or 3-input mins.
 template <class T, int S, int RC, bool K1, int ADDM, int MINM>
-__device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t unit, T &Treg,
-                                          int lane, T *stage, T *wsm)
+__device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t unit,
+                                          typename Tr<T>::TP &Treg, int lane, typename Tr<T>::TC *stage,
+                                          typename Tr<T>::TP *wsm)
 {
     using F = typename Tr<T>::FU;
-    constexpr int V = Tr<T>::V;
+    using TC = typename Tr<T>::TC;
+    using TP = typename Tr<T>::TP;
+    constexpr bool kIntCols = std::is_integral_v<TC>;
+    constexpr int V = VecOf<TC>::V;
     constexpr int G = S / V;
     constexpr int LOGV = ilog2c(V);
     constexpr int LOGG = ilog2c(G);
@@ -370,7 +449,7 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
     // Walked-row couplings w_r, read at every flip of a row >= RC.
     __syncwarp();
     if (lane >= B && lane < BL)
-        wsm[lane - B] = (T)f0;
+        wsm[lane - B] = (TP)f0;
     __syncwarp();
 
     // Column fields: lin(j) = sum_b j_b v_b; bits of j are [e | lane | g] (LOGV, 5, LOGG bits).
@@ -378,66 +457,70 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
     column_fields<F, V, G>(f0, lane, lin_t, lin_e, lin_g);
 
     // Initial suffix-dependent energies (walked bits all zero): E_s(j) + lin(j).
-    const T *Es = (const T *)d.Es;
-    T E[S];
+    const TC *Es = (const TC *)d.Es;
+    TC E[S];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        T ev[V];
-        vload<T>(Es + (g * 32 + lane) * V, ev);
+        TC ev[V];
+        vload<TC>(Es + (g * 32 + lane) * V, ev);
 #pragma unroll
         for (int e = 0; e < V; ++e)
-            E[g * V + e] = (T)((F)ev[e] + (lin_e[e] + lin_t + lin_g[g]));
+            E[g * V + e] = (TC)((F)ev[e] + (lin_e[e] + lin_t + lin_g[g]));
     }
 
     // Register rows r < RC: M_r[j] + w_r, the walked-fixed coupling of row r folded in.
-    const T *Mt = (const T *)d.M;
-    T Mr[RC][S];
+    const TC *Mt = (const TC *)d.M;
+    TC Mr[RC][S];
 #pragma unroll
     for (int r = 0; r < RC; ++r) {
         const F wr = __shfl_sync(kFull, f0, B + r);
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            T mv[V];
-            vload<T>(Mt + (size_t)r * NB + (g * 32 + lane) * V, mv);
+            TC mv[V];
+            vload<TC>(Mt + (size_t)r * NB + (g * 32 + lane) * V, mv);
 #pragma unroll
             for (int e = 0; e < V; ++e)
-                Mr[r][g * V + e] = (T)((F)mv[e] + wr);
+                Mr[r][g * V + e] = (TC)((F)mv[e] + wr);
         }
     }
 
-    // Threshold: a state is recorded when its energy is <= Treg (+ margin for float scans).
+    // Threshold: a state is recorded when its energy is <= Treg (+ margin).
     {
-        const T tg = Tr<T>::thr_load(st);
-        Treg = K1 ? Tr<T>::tmin(Treg, tg) : tg;
+        const TP tg = Tr<T>::thr_load(st);
+        Treg = K1 ? min(Treg, tg) : tg;
     }
-    const T mu = (T)a.margin;
-    T P = (T)cx;  // c(x_f) + coupling of the walked rows >= RC that are set
-    T u = Treg + mu - P;
+    const TP mu = (TP)a.margin;
+    const int32_t clampC = d.clampC;
+    TP P = (TP)cx;  // c(x_f) + coupling of the walked rows >= RC that are set
+    TP u = Treg + mu - P;
+    TC uc = to_col<T>(u, clampC);
 
     // Flip of a walked row kk >= RC (row from memory, runtime sign).
-    auto high_flip = [&](int kk, T sg) {
-        const T *row = Mt + (size_t)kk * NB;
+    auto high_flip = [&](int kk, int sgn) {
+        const TC *row = Mt + (size_t)kk * NB;
+        const TC sg = (TC)sgn;
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            T mv[V];
-            vload<T>(row + (g * 32 + lane) * V, mv);
+            TC mv[V];
+            vload<TC>(row + (g * 32 + lane) * V, mv);
 #pragma unroll
             for (int e = 0; e < V; ++e)
                 E[g * V + e] = E[g * V + e] + sg * mv[e];
         }
-        P = P + sg * wsm[kk];
+        P = P + (TP)sgn * wsm[kk];
         u = Treg + mu - P;
+        uc = to_col<T>(u, clampC);
     };
 
-    const T *ELp = (const T *)d.EL;
+    const TC *ELp = (const TC *)d.EL;
     const int nblk = 1 << (L - RC - 1);
     const uint64_t cbase = unit << BL;
 
     for (int blk = 0; blk < nblk; ++blk) {
         const int i0 = blk * BODY;
-        T elv[V];
+        TC elv[V];
         bool hit = false;
-        T Pmid = P;
+        TP Pmid = P;
         // Fast path: per step one add per column, a min over the columns and one compare whose
         // outcome is only OR-ed into `hit`, so consecutive steps can overlap freely.
         static_for<BODY>([&](auto pc) {
@@ -446,14 +529,14 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
                 constexpr int kk = ctzc(p);
                 if constexpr (kk < RC) {
                     constexpr bool neg = (p >> (kk + 1)) & 1;
-                    if constexpr (ADDM == 1 && !Tr<T>::kFloat) {
-                        const T mul = neg ? -(T)a.one : (T)a.one;
+                    if constexpr (ADDM == 1 && kIntCols) {
+                        const TC mul = neg ? -(TC)a.one : (TC)a.one;
 #pragma unroll
                         for (int q = 0; q < S; ++q)
                             E[q] = E[q] + Mr[kk][q] * mul;
-                    } else if constexpr (ADDM == 2 && !Tr<T>::kFloat) {
-                        const T mul = neg ? -(T)a.one : (T)a.one;
-                        const T z = (T)a.zero;
+                    } else if constexpr (ADDM == 2 && kIntCols) {
+                        const TC mul = neg ? -(TC)a.one : (TC)a.one;
+                        const TC z = (TC)a.zero;
 #pragma unroll
                         for (int q = 0; q < S; ++q) {
                             if (q % 4 == 0)
@@ -468,13 +551,13 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
                     }
                 } else {
                     Pmid = P;
-                    high_flip(RC, (blk & 1) ? (T)-1 : (T)1);
+                    high_flip(RC, (blk & 1) ? -1 : 1);
                 }
             }
             if constexpr (p % V == 0)
-                vload<T>(ELp + i0 + p, elv);
-            const T t = u - elv[p % V];
-            hit |= tree_min<T, MINM, S>(E) <= t;
+                vload<TC>(ELp + i0 + p, elv);
+            const TC t = uc - elv[p % V];
+            hit |= tree_min<TC, MINM, S>(E) <= t;
         });
         if (hit) {
             // Slow path (rare): rebuild every step of this body from the body-end registers and
@@ -482,28 +565,28 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
             // by the register rows and row RC whose Gray bits differ.
             const int iend = i0 + BODY - 1;
             const int gend = iend ^ (iend >> 1);
-            const T *rowRC = Mt + (size_t)RC * NB;
+            const TC *rowRC = Mt + (size_t)RC * NB;
 #pragma unroll 1
             for (int p = 0; p < BODY; ++p) {
                 const int i = i0 + p;
                 const int gp = i ^ (i >> 1);
-                T sr[RC];
+                TC sr[RC];
 #pragma unroll
                 for (int r = 0; r < RC; ++r)
-                    sr[r] = (T)(((gp >> r) & 1) - ((gend >> r) & 1));
+                    sr[r] = (TC)(((gp >> r) & 1) - ((gend >> r) & 1));
                 const int dRC = ((gp >> RC) & 1) - ((gend >> RC) & 1);
-                const T sRC = (T)dRC;
-                const T Pp = dRC == 0 ? P : Pmid;
-                const T elp = ELp[i];
-                T tp = (Treg + mu - Pp) - elp;
+                const TC sRC = (TC)dRC;
+                const TP Pp = dRC == 0 ? P : Pmid;
+                const TC elp = ELp[i];
+                TC tp = to_col<T>(Treg + mu - Pp, clampC) - elp;
 #pragma unroll
                 for (int g = 0; g < G; ++g) {
-                    T mv[V];
-                    vload<T>(rowRC + (g * 32 + lane) * V, mv);
+                    TC mv[V];
+                    vload<TC>(rowRC + (g * 32 + lane) * V, mv);
 #pragma unroll
                     for (int e = 0; e < V; ++e) {
                         const int q = g * V + e;
-                        T ev = E[q];
+                        TC ev = E[q];
 #pragma unroll
                         for (int r = 0; r < RC; ++r)
                             ev = ev + sr[r] * Mr[r][q];
@@ -511,28 +594,29 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
                     }
                 }
                 const uint64_t cb = cbase | ((uint64_t)gp << B);
-                const T Ep = Pp + elp;
+                const TP Ep = Pp + (TP)elp;
 #pragma unroll 1
                 for (int q = 0; q < S; ++q) {
-                    const T ev = stage[q * 32 + lane];
+                    const TC ev = stage[q * 32 + lane];
                     if (ev <= tp) {
-                        const T Et = ev + Ep;
+                        const TP Et = (TP)ev + Ep;
                         const uint32_t j = (uint32_t)(((q / V) * 32 + lane) * V + (q % V));
                         record<T>(a, inst, Et, cb | j);
                         if (K1 && Et < Treg) {
                             Treg = Et;
-                            tp = (Treg + mu - Pp) - elp;
+                            tp = to_col<T>(Treg + mu - Pp, clampC) - elp;
                             Tr<T>::thr_min(st, Et);
                         }
                     }
                 }
             }
             u = Treg + mu - P;
+            uc = to_col<T>(u, clampC);
         }
         if (blk + 1 < nblk) {
             const int ip = (blk + 1) * BODY;
             const int kk = __ffs(ip) - 1;
-            high_flip(kk, ((ip >> (kk + 1)) & 1) ? (T)-1 : (T)1);
+            high_flip(kk, ((ip >> (kk + 1)) & 1) ? -1 : 1);
         }
     }
 
@@ -545,21 +629,21 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
         F f0r, cxr, lt, le[V], lg[G];
         unit_fields<T>(W, n, k, BL, unit, lane, f0r, cxr);
         column_fields<F, V, G>(f0r, lane, lt, le, lg);
-        const T *rowL = Mt + (size_t)(L - 1) * NB;
+        const TC *rowL = Mt + (size_t)(L - 1) * NB;
         double dmax = 0.0;
 #pragma unroll
         for (int g = 0; g < G; ++g) {
-            T ev[V], mv[V];
-            vload<T>(Es + (g * 32 + lane) * V, ev);
-            vload<T>(rowL + (g * 32 + lane) * V, mv);
+            TC ev[V], mv[V];
+            vload<TC>(Es + (g * 32 + lane) * V, ev);
+            vload<TC>(rowL + (g * 32 + lane) * V, mv);
 #pragma unroll
             for (int e = 0; e < V; ++e) {
-                const T fresh = (T)((F)ev[e] + (le[e] + lt + lg[g])) + mv[e];
+                const TC fresh = (TC)((F)ev[e] + (le[e] + lt + lg[g])) + mv[e];
                 dmax = fmax(dmax, fabs((double)E[g * V + e] - (double)fresh));
             }
         }
         const F wl = __shfl_sync(kFull, f0r, B + L - 1);
-        dmax = fmax(dmax, fabs((double)P - (double)(T)(cxr + wl)));
+        dmax = fmax(dmax, fabs((double)P - (double)(TP)(cxr + wl)));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
@@ -571,13 +655,15 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
 template <class T, int S, int RC, bool K1, int MINB, int ADDM, int MINM>
 __global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs a)
 {
-    __shared__ T stage_all[kScanThreads / 32][S * 32];
-    __shared__ T wsm_all[kScanThreads / 32][kMaxWalkBits];
+    using TC = typename Tr<T>::TC;
+    using TP = typename Tr<T>::TP;
+    __shared__ TC stage_all[kScanThreads / 32][S * 32];
+    __shared__ TP wsm_all[kScanThreads / 32][kMaxWalkBits];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    T *stage = stage_all[warp];
-    T *wsm = wsm_all[warp];
+    TC *stage = stage_all[warp];
+    TP *wsm = wsm_all[warp];
     int cur = -1;
-    T Treg = (T)0;
+    TP Treg = (TP)0;
     for (;;) {
         unsigned long long item = 0;
         int stop = 0;

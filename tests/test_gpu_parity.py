@@ -78,7 +78,7 @@ def test_config1_n24(q):
     Q = wl.config1()
     r = q.solve(Q)
     check_int(r, oracle.solve(Q, method=oracle.DIRECT))
-    assert r.info["states_scanned"] == 1 << 24 and r.info["acc"] == "i32"
+    assert r.info["states_scanned"] == 1 << 24 and r.info["acc"] in ("i32", "i32f")
 
 
 @pytest.mark.parametrize("walk_bits", [4, 5, 8, 11, 13])
@@ -252,7 +252,7 @@ def test_n50_sampled_subcubes(q):
         r = q.solve(Q, topk=16, fix_bits=26, fix_value=int(v), walk_bits=12)
         i = r.info
         # the benchmark's 2^43-state steps plan 12 walked bits with the default variant too
-        assert i["acc"] == "i32" and i["walk_bits"] == 12
+        assert i["acc"] == "i32f" and i["walk_bits"] == 12  # exact in FP32 lanes for this plan
         assert i["split_k"] + i["walk_bits"] + i["suffix_bits"] == 50
         check_int(r, oracle.solve(Q, topk=16, fix_bits=26, fix_value=int(v)))
 
@@ -414,3 +414,31 @@ def test_window_through_overflow_split(q):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     res = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
     assert res.returncode == 0, res.stdout + res.stderr
+
+
+# --- integer energies in FP32 lanes versus the int32 kernel -----------------------------------
+
+def test_int32_kernel_when_fp32_lanes_disabled(q, monkeypatch):
+    monkeypatch.setenv("QUBO_NO_I32F", "1")
+    for n, seed in ((22, 1), (26, 2), (27, 3)):
+        Q = wl.upper_int(n, -1000, 1000, seed=seed)
+        r = q.solve(Q, topk=16)
+        assert r.info["acc"] == "i32"
+        check_int(r, oracle.solve(Q, topk=16))
+
+
+def test_fp32_lanes_rejected_beyond_2_24(q):
+    """Entries of +-2^20: the partial sums exceed 2^24, so the int32 kernel must run."""
+    Q = wl.upper_int(21, -(1 << 20), 1 << 20, seed=8)
+    r = q.solve(Q, topk=8)
+    assert r.info["acc"] == "i32"
+    check_int(r, oracle.solve(Q, topk=8))
+
+
+def test_fp32_lanes_near_the_limit(q):
+    """Entries sized so the plan's bound sits just under 2^24: exact FP32-lane scan, bit-exact."""
+    n = 27
+    Q = wl.upper_int(n, -105000, 105000, seed=9)  # S_nf + 2 S_ww ~ 0.97 * 2^24 for the default plan
+    r = q.solve(Q, topk=8)
+    check_int(r, oracle.solve(Q, topk=8))
+    assert r.info["acc"] == "i32f"
