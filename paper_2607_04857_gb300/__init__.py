@@ -297,6 +297,33 @@ def autotune_clear() -> None:
     load_library().qubo_autotune_clear()
 
 
+class BatchResults:
+    """Results of a batch as arrays (min, n_ties, tie codes, K lowest); indexing gives a Result."""
+
+    def __init__(self, count, dt, topk, states_cap, mn, ties, tk, tkE, infos):
+        self._args = (count, dt, topk, states_cap, mn, ties, tk, tkE, infos)
+        self.min = mn
+        self.count = count
+
+    def __len__(self):
+        return self.count
+
+    def __getitem__(self, i):
+        count, dt, topk, states_cap, mn, ties, tk, tkE, infos = self._args
+        if i < 0:
+            i += count
+        inf = infos[i]
+        k = inf.n_topk
+        isf = dt in (QUBO_F32, QUBO_F64)
+        return Result(float(mn[i]) if isf else int(mn[i]), int(inf.n_ties),
+                      ties[i * states_cap: i * states_cap + inf.n_written].copy(),
+                      tk[i * topk: i * topk + k].copy(), tkE[i * topk: i * topk + k].copy(),
+                      QUBO_TRUNCATED if inf.n_ties > states_cap else QUBO_OK, inf.as_dict())
+
+    def __iter__(self):
+        return (self[i] for i in range(self.count))
+
+
 class Batch:
     """Device-resident batch replayed as one CUDA graph (qubo_batch_*)."""
 
@@ -313,11 +340,12 @@ class Batch:
     def run(self, stream=None) -> None:
         _check(self._lib.qubo_batch_run(self._h, _stream_ptr(stream)), "qubo_batch_run")
 
-    def fetch(self) -> list[Result]:
+    def fetch(self) -> BatchResults:
+        """Wait for the last run; results stay in this batch's arrays until the next fetch."""
         mn, ties, tk, tkE, infos = self._out
         _check(self._lib.qubo_batch_fetch(self._h, _ptr(mn), _ptr(ties), _ptr(tk), _ptr(tkE), infos),
                "qubo_batch_fetch")
-        return _batch_results(self.count, self.dt, self.topk, self.states_cap, mn, ties, tk, tkE, infos)
+        return BatchResults(self.count, self.dt, self.topk, self.states_cap, mn, ties, tk, tkE, infos)
 
     def close(self) -> None:
         if getattr(self, "_h", None):
