@@ -112,6 +112,12 @@ int prepare(const void *Q, int n, qubo_dtype dt, uint32_t flags, HostInst &h)
 
 int acc_bytes(Acc a) { return (a == ACC_I32 || a == ACC_F32 || a == ACC_I32F) ? 4 : 8; }
 
+// Walked rows the run's kernel variant keeps in registers (a walk needs at least one more bit).
+int variant_reg_rows(const HostInst &h)
+{
+    return kVariantRegRows[acc_bytes(h.acc) == 4 && h.variant >= 0 && h.variant < kScanVariants ? h.variant : 0];
+}
+
 int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bits)
 {
     const int n = h.n;
@@ -126,7 +132,8 @@ int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bi
         return QUBO_ERR_ARG;
     h.states = 1ull << free_bits;
     h.B = suffix_bits(acc_bytes(h.acc), h.variant);
-    if (free_bits < h.B + kRegRows + 1) {
+    const int rc = variant_reg_rows(h);
+    if (free_bits < h.B + rc + 1) {
         h.small = 1;
         h.L = h.k = 0;
         h.sub_base = fix_bits ? (fix_value << free_bits) : 0;
@@ -142,10 +149,10 @@ int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bi
     else if (walk_bits > 0)
         L = walk_bits;
     else
-        L = std::max(kRegRows + 1, std::min(h.acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits,
-                                            free_bits - h.B - kTargetUnitsLog2));
+        L = std::max(rc + 1, std::min(h.acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits,
+                                      free_bits - h.B - kTargetUnitsLog2));
     const int k = n - h.B - L;
-    if (L < kRegRows + 1 || L > kMaxWalkBits || k < fix_bits || k > 63)
+    if (L < rc + 1 || L > kMaxWalkBits || k < fix_bits || k > 63)
         return QUBO_ERR_ARG;
     h.L = L;
     h.k = k;
@@ -1256,8 +1263,8 @@ int solve_one(Workspace &ws, HostInst &h, const qubo_options &o, size_t states_c
     // FP32 drift above the margin's budget: shorten the anchoring period (the walk), and as a
     // last resort rescan in FP64.
     while (!float_margin_ok(h, p, c.margin)) {
-        if (h.acc == ACC_F32 && !h.small && h.L > kRegRows + 1 && c.split_k <= 0) {
-            c.walk_bits = std::max(kRegRows + 1, h.L - 2);
+        if (h.acc == ACC_F32 && !h.small && h.L > variant_reg_rows(h) + 1 && c.split_k <= 0) {
+            c.walk_bits = std::max(variant_reg_rows(h) + 1, h.L - 2);
         } else {
             h.acc = ACC_F64;
             c.walk_bits = o.walk_bits;
@@ -1349,7 +1356,7 @@ int batch_prepare(const void *Q_packed, const int *n, const size_t *offsets, int
             h.variant = acc_bytes(acc) == 4 ? variant : 0;
             const int B = suffix_bits(acc_bytes(acc), h.variant);
             const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
-            const int walk = h.n - B >= kRegRows + 1 ? std::min(wmax, h.n - B) : 0;
+            const int walk = h.n - B >= variant_reg_rows(h) + 1 ? std::min(wmax, h.n - B) : 0;
             pst[i] = plan(h, 0, 0, 0, walk);
             if (!pst[i])
                 h.thr0 = threshold_bound(h, std::max(1, topk));
@@ -1368,7 +1375,7 @@ int batch_prepare(const void *Q_packed, const int *n, const size_t *offsets, int
             h.acc = ACC_I32F;
             h.variant = v2;
             const int B = suffix_bits(4, v2);
-            const int walk = h.n - B >= kRegRows + 1 ? std::min(kDefaultMaxWalkBits, h.n - B) : 0;
+            const int walk = h.n - B >= variant_reg_rows(h) + 1 ? std::min(kDefaultMaxWalkBits, h.n - B) : 0;
             if (plan(h, 0, 0, 0, walk) != QUBO_OK || (!h.small && !i32f_exact(h, &h.clampC))) {
                 all = false;
                 break;

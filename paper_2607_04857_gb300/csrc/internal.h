@@ -12,7 +12,7 @@ enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4, ACC_I32
 // Walked prefix rows kept in registers by the scan kernel (the largest of the compiled
 // variants); the inner loop is unrolled over 2^(RC+1) Gray steps so that every register-row
 // flip has a compile-time sign.  A plan needs walk_bits >= kRegRows + 1.
-constexpr int kRegRows = 3;
+constexpr int kRegRows = 4;
 // Compiled scan variants of the 4-byte accumulators: columns per thread S, register rows,
 // minimum resident blocks per SM, how integer adds are issued (0: compiler's choice, 1: all as
 // multiply-adds by a runtime 1 on the FMA pipe, 2: a quarter as 3-input adds with a runtime 0 on
@@ -20,14 +20,14 @@ constexpr int kRegRows = 3;
 // compile one variant: S = 16 with variant 0's register rows, blocks and min inputs.
 constexpr int kScanVariants = 8;
 constexpr int kVariantCols[kScanVariants] = {32, 32, 32, 16, 16, 32, 32, 16};
-constexpr int kVariantRegRows[kScanVariants] = {3, 2, 2, 3, 3, 2, 3, 2};
+constexpr int kVariantRegRows[kScanVariants] = {3, 2, 2, 3, 4, 2, 3, 2};
 constexpr int kVariantMinBlocks[kScanVariants] = {2, 2, 2, 3, 3, 3, 2, 3};
-constexpr int kVariantAddMode[kScanVariants] = {0, 0, 2, 0, 2, 0, 0, 0};
+constexpr int kVariantAddMode[kScanVariants] = {0, 0, 2, 0, 0, 0, 0, 0};
 constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 2, 3};
 // Default variant per 4-byte accumulator (measured on GB300; see the profiles).
 constexpr int kDefaultVariantI32 = 3;
-constexpr int kDefaultVariantF32 = 0;
-constexpr int kDefaultVariantI32F = 0;
+constexpr int kDefaultVariantF32 = 4;
+constexpr int kDefaultVariantI32F = 4;
 // Threads per block of the scan kernel (4 warps; every warp owns one work unit at a time).
 constexpr int kScanThreads = 128;
 // Longest Gray walk inside one work unit (also the FP32 re-anchoring period).
