@@ -228,7 +228,7 @@ int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int wal
 // Upper bound on the K-th lowest energy (with multiplicity) of the run's sub-cube: the K-th lowest
 // energy among distinct states met by greedy one-flip descents from seeded random starts.  Any
 // K distinct states of the range bound it from above; with fewer than K found, beta does.
-double threshold_bound(const HostInst &h, int K)
+double threshold_bound(const HostInst &h, int K, int restarts = 24)
 {
     const int n = h.n, fb = h.fix_bits, free_bits = n - fb;
     const uint64_t base = fb ? (h.fix_value << free_bits) : 0;
@@ -257,7 +257,6 @@ double threshold_bound(const HostInst &h, int K)
             seen.emplace_back(E, x);
     };
     std::mt19937_64 rng(0x9e3779b97f4a7c15ull ^ h.fix_value ^ ((uint64_t)n << 56));
-    const int restarts = 24;
     std::vector<double> hf(n);
     for (int r = 0; r < restarts; ++r) {
         uint64_t x = base | (r == 0 ? 0 : (rng() & fmask));
@@ -1005,6 +1004,8 @@ int job_enqueue_finalize(Workspace &ws, Job &j, unsigned long long max_count, un
     return QUBO_OK;
 }
 
+Part part_from(const Down &d, const Job &j, int i);
+
 // After the stream has finished: timings and per-instance results from the staging buffer.
 void job_unpack(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seconds)
 {
@@ -1017,8 +1018,16 @@ void job_unpack(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_sec
         j.scan_seconds = ms * 1e-3;
     const Down d = down_view(ws, j);
     parts.assign(ni, Part());
-    for (int i = 0; i < ni; ++i) {
-        Part &p = parts[i];
+    for (int i = 0; i < ni; ++i)
+        parts[i] = part_from(d, j, i);
+}
+
+// Per-instance result of a finished job, read from the download staging buffer.
+Part part_from(const Down &d, const Job &j, int i)
+{
+    const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
+    Part p;
+    {
         const ResOut &r = d.res[i];
         p.is_float = is_float;
         p.has = r.has != 0;
@@ -1041,6 +1050,7 @@ void job_unpack(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_sec
         p.err = ubits_to_double(d.sts[i].err);
         p.overflow = d.sts[i].dropped > 0;
     }
+    return p;
 }
 
 // Wait for the scan, finalize with the exact record count, download and unpack.
@@ -1358,8 +1368,10 @@ int batch_prepare(const void *Q_packed, const int *n, const size_t *offsets, int
             const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
             const int walk = h.n - B >= variant_reg_rows(h) + 1 ? std::min(wmax, h.n - B) : 0;
             pst[i] = plan(h, 0, 0, 0, walk);
+            // batches are many small instances: fewer descents (K = 1 thresholds also tighten on
+            // the device as soon as a lower state is found)
             if (!pst[i])
-                h.thr0 = threshold_bound(h, std::max(1, topk));
+                h.thr0 = threshold_bound(h, std::max(1, topk), topk > 1 ? 16 : 6);
         }
     };
     parallel(plan_range);
@@ -1876,11 +1888,15 @@ int qubo_batch_fetch(qubo_batch *b, void *out_min, uint64_t *out_states, uint64_
     if ((st = job_wait(b->ws, j, b->ws.ev[2])))
         return st;
     CK(cudaStreamSynchronize(j.stream));
-    std::vector<Part> parts;
     double gs = 0.0;
-    job_unpack(b->ws, j, parts, &gs);
+    {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b->ws.ev[0], b->ws.ev[2]) == cudaSuccess)
+            gs = ms * 1e-3;
+        if (cudaEventElapsedTime(&ms, b->ws.ev[3], b->ws.ev[1]) == cudaSuccess)
+            j.scan_seconds = ms * 1e-3;
+    }
     // the graph's launches: the same kernels a direct run makes, with every sort stage present
-    j.launches = 0;
     {
         const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
         unsigned long long P = 1;
@@ -1897,6 +1913,10 @@ int qubo_batch_fetch(qubo_batch *b, void *out_min, uint64_t *out_states, uint64_
     j.d2h = sizeof(ResOut) * b->count + sizeof(InstState) * b->count + 8 * j.cap * b->count + 16 * (size_t)j.K * b->count;
     if (j.aborted)
         return QUBO_ERR_TIMEOUT;
+    const Down d = down_view(b->ws, j);
+    const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
+    SolveStats stats;
+    stats.add(j, gs);
     int worst = QUBO_OK;
     SolveCfg c;
     c.K = b->topk;
@@ -1904,10 +1924,54 @@ int qubo_batch_fetch(qubo_batch *b, void *out_min, uint64_t *out_states, uint64_
     c.variant = j.variant;
     for (int r = 0; r < b->count; ++r) {
         const int i = b->order[r];
-        Part &p = parts[r];
         HostInst &h = b->hs[i];
-        SolveStats stats;
-        stats.add(j, gs);
+        const ResOut &res = d.res[r];
+        const InstState &sts = d.sts[r];
+        const double drift = ubits_to_double(sts.drift);
+        const bool fast = res.has && sts.dropped == 0 && sts.scanned == (1ull << h.n) &&
+                          (h.acc != ACC_F32 || 2.0 * drift + 8.0 * std::ldexp(1.0, -24) * (1.0 + h.beta) < c.margin);
+        qubo_result *inf = info ? info + i : nullptr;
+        if (fast) {
+            // common case: copy straight from the staging buffer
+            if (h.is_float)
+                ((double *)out_min)[i] = res.min_f;
+            else
+                ((int64_t *)out_min)[i] = res.min_i;
+            if (b->cap)
+                std::memcpy(out_states + (size_t)i * b->cap, d.ties + (size_t)r * b->cap,
+                            sizeof(uint64_t) * res.n_written);
+            for (int t = 0; t < res.nk; ++t) {
+                out_topk[(size_t)i * b->topk + t] = d.tk[(size_t)r * b->topk + t];
+                if (out_topk_E) {
+                    const int64_t e = d.tke[(size_t)r * b->topk + t];
+                    if (h.is_float)
+                        ((double *)out_topk_E)[(size_t)i * b->topk + t] = bits_to_double(e);
+                    else
+                        ((int64_t *)out_topk_E)[(size_t)i * b->topk + t] = e;
+                }
+            }
+            if (inf) {
+                std::memset(inf, 0, sizeof(*inf));
+                inf->min_i = h.is_float ? 0 : res.min_i;
+                inf->min_f = res.min_f;
+                inf->n_ties = res.n_ties;
+                inf->n_written = res.n_written;
+                inf->truncated = res.n_ties > b->cap ? 1 : 0;
+                inf->acc = (int32_t)h.acc;
+                inf->n_topk = res.nk;
+                inf->fp32_max_abs_err = is_float ? ubits_to_double(sts.err) : 0.0;
+                inf->fp32_max_drift = is_float ? drift : 0.0;
+                inf->n_near_ties = res.n_near;
+                inf->states_scanned = sts.scanned;
+                inf->candidates = sts.nrec;
+                fill_plan_info(h, stats, b->t0, inf);
+            }
+            if (res.n_ties > b->cap)
+                worst = std::max(worst, (int)QUBO_TRUNCATED);
+            continue;
+        }
+        Part p = part_from(d, j, r);
+        SolveStats st2 = stats;
         if (p.overflow || !float_margin_ok(h, p, c.margin)) {
             // rare: solve this instance alone on the shared workspace (the graph's is fixed)
             Workspace *sw = nullptr;
@@ -1922,7 +1986,7 @@ int qubo_batch_fetch(qubo_batch *b, void *out_min, uint64_t *out_states, uint64_
             if (!float_margin_ok(hc, p, c.margin))
                 hc.acc = ACC_F64;
             p = Part();
-            if ((st = solve_range(*sw, hc, 0, 0, c, j.stream, p, stats, 0.0)))
+            if ((st = solve_range(*sw, hc, 0, 0, c, j.stream, p, st2, 0.0)))
                 return st;
         }
         if (p.scanned != (1ull << h.n) || !p.has)
@@ -1932,12 +1996,11 @@ int qubo_batch_fetch(qubo_batch *b, void *out_min, uint64_t *out_states, uint64_
         if (out_topk_E)
             otke = h.is_float ? (void *)((double *)out_topk_E + (size_t)i * b->topk)
                               : (void *)((int64_t *)out_topk_E + (size_t)i * b->topk);
-        qubo_result *inf = info ? info + i : nullptr;
         if (inf)
             std::memset(inf, 0, sizeof(*inf));
         fill_outputs(h, p, b->topk, b->cap, om, out_states ? out_states + (size_t)i * b->cap : nullptr,
                      out_topk ? out_topk + (size_t)i * b->topk : nullptr, otke, inf);
-        fill_plan_info(h, stats, b->t0, inf);
+        fill_plan_info(h, st2, b->t0, inf);
         if (p.n_ties > b->cap)
             worst = std::max(worst, (int)QUBO_TRUNCATED);
     }

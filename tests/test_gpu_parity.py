@@ -435,10 +435,21 @@ def test_fp32_lanes_rejected_beyond_2_24(q):
     check_int(r, oracle.solve(Q, topk=8))
 
 
-def test_fp32_lanes_near_the_limit(q):
-    """Entries sized so the plan's bound sits just under 2^24: exact FP32-lane scan, bit-exact."""
-    n = 27
-    Q = wl.upper_int(n, -105000, 105000, seed=9)  # S_nf + 2 S_ww ~ 0.97 * 2^24 for the default plan
-    r = q.solve(Q, topk=8)
+def plan_bound(Q, suffix_bits, walk_bits):
+    """S_nf + 2 S_ww of a plan: the largest magnitude the FP32-lane scan would form."""
+    U = np.abs(oracle.fold(Q)).astype(np.float64)
+    nf = suffix_bits + walk_bits
+    return U[:nf, :].sum() + 2 * U[suffix_bits:nf, suffix_bits:nf].sum()
+
+
+@pytest.mark.parametrize("lim", [60000, 95000, 100000, 105000, 120000])
+def test_fp32_lanes_chosen_exactly_when_bounded(q, lim):
+    """Entries sized around the 2^24 bound: the FP32-lane scan is used exactly when the run's
+    plan keeps S_nf + 2 S_ww + 2 below 2^24, and the results are bit-exact either way."""
+    Q = wl.upper_int(27, -lim, lim, seed=9)
+    r = q.solve(Q, topk=8, walk_bits=5)  # the same plan for either kernel (both 9 suffix bits)
     check_int(r, oracle.solve(Q, topk=8))
-    assert r.info["acc"] == "i32f"
+    i = r.info
+    assert (i["suffix_bits"], i["walk_bits"]) == (9, 5)
+    expect = "i32f" if plan_bound(Q, 9, 5) + 2 < 2**24 else "i32"
+    assert i["acc"] == expect
