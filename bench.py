@@ -137,7 +137,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("scan_impl.cuh", "scan_i32.cu", "scan_f32.cu", "scan_i32f.cu", "internal.h"):
+    for f in ("scan_impl.cuh", "scan_i32.cu", "scan_f32.cu", "scan_i32f.cu", "scan_i16p.cu", "internal.h"):
         with open(os.path.join(ROOT, "paper_2607_04857_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

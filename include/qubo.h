@@ -36,8 +36,17 @@ typedef enum { QUBO_I16 = 1, QUBO_I32 = 2, QUBO_F32 = 3, QUBO_F64 = 4 } qubo_dty
 
 /* Accumulator the scan ran in (reported in qubo_result.acc).  QUBO_ACC_I32F: integer energies
  * held exactly in FP32 lanes, chosen when every partial sum of the run's plan stays below 2^24
- * in magnitude (results are exact integers, as with QUBO_ACC_I32). */
-typedef enum { QUBO_ACC_I32 = 1, QUBO_ACC_I64 = 2, QUBO_ACC_F32 = 3, QUBO_ACC_F64 = 4, QUBO_ACC_I32F = 5 } qubo_acc;
+ * in magnitude.  QUBO_ACC_I16P: integer energies held as two 16-bit lanes per 32-bit word,
+ * chosen (before QUBO_ACC_I32F) when every column value of the run's plan provably lies in
+ * [-32768, 32767].  Both give exact integer results, as QUBO_ACC_I32 does. */
+typedef enum {
+    QUBO_ACC_I32 = 1,
+    QUBO_ACC_I64 = 2,
+    QUBO_ACC_F32 = 3,
+    QUBO_ACC_F64 = 4,
+    QUBO_ACC_I32F = 5,
+    QUBO_ACC_I16P = 6
+} qubo_acc;
 
 typedef enum {
     QUBO_OK = 0,

@@ -59,6 +59,7 @@ struct HostInst {
     uint64_t items = 0, states = 0;
     double thr0 = 0.0;  // initial threshold (a bound on the K-th lowest energy of the range)
     int32_t clampC = 0; // ACC_I32F: threshold clamp
+    int32_t col_lo = 0, col_hi = 0;  // ACC_I16P: proven range of every column value
 };
 
 bool dtype_ok(qubo_dtype dt) { return dt == QUBO_I16 || dt == QUBO_I32 || dt == QUBO_F32 || dt == QUBO_F64; }
@@ -110,7 +111,19 @@ int prepare(const void *Q, int n, qubo_dtype dt, uint32_t flags, HostInst &h)
     return QUBO_OK;
 }
 
-int acc_bytes(Acc a) { return (a == ACC_I32 || a == ACC_F32 || a == ACC_I32F) ? 4 : 8; }
+int acc_bytes(Acc a) { return (a == ACC_I32 || a == ACC_F32 || a == ACC_I32F || a == ACC_I16P) ? 4 : 8; }
+
+// Suffix bits (log2 of the columns of one work unit) of an accumulator and kernel variant.
+int acc_suffix_bits(Acc a, int variant)
+{
+    return a == ACC_I16P ? packed_suffix_bits(variant) : suffix_bits(acc_bytes(a), variant);
+}
+
+// Columns held by one thread (two per word in the packed scan).
+int acc_cols_per_thread(Acc a, int variant)
+{
+    return cols_per_thread(acc_bytes(a), variant) * (a == ACC_I16P ? 2 : 1);
+}
 
 // Walked rows the run's kernel variant keeps in registers (a walk needs at least one more bit).
 int variant_reg_rows(const HostInst &h)
@@ -131,7 +144,7 @@ int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bi
     if (free_bits > 63)
         return QUBO_ERR_ARG;
     h.states = 1ull << free_bits;
-    h.B = suffix_bits(acc_bytes(h.acc), h.variant);
+    h.B = acc_suffix_bits(h.acc, h.variant);
     const int rc = variant_reg_rows(h);
     if (free_bits < h.B + rc + 1) {
         h.small = 1;
@@ -171,7 +184,12 @@ int scan_variant(Acc acc = ACC_I32)
         if (x >= 0 && x < kScanVariants)
             return x;
     }
-    return acc == ACC_F32 ? kDefaultVariantF32 : (acc == ACC_I32F ? kDefaultVariantI32F : kDefaultVariantI32);
+    switch (acc) {
+    case ACC_F32: return kDefaultVariantF32;
+    case ACC_I32F: return kDefaultVariantI32F;
+    case ACC_I16P: return kDefaultVariantI16P;
+    default: return kDefaultVariantI32;
+    }
 }
 
 // The variant a run uses: the caller's (tuned) choice, else the accumulator's default.
@@ -209,17 +227,91 @@ bool i32f_allowed()
     return !(v && v[0] == '1');
 }
 
-// Accumulator, kernel variant and plan of one run.  Integer instances scan in FP32 lanes when
-// the plan keeps every value exact (and the plain form was not asked for).
+// Integer energies can be scanned as packed 16-bit lanes when every column value the plan's
+// kernel holds lies in [-32768, 32767].  For suffix pattern j, a column holds
+//   E_s(j) + sum_{i outside the suffix} x_i c_i(j) + sum_{r < RC} x_r w_r,
+// with c_i(j) = sum_{b in j} U_bi, w_r = sum_{f fixed} x_f U_rf (the couplings of the register
+// rows folded into their table rows).  Its range over all outside bits is bounded by taking every
+// c_i(j) and every U_rf at its sign's extreme, computed exactly for each j.  The scan's
+// threshold arithmetic (threshold - prefix - E_L + 2^15 in int32) asks beta < 2^29 as well.
+bool i16p_exact(HostInst &h)
+{
+    if (h.small || h.is_float || h.beta >= 536870912.0)
+        return false;
+    const int n = h.n, B = h.B, rc = variant_reg_rows(h), nf = h.B + h.L;
+    auto U = [&](int i, int j) { return i < j ? h.Ui[(size_t)i * n + j] : h.Ui[(size_t)j * n + i]; };
+    int64_t wpos = 0, wneg = 0;
+    for (int r = B; r < B + rc; ++r)
+        for (int f = nf; f < n; ++f) {
+            const int64_t u = U(r, f);
+            (u > 0 ? wpos : wneg) += u;
+        }
+    // quick accept: the sum of |U| over every entry a column can contain
+    int64_t crude = wpos - wneg;
+    for (int b = 0; b < B; ++b)
+        for (int i = b; i < n; ++i) {
+            const int64_t u = U(b, i);
+            crude += u < 0 ? -u : u;
+        }
+    if (crude <= 32767) {
+        h.col_lo = (int32_t)-crude;
+        h.col_hi = (int32_t)crude;
+        return true;
+    }
+    // exact per-pattern range: c[j][i] for every variable i, built from j without its lowest bit
+    const size_t NB = 1ull << B;
+    std::vector<int64_t> c(NB * n, 0), es(NB, 0);
+    int64_t lo = 0, hi = 0;
+    for (size_t j = 1; j < NB; ++j) {
+        const int b = __builtin_ctzll(j);
+        const size_t jp = j & (j - 1);
+        const int64_t *cp = &c[jp * n];
+        int64_t *cj = &c[j * n];
+        for (int i = 0; i < n; ++i)
+            cj[i] = cp[i] + (i == b ? 0 : U(b, i));
+        es[j] = es[jp] + U(b, b) + cp[b];
+        int64_t up = es[j], dn = es[j];
+        for (int i = B; i < n; ++i)
+            (cj[i] > 0 ? up : dn) += cj[i];
+        lo = std::min(lo, dn);
+        hi = std::max(hi, up);
+    }
+    lo += wneg;
+    hi += wpos;
+    if (lo < -32768 || hi > 32767)
+        return false;
+    h.col_lo = (int32_t)lo;
+    h.col_hi = (int32_t)hi;
+    return true;
+}
+
+bool i16p_allowed()
+{
+    const char *v = std::getenv("QUBO_NO_I16P");
+    return !(v && v[0] == '1');
+}
+
+// Accumulator, kernel variant and plan of one run.  Integer instances scan in packed 16-bit lanes
+// or else in FP32 lanes when the plan keeps every value exact (and the plain form was not asked
+// for), else in int32.
 int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bits, int variant_req,
              uint32_t flags)
 {
-    if ((h.acc == ACC_I32 || h.acc == ACC_I32F) && !(flags & QUBO_FLAG_PLAIN)) {
-        h.acc = ACC_I32F;
-        h.variant = pick_variant(h.acc, variant_req);
-        if (!i32f_allowed() || plan(h, fix_bits, fix_value, split_k, walk_bits) != QUBO_OK ||
-            !i32f_exact(h, &h.clampC))
-            h.acc = ACC_I32;
+    if ((h.acc == ACC_I32 || h.acc == ACC_I32F || h.acc == ACC_I16P) && !(flags & QUBO_FLAG_PLAIN)) {
+        Acc chosen = ACC_I32;
+        if (i16p_allowed()) {
+            h.acc = ACC_I16P;
+            h.variant = pick_variant(h.acc, variant_req);
+            if (plan(h, fix_bits, fix_value, split_k, walk_bits) == QUBO_OK && i16p_exact(h))
+                chosen = ACC_I16P;
+        }
+        if (chosen == ACC_I32 && i32f_allowed()) {
+            h.acc = ACC_I32F;
+            h.variant = pick_variant(h.acc, variant_req);
+            if (plan(h, fix_bits, fix_value, split_k, walk_bits) == QUBO_OK && i32f_exact(h, &h.clampC))
+                chosen = ACC_I32F;
+        }
+        h.acc = chosen;
     }
     h.variant = acc_bytes(h.acc) == 4 ? pick_variant(h.acc, variant_req) : 0;
     return plan(h, fix_bits, fix_value, split_k, walk_bits);
@@ -339,7 +431,8 @@ unsigned long long encode_thr(Acc acc, double t)
 {
     switch (acc) {
     case ACC_I32:
-    case ACC_I32F: return (unsigned long long)(uint32_t)(int32_t)t;
+    case ACC_I32F:
+    case ACC_I16P: return (unsigned long long)(uint32_t)(int32_t)t;
     case ACC_I64: return (unsigned long long)(int64_t)t;
     case ACC_F32: {
         float f = (float)t;
@@ -356,7 +449,8 @@ unsigned long long encode_max(Acc acc)
 {
     switch (acc) {
     case ACC_I32:
-    case ACC_I32F: return (unsigned long long)(uint32_t)INT32_MAX;
+    case ACC_I32F:
+    case ACC_I16P: return (unsigned long long)(uint32_t)INT32_MAX;
     case ACC_I64: return (unsigned long long)INT64_MAX;
     case ACC_F32: return ord32h(INFINITY);
     case ACC_F64: return ord64h(INFINITY);
@@ -823,7 +917,7 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
             d.W64 = (const double *)(dev + j.off_W64[i]);
             d.U64 = (const double *)(dev + j.off_U64[i]);
         } else {
-            if (j.acc == ACC_I32 || j.acc == ACC_I32F) {
+            if (j.acc == ACC_I32 || j.acc == ACC_I32F || j.acc == ACC_I16P) {
                 int32_t *W = (int32_t *)(up + j.off_W[i]);
                 for (int a = 0; a < h.n; ++a)
                     for (int b = 0; b < h.n; ++b)
@@ -1307,7 +1401,7 @@ void fill_plan_info(const HostInst &h, const SolveStats &stats, double t0, qubo_
     info->split_k = h.k;
     info->walk_bits = h.L;
     info->suffix_bits = h.small ? 0 : h.B;
-    info->cols_per_thread = h.small ? 0 : cols_per_thread(acc_bytes(h.acc), h.variant);
+    info->cols_per_thread = h.small ? 0 : acc_cols_per_thread(h.acc, h.variant);
     info->threads = kScanThreads;
     info->blocks = stats.blocks;
     info->passes = stats.passes;
@@ -1364,7 +1458,7 @@ int batch_prepare(const void *Q_packed, const int *n, const size_t *offsets, int
         for (int i = lo; i < hi; ++i) {
             HostInst &h = hs[i];
             h.variant = acc_bytes(acc) == 4 ? variant : 0;
-            const int B = suffix_bits(acc_bytes(acc), h.variant);
+            const int B = acc_suffix_bits(acc, h.variant);
             const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
             const int walk = h.n - B >= variant_reg_rows(h) + 1 ? std::min(wmax, h.n - B) : 0;
             pst[i] = plan(h, 0, 0, 0, walk);
@@ -1378,26 +1472,38 @@ int batch_prepare(const void *Q_packed, const int *n, const size_t *offsets, int
     for (int i = 0; i < count; ++i)
         if (pst[i])
             return pst[i];
-    if (acc == ACC_I32 && i32f_allowed()) {
-        // one accumulator for the batch: FP32 lanes when every instance's plan is exact
+    // One accumulator for the batch: packed 16-bit lanes, else FP32 lanes, when every
+    // instance's plan is exact in it (instances evaluated directly need nothing).
+    for (const Acc alt_acc : {ACC_I16P, ACC_I32F}) {
+        if (acc != ACC_I32 || !(alt_acc == ACC_I16P ? i16p_allowed() : i32f_allowed()))
+            break;
         std::vector<HostInst> alt = hs;
-        const int v2 = pick_variant(ACC_I32F, -1);
-        bool all = true;
-        for (auto &h : alt) {
-            h.acc = ACC_I32F;
-            h.variant = v2;
-            const int B = suffix_bits(4, v2);
-            const int walk = h.n - B >= variant_reg_rows(h) + 1 ? std::min(kDefaultMaxWalkBits, h.n - B) : 0;
-            if (plan(h, 0, 0, 0, walk) != QUBO_OK || (!h.small && !i32f_exact(h, &h.clampC))) {
-                all = false;
-                break;
+        int v2 = pick_variant(alt_acc, -1);
+        int tv = 0, tw = 0;
+        if (tuned_plan(alt_acc, 0, &tv, &tw))
+            v2 = tv;
+        std::atomic<bool> all{true};
+        auto alt_range = [&](int lo, int hi) {
+            for (int i = lo; i < hi && all.load(std::memory_order_relaxed); ++i) {
+                HostInst &h = alt[i];
+                h.acc = alt_acc;
+                h.variant = v2;
+                const int B = acc_suffix_bits(alt_acc, v2);
+                const int walk =
+                    h.n - B >= variant_reg_rows(h) + 1 ? std::min(kDefaultMaxWalkBits, h.n - B) : 0;
+                const bool ok = plan(h, 0, 0, 0, walk) == QUBO_OK &&
+                                (h.small || (alt_acc == ACC_I16P ? i16p_exact(h) : i32f_exact(h, &h.clampC)));
+                if (!ok)
+                    all = false;
             }
-        }
+        };
+        parallel(alt_range);
         if (all) {
             for (size_t i = 0; i < hs.size(); ++i) {
                 alt[i].thr0 = hs[i].thr0;
                 hs[i] = std::move(alt[i]);
             }
+            break;
         }
     }
     // longest work first (LPT order) so the tail of the persistent launch is short
@@ -2105,11 +2211,13 @@ int qubo_autotune_batched(const void *Q_packed, const int *n, const size_t *offs
         bool ok = true;
         for (auto &h : hv) {
             h.variant = acc_bytes(acc) == 4 ? v : 0;
-            const int B = suffix_bits(acc_bytes(acc), h.variant);
+            const int B = acc_suffix_bits(acc, h.variant);
             const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
             const int walk = h.n - B >= kVariantRegRows[v] + 1 ? std::min(wmax, h.n - B) : 0;
             if (plan(h, 0, 0, 0, walk))
                 ok = false;
+            else if (!h.small && ((acc == ACC_I16P && !i16p_exact(h)) || (acc == ACC_I32F && !i32f_exact(h, &h.clampC))))
+                ok = false;  // this variant's plan leaves the batch's lanes inexact
         }
         if (!ok)
             continue;

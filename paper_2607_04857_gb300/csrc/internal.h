@@ -7,7 +7,8 @@
 namespace qubo {
 
 // ACC_I32F: integer energies scanned exactly in FP32 lanes (partial sums below 2^24).
-enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4, ACC_I32F = 5 };
+// ACC_I16P: integer energies whose column values fit 16 bits, two columns per 32-bit word.
+enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4, ACC_I32F = 5, ACC_I16P = 6 };
 
 // Walked prefix rows kept in registers by the scan kernel (the largest of the compiled
 // variants); the inner loop is unrolled over 2^(RC+1) Gray steps so that every register-row
@@ -28,6 +29,7 @@ constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 2, 3};
 constexpr int kDefaultVariantI32 = 3;
 constexpr int kDefaultVariantF32 = 4;
 constexpr int kDefaultVariantI32F = 4;
+constexpr int kDefaultVariantI16P = 3;
 // Threads per block of the scan kernel (4 warps; every warp owns one work unit at a time).
 constexpr int kScanThreads = 128;
 // Longest Gray walk inside one work unit (also the FP32 re-anchoring period).
@@ -114,8 +116,11 @@ constexpr int suffix_bits(int bytes, int variant = 0)
 {
     return cols_per_thread(bytes, variant) == 32 ? 10 : 9;
 }
+// The packed 16-bit scan holds two columns in each of its S words: one more suffix bit.
+constexpr int packed_suffix_bits(int variant) { return suffix_bits(4, variant) + 1; }
 
 struct i32f;  // tag of the integer-in-FP32 accumulator (scan_impl.cuh)
+struct i16p;  // tag of the packed 16-bit accumulator (scan_impl.cuh)
 
 // ---- launchers (scan_*.cu, one translation unit per accumulator type) -------------------------
 template <class T>

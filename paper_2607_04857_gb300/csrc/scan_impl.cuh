@@ -51,12 +51,14 @@ struct Tr;
 // holding exact integers (FP32 adds use both halves of the fused multiply-add pipe), while the
 // prefix energy and thresholds stay int32.
 struct i32f {};
+struct i16p {};
 
 template <>
 struct Tr<int32_t> {
     using TC = int32_t;
     using TP = int32_t;
     static constexpr bool kIntInFloat = false;
+    static constexpr int kPack = 1;
     using F = int32_t;   // precision of the tables
     using FU = int32_t;  // precision of the per-unit fields
     using Vec = int4;
@@ -75,6 +77,7 @@ struct Tr<int64_t> {
     using TC = int64_t;
     using TP = int64_t;
     static constexpr bool kIntInFloat = false;
+    static constexpr int kPack = 1;
     using F = int64_t;
     using FU = int64_t;
     using Vec = longlong2;
@@ -93,6 +96,7 @@ struct Tr<float> {
     using TC = float;
     using TP = float;
     static constexpr bool kIntInFloat = false;
+    static constexpr int kPack = 1;
     using F = double;
     using FU = float;
     using Vec = float4;
@@ -116,6 +120,7 @@ struct Tr<double> {
     using TC = double;
     using TP = double;
     static constexpr bool kIntInFloat = false;
+    static constexpr int kPack = 1;
     using F = double;
     using FU = double;
     using Vec = double2;
@@ -138,6 +143,7 @@ struct Tr<i32f> {
     using TC = float;
     using TP = int32_t;
     static constexpr bool kIntInFloat = true;
+    static constexpr int kPack = 1;
     using F = int32_t;
     using FU = int32_t;
     using Vec = float4;
@@ -149,6 +155,29 @@ struct Tr<i32f> {
     __device__ static int64_t bits(int32_t v) { return v; }
     __device__ static int32_t tmin(int32_t a, int32_t b) { return min(a, b); }
 };
+
+// Small integer instances (every column energy within +-32767): two columns per 32-bit word,
+// each a 16-bit lane biased by 2^15, so one 32-bit add updates both columns exactly (no lane
+// ever leaves [0, 65535], so no carry crosses) and packed unsigned mins reduce two per
+// instruction.  The table rows are stored as packed deltas lo + 65536 * hi.
+template <>
+struct Tr<i16p> {
+    using TC = uint32_t;
+    using TP = int32_t;
+    static constexpr bool kIntInFloat = false;
+    static constexpr int kPack = 2;
+    using F = int32_t;
+    using FU = int32_t;
+    using Vec = uint4;
+    static constexpr int V = 4;
+    static constexpr bool kFloat = false;
+    __device__ static int32_t thr_load(const InstState *s) { return *(const volatile int32_t *)&s->thr; }
+    __device__ static void thr_min(InstState *s, int32_t v) { atomicMin((int *)&s->thr, v); }
+    __device__ static void gmin_min(InstState *s, int32_t v) { atomicMin((int *)&s->gmin, v); }
+    __device__ static int64_t bits(int32_t v) { return v; }
+    __device__ static int32_t tmin(int32_t a, int32_t b) { return min(a, b); }
+};
+constexpr int32_t kLaneBias = 32768;
 
 // Column value of a prefix-type threshold.  For FP32 columns holding integers the threshold is
 // clamped to +-C first: beyond C every column (|column| <= C - 1 - max|E_L|) is decided the same
@@ -179,6 +208,7 @@ __device__ __forceinline__ const typename Tr<T>::FU *unit_matrix(const Inst &d)
 __device__ __forceinline__ void vsplit(const int4 &v, int32_t (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
 __device__ __forceinline__ void vsplit(const float4 &v, float (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
 __device__ __forceinline__ void vsplit(const longlong2 &v, int64_t (&o)[2]) { o[0] = v.x; o[1] = v.y; }
+__device__ __forceinline__ void vsplit(const uint4 &v, uint32_t (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
 __device__ __forceinline__ void vsplit(const double2 &v, double (&o)[2]) { o[0] = v.x; o[1] = v.y; }
 
 // 16-byte read-only load of consecutive table entries (4 x 4 bytes or 2 x 8 bytes).
@@ -190,6 +220,8 @@ template <>
 struct VecOf<float> { using type = float4; static constexpr int V = 4; };
 template <>
 struct VecOf<int64_t> { using type = longlong2; static constexpr int V = 2; };
+template <>
+struct VecOf<uint32_t> { using type = uint4; static constexpr int V = 4; };
 template <>
 struct VecOf<double> { using type = double2; static constexpr int V = 2; };
 
@@ -231,6 +263,9 @@ __device__ __forceinline__ float emin3(float a, float b, float c)
     return d;
 }
 __device__ __forceinline__ double emin3(double a, double b, double c) { return fmin(fmin(a, b), c); }
+// uint32 columns are pairs of biased 16-bit lanes: lane-wise unsigned mins.
+__device__ __forceinline__ uint32_t emin(uint32_t a, uint32_t b) { return __vminu2(a, b); }
+__device__ __forceinline__ uint32_t emin3(uint32_t a, uint32_t b, uint32_t c) { return __vimin3_u16x2(a, b, c); }
 
 // min over N register values: a tree of 2-input (MINM == 2) or 3-input (MINM == 3) mins.
 template <class T, int MINM, int N>
@@ -284,13 +319,26 @@ template <class T>
 __global__ void tables_kernel(const Inst *insts)
 {
     using F = typename Tr<T>::F;
+    using TC = typename Tr<T>::TC;
+    using TP = typename Tr<T>::TP;
+    constexpr bool kPacked = Tr<T>::kPack == 2;
     const Inst &d = insts[blockIdx.y];
     if (d.small)
         return;
     const int n = d.n, B = d.B, L = d.L;
     const long NB = 1l << B, NL = 1l << L;
-    const long total = NB * (L + 1) + NL;
+    const long NM = kPacked ? NB / 2 : NB;  // words per interaction row
+    const long total = NB + NM * L + NL;
     const F *W = field_matrix<T>(d);
+    // M_int row r at column j: coupling of walked variable r to the suffix pattern j
+    auto m_entry = [&](long r, long j) {
+        const int vr = B + (int)r;
+        F acc = 0;
+        for (int b = 0; b < B; ++b)
+            if ((j >> b) & 1)
+                acc += W[vr * n + b];
+        return acc;
+    };
     for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
         if (idx < NB) {  // E_s(j): energy of the suffix pattern j alone
             const long j = idx;
@@ -303,17 +351,18 @@ __global__ void tables_kernel(const Inst *insts)
                     if ((j >> b2) & 1)
                         acc += W[b * n + b2];
             }
-            ((typename Tr<T>::TC *)d.Es)[j] = (typename Tr<T>::TC)acc;
-        } else if (idx < NB * (L + 1)) {  // M_int row r: coupling of walked variable r to pattern j
-            const long r = (idx - NB) / NB, j = (idx - NB) % NB;
-            const int vr = B + (int)r;
-            F acc = 0;
-            for (int b = 0; b < B; ++b)
-                if ((j >> b) & 1)
-                    acc += W[vr * n + b];
-            ((typename Tr<T>::TC *)d.M)[r * NB + j] = (typename Tr<T>::TC)acc;
+            if constexpr (kPacked)
+                ((TP *)d.Es)[j] = (TP)acc;
+            else
+                ((TC *)d.Es)[j] = (TC)acc;
+        } else if (idx < NB + NM * L) {
+            const long r = (idx - NB) / NM, w = (idx - NB) % NM;
+            if constexpr (kPacked)  // packed delta: column w in the low lane, w + NB/2 in the high
+                ((TC *)d.M)[r * NM + w] = (uint32_t)m_entry(r, w) + ((uint32_t)m_entry(r, w + NB / 2) << 16);
+            else
+                ((TC *)d.M)[r * NM + w] = (TC)m_entry(r, w);
         } else {  // E_L(g(i)): energy of the i-th walked pattern, stored in walk order
-            const long i = idx - NB * (L + 1);
+            const long i = idx - NB - NM * L;
             const long g = i ^ (i >> 1);
             F acc = 0;
             for (int r = 0; r < L; ++r) {
@@ -324,7 +373,10 @@ __global__ void tables_kernel(const Inst *insts)
                     if ((g >> r2) & 1)
                         acc += W[(B + r) * n + (B + r2)];
             }
-            ((typename Tr<T>::TC *)d.EL)[i] = (typename Tr<T>::TC)acc;
+            if constexpr (kPacked)  // stored minus the lane bias: threshold - E_L is then a lane value
+                ((TP *)d.EL)[i] = (TP)acc - kLaneBias;
+            else
+                ((TC *)d.EL)[i] = (TC)acc;
         }
     }
 }
@@ -652,6 +704,197 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
     }
 }
 
+// ---- one work unit, packed 16-bit columns (small integer instances) ----------------------------
+// Word w = (g * 32 + lane) * V + e of a thread holds column w in its low lane and column
+// w + NB/2 in its high lane, each biased by 2^15.  One 32-bit add moves both columns; the tree of
+// packed unsigned mins leaves the two lane minima in one word, and the step's test compares the
+// smaller lane with threshold - E_L (E_L is stored minus the bias, so that difference is already
+// in lane units).  Everything else follows scan_unit.
+template <int S, int RC, bool K1, int ADDM, int MINM>
+__device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &d, int inst, uint64_t unit,
+                                                 int32_t &Treg, int lane, uint32_t *stage, int32_t *wsm)
+{
+    using T = i16p;
+    using F = int32_t;
+    constexpr int V = 4;
+    constexpr int G = S / V;
+    constexpr int LOGV = ilog2c(V);
+    constexpr int LOGG = ilog2c(G);
+    constexpr int B = LOGV + 5 + LOGG + 1;
+    constexpr int NW = 1 << (B - 1);  // words per table row
+    constexpr int BODY = 1 << (RC + 1);
+    const int n = d.n, L = d.L, k = d.k, BL = B + L;
+    InstState *st = a.state + inst;
+    const F *W = unit_matrix<T>(d);
+
+    F f0, cx;
+    unit_fields<T>(W, n, k, BL, unit, lane, f0, cx);
+    __syncwarp();
+    if (lane >= B && lane < BL)
+        wsm[lane - B] = f0;
+    __syncwarp();
+
+    // Column fields of the low lane; the high lane adds the field of suffix bit B - 1.
+    F lin_t, lin_e[V], lin_g[G];
+    column_fields<F, V, G>(f0, lane, lin_t, lin_e, lin_g);
+    const F vtop = __shfl_sync(kFull, f0, B - 1);
+
+    const int32_t *Es = (const int32_t *)d.Es;
+    uint32_t E[S];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        int32_t lo[V], hi[V];
+        vload<int32_t>(Es + (g * 32 + lane) * V, lo);
+        vload<int32_t>(Es + NW + (g * 32 + lane) * V, hi);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const F lin = lin_e[e] + lin_t + lin_g[g];
+            E[g * V + e] = (uint32_t)(lo[e] + lin + kLaneBias) + ((uint32_t)(hi[e] + lin + vtop + kLaneBias) << 16);
+        }
+    }
+
+    // Register rows: packed M_r plus w_r on both lanes.
+    const uint32_t *Mt = (const uint32_t *)d.M;
+    uint32_t Mr[RC][S];
+#pragma unroll
+    for (int r = 0; r < RC; ++r) {
+        const uint32_t wr2 = (uint32_t)__shfl_sync(kFull, f0, B + r) * 65537u;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            uint32_t mv[V];
+            vload<uint32_t>(Mt + (size_t)r * NW + (g * 32 + lane) * V, mv);
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                Mr[r][g * V + e] = mv[e] + wr2;
+        }
+    }
+
+    {
+        const int32_t tg = Tr<T>::thr_load(st);
+        Treg = K1 ? min(Treg, tg) : tg;
+    }
+    const int32_t mu = (int32_t)a.margin;
+    int32_t P = cx;
+    int32_t u = Treg + mu - P;
+
+    auto high_flip = [&](int kk, int sgn) {
+        const uint32_t *row = Mt + (size_t)kk * NW;
+        const uint32_t sg = (uint32_t)sgn;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            uint32_t mv[V];
+            vload<uint32_t>(row + (g * 32 + lane) * V, mv);
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                E[g * V + e] = E[g * V + e] + sg * mv[e];
+        }
+        P = P + sgn * wsm[kk];
+        u = Treg + mu - P;
+    };
+
+    const int32_t *ELp = (const int32_t *)d.EL;
+    const int nblk = 1 << (L - RC - 1);
+    const uint64_t cbase = unit << BL;
+
+    for (int blk = 0; blk < nblk; ++blk) {
+        const int i0 = blk * BODY;
+        int32_t elv[V];
+        bool hit = false;
+        int32_t Pmid = P;
+        static_for<BODY>([&](auto pc) {
+            constexpr int p = decltype(pc)::value;
+            if constexpr (p > 0) {
+                constexpr int kk = ctzc(p);
+                if constexpr (kk < RC) {
+                    constexpr bool neg = (p >> (kk + 1)) & 1;
+                    if constexpr (ADDM == 2) {
+                        const uint32_t z = (uint32_t)a.zero;
+#pragma unroll
+                        for (int q = 0; q < S; ++q) {
+                            if (q % 4 == 0)
+                                E[q] = neg ? (E[q] - Mr[kk][q]) + z : (E[q] + Mr[kk][q]) + z;
+                            else
+                                E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < S; ++q)
+                            E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
+                    }
+                } else {
+                    Pmid = P;
+                    high_flip(RC, (blk & 1) ? -1 : 1);
+                }
+            }
+            if constexpr (p % V == 0)
+                vload<int32_t>(ELp + i0 + p, elv);
+            const int32_t t = u - elv[p % V];
+            const uint32_t mw = tree_min<uint32_t, MINM, S>(E);
+            hit |= min((int32_t)(mw & 0xffffu), (int32_t)(mw >> 16)) <= t;
+        });
+        if (hit) {
+            const int iend = i0 + BODY - 1;
+            const int gend = iend ^ (iend >> 1);
+            const uint32_t *rowRC = Mt + (size_t)RC * NW;
+#pragma unroll 1
+            for (int p = 0; p < BODY; ++p) {
+                const int i = i0 + p;
+                const int gp = i ^ (i >> 1);
+                uint32_t sr[RC];
+#pragma unroll
+                for (int r = 0; r < RC; ++r)
+                    sr[r] = (uint32_t)(((gp >> r) & 1) - ((gend >> r) & 1));
+                const int dRC = ((gp >> RC) & 1) - ((gend >> RC) & 1);
+                const uint32_t sRC = (uint32_t)dRC;
+                const int32_t Pp = dRC == 0 ? P : Pmid;
+                const int32_t el = ELp[i] + kLaneBias;
+                int32_t tp = Treg + mu - Pp - el;
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    uint32_t mv[V];
+                    vload<uint32_t>(rowRC + (g * 32 + lane) * V, mv);
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const int q = g * V + e;
+                        uint32_t ev = E[q];
+#pragma unroll
+                        for (int r = 0; r < RC; ++r)
+                            ev = ev + sr[r] * Mr[r][q];
+                        stage[q * 32 + lane] = ev + sRC * mv[e];
+                    }
+                }
+                const uint64_t cb = cbase | ((uint64_t)gp << B);
+                const int32_t Ep = Pp + el;
+#pragma unroll 1
+                for (int q = 0; q < 2 * S; ++q) {
+                    const uint32_t word = stage[(q >> 1) * 32 + lane];
+                    const int32_t col = (int32_t)((q & 1) ? (word >> 16) : (word & 0xffffu)) - kLaneBias;
+                    if (col <= tp) {
+                        const int32_t Et = col + Ep;
+                        const int qw = q >> 1;
+                        const uint32_t j = (uint32_t)(((qw / V) * 32 + lane) * V + (qw % V)) + ((q & 1) ? NW : 0);
+                        record<T>(a, inst, Et, cb | j);
+                        if (K1 && Et < Treg) {
+                            Treg = Et;
+                            tp = Treg + mu - Pp - el;
+                            Tr<T>::thr_min(st, Et);
+                        }
+                    }
+                }
+            }
+            u = Treg + mu - P;
+        }
+        if (blk + 1 < nblk) {
+            const int ip = (blk + 1) * BODY;
+            const int kk = __ffs(ip) - 1;
+            high_flip(kk, ((ip >> (kk + 1)) & 1) ? -1 : 1);
+        }
+    }
+
+    if (lane == 0)
+        atomicAdd(&st->scanned, 1ull << BL);
+}
+
 template <class T, int S, int RC, bool K1, int MINB, int ADDM, int MINM>
 __global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs a)
 {
@@ -696,6 +939,8 @@ __global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs
         const uint64_t off = item - a.item_base[inst];
         if (d.small)
             small_unit<T>(a, d, inst, lane);
+        else if constexpr (Tr<T>::kPack == 2)
+            scan_unit_packed<S, RC, K1, ADDM, MINM>(a, d, inst, d.unit_begin + off, Treg, lane, stage, wsm);
         else
             scan_unit<T, S, RC, K1, ADDM, MINM>(a, d, inst, d.unit_begin + off, Treg, lane, stage, wsm);
     }

@@ -60,12 +60,21 @@ def test_direct_path_small_n(q, n):
         check_int(q.solve(Q, topk=K), oracle.solve(Q, method=oracle.DIRECT, topk=K))
 
 
+# Integer kernels: packed 16-bit lanes (chosen first for these small entries), FP32 lanes, int32.
+LANES = {"i16p": {}, "i32f": {"QUBO_NO_I16P": "1"}, "i32": {"QUBO_NO_I16P": "1", "QUBO_NO_I32F": "1"}}
+
+
 @pytest.mark.parametrize("n", [14, 15, 16, 19, 22, 26])
 @pytest.mark.parametrize("topk", [0, 1, 16])
-def test_int_parity(q, n, topk):
+@pytest.mark.parametrize("lanes", list(LANES))
+def test_int_parity(q, n, topk, lanes, monkeypatch):
+    for k, v in LANES[lanes].items():
+        monkeypatch.setenv(k, v)
     for seed in range(2):
         Q = wl.upper_int(n, -30, 30, seed=1000 * n + seed)
-        check_int(q.solve(Q, topk=topk), oracle.solve(Q, topk=topk))
+        r = q.solve(Q, topk=topk)
+        assert r.info["acc"] == lanes
+        check_int(r, oracle.solve(Q, topk=topk))
 
 
 def test_full_nonsymmetric_int_q(q):
@@ -78,7 +87,7 @@ def test_config1_n24(q):
     Q = wl.config1()
     r = q.solve(Q)
     check_int(r, oracle.solve(Q, method=oracle.DIRECT))
-    assert r.info["states_scanned"] == 1 << 24 and r.info["acc"] in ("i32", "i32f")
+    assert r.info["states_scanned"] == 1 << 24 and r.info["acc"] in ("i32", "i32f", "i16p")
 
 
 @pytest.mark.parametrize("walk_bits", [4, 5, 8, 11, 13])
@@ -275,9 +284,14 @@ def test_time_limit_returns_timeout(q):
 def test_scan_variants_agree(q, variant, monkeypatch):
     monkeypatch.setenv("QUBO_SCAN_VARIANT", str(variant))
     Q = wl.upper_int(27, -300, 300, seed=90)
-    check_int(q.solve(Q, topk=16), oracle.solve(Q, topk=16))
     Qk1 = wl.upper_int(26, -300, 300, seed=91)
-    check_int(q.solve(Qk1), oracle.solve(Qk1))
+    for lanes in ("i32f", "i32"):
+        for k, v in LANES[lanes].items():
+            monkeypatch.setenv(k, v)
+        r = q.solve(Q, topk=16)
+        assert r.info["acc"] == lanes
+        check_int(r, oracle.solve(Q, topk=16))
+        check_int(q.solve(Qk1), oracle.solve(Qk1))
     Qf = wl.sk_float32(25, seed=92)
     r = q.solve(Qf, topk=8)
     assert r.info["acc"] == "f32"
@@ -419,6 +433,7 @@ def test_window_through_overflow_split(q):
 # --- integer energies in FP32 lanes versus the int32 kernel -----------------------------------
 
 def test_int32_kernel_when_fp32_lanes_disabled(q, monkeypatch):
+    monkeypatch.setenv("QUBO_NO_I16P", "1")
     monkeypatch.setenv("QUBO_NO_I32F", "1")
     for n, seed in ((22, 1), (26, 2), (27, 3)):
         Q = wl.upper_int(n, -1000, 1000, seed=seed)
@@ -443,9 +458,10 @@ def plan_bound(Q, suffix_bits, walk_bits):
 
 
 @pytest.mark.parametrize("lim", [60000, 95000, 100000, 105000, 120000])
-def test_fp32_lanes_chosen_exactly_when_bounded(q, lim):
+def test_fp32_lanes_chosen_exactly_when_bounded(q, lim, monkeypatch):
     """Entries sized around the 2^24 bound: the FP32-lane scan is used exactly when the run's
     plan keeps S_nf + 2 S_ww + 2 below 2^24, and the results are bit-exact either way."""
+    monkeypatch.setenv("QUBO_NO_I16P", "1")
     Q = wl.upper_int(27, -lim, lim, seed=9)
     r = q.solve(Q, topk=8, walk_bits=5)  # the same plan for either kernel (both 9 suffix bits)
     check_int(r, oracle.solve(Q, topk=8))
