@@ -8,7 +8,7 @@ instance with its top `--fix-bits` code bits fixed (2^(50-fix_bits) states); con
 take consecutive sub-cubes, so 2^fix_bits steps cover the whole instance.  The rate is states
 per second (2^n / total time, the paper's convention, Sec. 5.3).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n50_int32|n44_fp32|batched]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n50_int32|n44_fp32|maxcut_n48|batched]
   python bench.py --impl reference ...   (the CPU oracle on the host cores, same workload)
 
 Under torchrun every rank takes disjoint sub-cubes (no data-path collective; weak scaling).
@@ -36,6 +36,9 @@ LANES_PER_SM = 128          # FP32/INT32 lanes per Blackwell SM
 ALG_OPS_PER_STATE = 2       # one add and one min per state (Sec. 3.2; Sec. 4.2 on the min)
 PAPER_CONTEXT = "7.47e12 states/s, int16 energies, 1x H100 (paper Tab. 1); other machine and dtype"
 PROFILE_JSON = os.path.join(ROOT, "profiles", "scan_kernel_counters.json")
+# arithmetic type of each accumulator the library reports (integer results are exact in all)
+ACC_DTYPE = {"i32": "int32", "i64": "int64", "f32": "f32", "f64": "f64", "i32f": "f32 (integer-valued)",
+             "i16p": "u16x2 (integer-valued, packed)"}
 
 
 def log(*a):
@@ -62,6 +65,13 @@ def make_workload(name: str, fix_bits: int | None):
                             "entries": "symmetric FP32, off-diagonal N(0,1)/sqrt(44), diagonal N(0,1)",
                             "anchor": "re-anchored at every unit start: 2^10 Gray steps per walk",
                             "step": f"one sub-cube of 2^{44 - fb} states (top {fb} code bits fixed)"})
+    if name == "maxcut_n48":
+        fb = 6 if fix_bits is None else fix_bits
+        return dict(name=name, Q=wl.maxcut_qubo(48, 0.5, seed=48), n=48, topk=16, fix_bits=fb,
+                    metric="states/s (n=48 Max-Cut QUBO)", unit="states/s", dtype="int32",
+                    config={"workload": "maxcut_n48_top16", "n": 48, "topk": 16, "seed": 48,
+                            "entries": "Max-Cut of G(48, 0.5), edge weights +-1 (int16)",
+                            "step": f"one sub-cube of 2^{48 - fb} states (top {fb} code bits fixed)"})
     if name == "batched":
         return dict(name=name, Qs=wl.config4(), topk=0, metric="instances/s (4096 QUBOs, n uniform in 16..32)",
                     unit="instances/s", dtype="int32",
@@ -256,7 +266,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n50_int32", choices=["n50_int32", "n44_fp32", "batched"])
+    ap.add_argument("--workload", default="n50_int32", choices=["n50_int32", "n44_fp32", "maxcut_n48", "batched"])
     ap.add_argument("--fix-bits", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-loop", action="store_true",
@@ -418,15 +428,19 @@ def main():
         per_launch_states = states_per_step
     else:
         per_launch_states = states_per_step
+    acc = infos[0].get("acc", "i32")
+    W["dtype"] = ACC_DTYPE.get(acc, acc)
+    # the packed scan holds two 16-bit columns in each 32-bit lane: twice the lane-ops per cycle
+    halves = 2 if acc == "i16p" else 1
     achieved = ALG_OPS_PER_STATE * per_launch_states / mean_scan / 1e9
     clk_max = (clocks or {}).get("sm_max_mhz") or 2070.0
-    peak = sms * LANES_PER_SM * clk_max * 1e6 / 1e9
+    peak = halves * sms * LANES_PER_SM * clk_max * 1e6 / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
             "traffic": None, "kernel": "scan_kernel",
-            "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x {clk_max:.0f} MHz; 2 ops/state (add + min)"}
+            "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes" + (" x 2 packed 16-bit halves" if halves == 2 else "")
+                          + f" x {clk_max:.0f} MHz; 2 ops/state (add + min)"}
     if clocks and clocks.get("sm_mhz"):
-        roof["frac_at_sampled_clock"] = achieved / (sms * LANES_PER_SM * clocks["sm_mhz"] * 1e-3)
-    acc = infos[0].get("acc", "i32")
+        roof["frac_at_sampled_clock"] = achieved / (halves * sms * LANES_PER_SM * clocks["sm_mhz"] * 1e-3)
     prof = profile_counters(acc)
     if prof:
         # DRAM bytes per launch, scaled from the captured launch by the states it processed

@@ -122,13 +122,20 @@ int acc_suffix_bits(Acc a, int variant)
 // Columns held by one thread (two per word in the packed scan).
 int acc_cols_per_thread(Acc a, int variant)
 {
-    return cols_per_thread(acc_bytes(a), variant) * (a == ACC_I16P ? 2 : 1);
+    return a == ACC_I16P ? 2 * packed_words(variant) : cols_per_thread(acc_bytes(a), variant);
+}
+
+// Walked rows a compiled variant keeps in registers (a walk needs at least one more bit).
+int reg_rows_of(Acc a, int variant)
+{
+    const int v = variant >= 0 && variant < kScanVariants ? variant : 0;
+    return a == ACC_I16P ? kPackedRegRows[v] : kVariantRegRows[acc_bytes(a) == 4 ? v : 0];
 }
 
 // Walked rows the run's kernel variant keeps in registers (a walk needs at least one more bit).
 int variant_reg_rows(const HostInst &h)
 {
-    return kVariantRegRows[acc_bytes(h.acc) == 4 && h.variant >= 0 && h.variant < kScanVariants ? h.variant : 0];
+    return reg_rows_of(h.acc, h.variant);
 }
 
 int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bits)
@@ -2158,7 +2165,7 @@ int qubo_autotune(const void *Q_host, int n, qubo_dtype dtype, int fix_bits, qub
             c.walk_bits = L;
             HostInst t = h;
             t.variant = v;
-            if (plan(t, fix_bits, 0, 0, L) || kVariantRegRows[v] + 1 > L)
+            if (plan(t, fix_bits, 0, 0, L) || reg_rows_of(t.acc, v) + 1 > L)
                 continue;
             double rate = 0.0;
             for (int rep = 0; rep < 2; ++rep) {  // the first run warms the workspace
@@ -2213,7 +2220,7 @@ int qubo_autotune_batched(const void *Q_packed, const int *n, const size_t *offs
             h.variant = acc_bytes(acc) == 4 ? v : 0;
             const int B = acc_suffix_bits(acc, h.variant);
             const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
-            const int walk = h.n - B >= kVariantRegRows[v] + 1 ? std::min(wmax, h.n - B) : 0;
+            const int walk = h.n - B >= reg_rows_of(acc, v) + 1 ? std::min(wmax, h.n - B) : 0;
             if (plan(h, 0, 0, 0, walk))
                 ok = false;
             else if (!h.small && ((acc == ACC_I16P && !i16p_exact(h)) || (acc == ACC_I32F && !i32f_exact(h, &h.clampC))))

@@ -15,21 +15,31 @@ enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4, ACC_I32
 // flip has a compile-time sign.  A plan needs walk_bits >= kRegRows + 1.
 constexpr int kRegRows = 4;
 // Compiled scan variants of the 4-byte accumulators: columns per thread S, register rows,
-// minimum resident blocks per SM, how integer adds are issued (0: compiler's choice, 1: all as
-// multiply-adds by a runtime 1 on the FMA pipe, 2: a quarter as 3-input adds with a runtime 0 on
-// the ALU pipe and the rest as multiply-adds), 2- or 3-input mins.  The 8-byte accumulators
+// minimum resident blocks per SM, how the adds are issued (0: compiler's choice, 1: integer adds
+// as multiply-adds by a runtime 1 on the FMA pipe, 2: a quarter of the integer adds as 3-input
+// adds with a runtime 0 on the ALU pipe, 4: FP32 adds as paired f32x2 operations, two columns
+// per instruction, 5, 6, 7: a half, a quarter or three quarters of them paired; a mode that
+// does not apply to the column type leaves the choice to the compiler), 2- or 3-input mins.  The 8-byte accumulators
 // compile one variant: S = 16 with variant 0's register rows, blocks and min inputs.
 constexpr int kScanVariants = 8;
-constexpr int kVariantCols[kScanVariants] = {32, 32, 32, 16, 16, 32, 32, 16};
-constexpr int kVariantRegRows[kScanVariants] = {3, 2, 2, 3, 4, 2, 3, 2};
-constexpr int kVariantMinBlocks[kScanVariants] = {2, 2, 2, 3, 3, 3, 2, 3};
-constexpr int kVariantAddMode[kScanVariants] = {0, 0, 2, 0, 0, 0, 0, 0};
-constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 2, 3};
+constexpr int kVariantCols[kScanVariants] = {32, 16, 16, 16, 16, 16, 32, 16};
+constexpr int kVariantRegRows[kScanVariants] = {3, 4, 4, 3, 4, 4, 3, 4};
+constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 3, 3, 3, 3, 2, 3};
+constexpr int kVariantAddMode[kScanVariants] = {0, 6, 7, 0, 0, 4, 4, 5};
+constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 3, 3};
 // Default variant per 4-byte accumulator (measured on GB300; see the profiles).
 constexpr int kDefaultVariantI32 = 3;
-constexpr int kDefaultVariantF32 = 4;
-constexpr int kDefaultVariantI32F = 4;
-constexpr int kDefaultVariantI16P = 3;
+constexpr int kDefaultVariantF32 = 7;
+constexpr int kDefaultVariantI32F = 1;
+constexpr int kDefaultVariantI16P = 1;
+// Compiled variants of the packed 16-bit scan: S words per thread (2 S columns), register rows,
+// minimum resident blocks per SM, and how the adds are issued (0: compiler's choice; 2 and 3: one
+// add in four or in eight as a 3-input add with a runtime 0, which the ALU pipe executes, so
+// that the ALU and FMA pipes share the adds).  All use 3-input mins.
+constexpr int kPackedWords[kScanVariants] = {16, 16, 16, 16, 16, 32, 32, 16};
+constexpr int kPackedRegRows[kScanVariants] = {3, 3, 3, 3, 3, 2, 2, 2};
+constexpr int kPackedMinBlocks[kScanVariants] = {3, 3, 3, 4, 4, 2, 2, 4};
+constexpr int kPackedAddMode[kScanVariants] = {0, 3, 2, 0, 3, 0, 3, 3};
 // Threads per block of the scan kernel (4 warps; every warp owns one work unit at a time).
 constexpr int kScanThreads = 128;
 // Longest Gray walk inside one work unit (also the FP32 re-anchoring period).
@@ -116,8 +126,12 @@ constexpr int suffix_bits(int bytes, int variant = 0)
 {
     return cols_per_thread(bytes, variant) == 32 ? 10 : 9;
 }
-// The packed 16-bit scan holds two columns in each of its S words: one more suffix bit.
-constexpr int packed_suffix_bits(int variant) { return suffix_bits(4, variant) + 1; }
+// The packed 16-bit scan holds two columns in each of its S words: log2(64 S) suffix bits.
+constexpr int packed_words(int variant)
+{
+    return kPackedWords[(variant >= 0 && variant < kScanVariants) ? variant : 0];
+}
+constexpr int packed_suffix_bits(int variant) { return packed_words(variant) == 32 ? 11 : 10; }
 
 struct i32f;  // tag of the integer-in-FP32 accumulator (scan_impl.cuh)
 struct i16p;  // tag of the packed 16-bit accumulator (scan_impl.cuh)

@@ -8,10 +8,9 @@ namespace {
 template <int VAR, bool K1>
 constexpr auto kernel_of()
 {
-    constexpr int kS = cols_per_thread(4, VAR);  // words per thread
+    constexpr int kS = packed_words(VAR);  // words per thread, two columns each
     static_assert(ilog2c(64 * kS) == packed_suffix_bits(VAR), "suffix bits must match the column layout");
-    return scan_kernel<i16p, kS, kVariantRegRows[VAR], K1, kVariantMinBlocks[VAR], kVariantAddMode[VAR],
-                       kVariantMinInputs[VAR]>;
+    return scan_kernel<i16p, kS, kPackedRegRows[VAR], K1, kPackedMinBlocks[VAR], kPackedAddMode[VAR], 3>;
 }
 
 template <bool K1>

@@ -267,6 +267,27 @@ __device__ __forceinline__ double emin3(double a, double b, double c) { return f
 __device__ __forceinline__ uint32_t emin(uint32_t a, uint32_t b) { return __vminu2(a, b); }
 __device__ __forceinline__ uint32_t emin3(uint32_t a, uint32_t b, uint32_t c) { return __vimin3_u16x2(a, b, c); }
 
+// Paired FP32 arithmetic (one instruction updates two columns): x += a, y += b; x -= a, y -= b;
+// x += a * s, y += b * s.  Each lane is rounded exactly as the scalar operation would be.
+__device__ __forceinline__ void add_f32x2(float &x, float &y, float a, float b)
+{
+    asm("{\n\t.reg .b64 p, q;\n\tmov.b64 p, {%0, %1};\n\tmov.b64 q, {%2, %3};\n\t"
+        "add.rn.f32x2 p, p, q;\n\tmov.b64 {%0, %1}, p;\n\t}"
+        : "+f"(x), "+f"(y) : "f"(a), "f"(b));
+}
+__device__ __forceinline__ void sub_f32x2(float &x, float &y, float a, float b)
+{
+    asm("{\n\t.reg .b64 p, q;\n\tmov.b64 p, {%0, %1};\n\tmov.b64 q, {%2, %3};\n\t"
+        "sub.rn.f32x2 p, p, q;\n\tmov.b64 {%0, %1}, p;\n\t}"
+        : "+f"(x), "+f"(y) : "f"(a), "f"(b));
+}
+__device__ __forceinline__ void fma_f32x2(float &x, float &y, float a, float b, float s)
+{
+    asm("{\n\t.reg .b64 p, q, r;\n\tmov.b64 p, {%0, %1};\n\tmov.b64 q, {%2, %3};\n\tmov.b64 r, {%4, %4};\n\t"
+        "fma.rn.f32x2 p, q, r, p;\n\tmov.b64 {%0, %1}, p;\n\t}"
+        : "+f"(x), "+f"(y) : "f"(a), "f"(b), "f"(s));
+}
+
 // min over N register values: a tree of 2-input (MINM == 2) or 3-input (MINM == 3) mins.
 template <class T, int MINM, int N>
 __device__ __forceinline__ T tree_min(const T (&E)[N])
@@ -472,6 +493,7 @@ __device__ __forceinline__ void column_fields(F f0, int lane, F &lin_t, F (&lin_
 }
 
 // ---- one work unit: all 2^(B+L) states with fixed bits x_f = unit --------------------------------
+// ADDM == 4 issues FP32 column adds as paired f32x2 operations (two columns per instruction).
 // ADDM == 1 issues the integer adds as multiply-adds by a runtime +-1 (fused multiply-add
 // pipe) so that the integer ALU pipe is left to the mins; ADDM == 2 sends a quarter of them to
 // the ALU pipe as 3-input adds; MINM selects 2- or 3-input mins.
@@ -555,9 +577,15 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
         for (int g = 0; g < G; ++g) {
             TC mv[V];
             vload<TC>(row + (g * 32 + lane) * V, mv);
+            if constexpr (ADDM >= 4 && std::is_same_v<TC, float>) {
 #pragma unroll
-            for (int e = 0; e < V; ++e)
-                E[g * V + e] = E[g * V + e] + sg * mv[e];
+                for (int e = 0; e < V; e += 2)
+                    fma_f32x2(E[g * V + e], E[g * V + e + 1], mv[e], mv[e + 1], sg);
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    E[g * V + e] = E[g * V + e] + sg * mv[e];
+            }
         }
         P = P + (TP)sgn * wsm[kk];
         u = Treg + mu - P;
@@ -573,15 +601,35 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
         TC elv[V];
         bool hit = false;
         TP Pmid = P;
-        // Fast path: per step one add per column, a min over the columns and one compare whose
-        // outcome is only OR-ed into `hit`, so consecutive steps can overlap freely.
+        // Running minima over the steps of each half body (the row-RC flip between the halves
+        // moves the threshold) of (minimum over the columns + E_L of the step); a column can be
+        // at or below the threshold exactly when its half's minimum is at or below uc.
+        TC acc_lo, acc_hi, mprev;
+        // Fast path: per step one add per column, a min over the columns, one add of the step's
+        // E_L and half a 3-input min into the running minimum; one compare per half body.
         static_for<BODY>([&](auto pc) {
             constexpr int p = decltype(pc)::value;
             if constexpr (p > 0) {
                 constexpr int kk = ctzc(p);
                 if constexpr (kk < RC) {
                     constexpr bool neg = (p >> (kk + 1)) & 1;
-                    if constexpr (ADDM == 1 && kIntCols) {
+                    if constexpr (ADDM >= 4 && std::is_same_v<TC, float>) {
+                        // pairs taken as f32x2: all (4), every 2nd (5), every 4th (6), 3 of 4 (7)
+#pragma unroll
+                        for (int q = 0; q < S; q += 2) {
+                            const int pr = q / 2;
+                            if (ADDM == 4 || (ADDM == 5 && pr % 2 == 0) || (ADDM == 6 && pr % 4 == 0) ||
+                                (ADDM == 7 && pr % 4 != 0)) {
+                                if constexpr (neg)
+                                    sub_f32x2(E[q], E[q + 1], Mr[kk][q], Mr[kk][q + 1]);
+                                else
+                                    add_f32x2(E[q], E[q + 1], Mr[kk][q], Mr[kk][q + 1]);
+                            } else {
+                                E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
+                                E[q + 1] = neg ? E[q + 1] - Mr[kk][q + 1] : E[q + 1] + Mr[kk][q + 1];
+                            }
+                        }
+                    } else if constexpr (ADDM == 1 && kIntCols) {
                         const TC mul = neg ? -(TC)a.one : (TC)a.one;
 #pragma unroll
                         for (int q = 0; q < S; ++q)
@@ -608,9 +656,19 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
             }
             if constexpr (p % V == 0)
                 vload<TC>(ELp + i0 + p, elv);
-            const TC t = uc - elv[p % V];
-            hit |= tree_min<TC, MINM, S>(E) <= t;
+            const TC mp = tree_min<TC, MINM, S>(E) + elv[p % V];
+            constexpr int HALF = BODY / 2, ph = p % HALF;
+            TC &acc = p < HALF ? acc_lo : acc_hi;
+            if constexpr (ph % 2 == 0)
+                mprev = mp;
+            else if constexpr (ph == 1)
+                acc = emin(mprev, mp);
+            else
+                acc = emin3(acc, mprev, mp);
+            if constexpr (p == HALF - 1)
+                hit = acc_lo <= uc;  // before the row-RC flip moves uc
         });
+        hit = hit || acc_hi <= uc;
         if (hit) {
             // Slow path (rare): rebuild every step of this body from the body-end registers and
             // record each column at or below the threshold.  Step p differs from the last step
@@ -801,17 +859,18 @@ __device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &
         int32_t elv[V];
         bool hit = false;
         int32_t Pmid = P;
+        int32_t acc_lo, acc_hi, mprev;  // as in scan_unit, in lane units
         static_for<BODY>([&](auto pc) {
             constexpr int p = decltype(pc)::value;
             if constexpr (p > 0) {
                 constexpr int kk = ctzc(p);
                 if constexpr (kk < RC) {
                     constexpr bool neg = (p >> (kk + 1)) & 1;
-                    if constexpr (ADDM == 2) {
+                    if constexpr (ADDM == 2 || ADDM == 3) {
                         const uint32_t z = (uint32_t)a.zero;
 #pragma unroll
                         for (int q = 0; q < S; ++q) {
-                            if (q % 4 == 0)
+                            if (q % (ADDM == 2 ? 4 : 8) == 0)
                                 E[q] = neg ? (E[q] - Mr[kk][q]) + z : (E[q] + Mr[kk][q]) + z;
                             else
                                 E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
@@ -828,10 +887,20 @@ __device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &
             }
             if constexpr (p % V == 0)
                 vload<int32_t>(ELp + i0 + p, elv);
-            const int32_t t = u - elv[p % V];
             const uint32_t mw = tree_min<uint32_t, MINM, S>(E);
-            hit |= min((int32_t)(mw & 0xffffu), (int32_t)(mw >> 16)) <= t;
+            const int32_t mp = min((int32_t)(mw & 0xffffu), (int32_t)(mw >> 16)) + elv[p % V];
+            constexpr int HALF = BODY / 2, ph = p % HALF;
+            int32_t &acc = p < HALF ? acc_lo : acc_hi;
+            if constexpr (ph % 2 == 0)
+                mprev = mp;
+            else if constexpr (ph == 1)
+                acc = min(mprev, mp);
+            else
+                acc = __vimin3_s32(acc, mprev, mp);
+            if constexpr (p == HALF - 1)
+                hit = acc_lo <= u;
         });
+        hit = hit || acc_hi <= u;
         if (hit) {
             const int iend = i0 + BODY - 1;
             const int gend = iend ^ (iend >> 1);
