@@ -170,6 +170,39 @@ int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets
                        size_t states_cap_per_inst, uint64_t *out_topk, void *out_topk_E,
                        qubo_result *info, void *stream);
 
+/*
+ * Instances wider than one scan (the paper's scaling by fixed bits, Sec. 4.3, with the
+ * subproblem of Sec. 3.3.1): variables 0..n_inner-1 are scanned on the GPU, variables
+ * n_inner..n-1 (the outer ones, at most 64) are fixed, one sub-problem per outer value v
+ * (variable n_inner + f = bit f of v).  Sub-problem v keeps the couplings among the inner
+ * variables, adds to each inner diagonal the couplings to the set outer variables, and carries
+ * the constant c(v) of the set outer variables; its minimum plus c(v) is the minimum over its
+ * 2^n_inner states.  The call solves the outer values outer_begin .. outer_begin+outer_count-1
+ * (contiguous ranges shard over callers; qubo_merge-style merging of the results is by energy,
+ * then code) and returns the minimum over all of them, the exact tie count, the smallest tie
+ * codes and the K lowest states.  Sub-problems of n_inner <= 40 variables run as batches of up
+ * to 4096 in one persistent launch each; wider ones run one after another.
+ *   Q_host      n x n row-major host matrix of type dtype, n_inner <= n <= QUBO_WIDE_MAX_N,
+ *               n - n_inner <= 64, 1 <= n_inner <= 64.
+ *   opt         topk, flags, margin and time_limit_s are used (fix_bits must be 0); may be NULL.
+ *   out_min     int64_t* (integer Q) or double* (float Q: the FP64 minimum of the sub-problem
+ *               plus c(v) in FP64).
+ *   out_states  host, 2 * states_cap words: state t is the 128-bit code (word 2t = bits 0..63,
+ *               word 2t+1 = bits 64..127; bit i = variable i), ascending.
+ *   out_n_ties  host (may be NULL): the exact number of minimisers in the range.
+ *   out_topk    host, 2 * topk words (128-bit codes as above), ordered by (E, code);
+ *               out_topk_E host, topk energies (int64_t or double).
+ *   info        optional: totals over the sub-problems (states, candidates, device times,
+ *               launches, copies) and the last sub-problem's plan; info->n = n.
+ * Returns QUBO_OK, QUBO_TRUNCATED (more ties than states_cap), QUBO_ERR_TIMEOUT (the time limit
+ * passed; checked between sub-problem groups and inside wide sub-problems) or an error.
+ */
+#define QUBO_WIDE_MAX_N 128
+int qubo_solve_wide(const void *Q_host, int n, qubo_dtype dtype, int n_inner, uint64_t outer_begin,
+                    uint64_t outer_count, const qubo_options *opt, void *out_min, uint64_t *out_states,
+                    size_t states_cap, uint64_t *out_n_ties, uint64_t *out_topk, void *out_topk_E,
+                    qubo_result *info, void *stream);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Device-resident batches, replayed as one CUDA graph.                                      */
 /* ---------------------------------------------------------------------------------------- */

@@ -60,6 +60,8 @@ def _load():
     lib.oracle_solve_f64.restype = i32
     lib.oracle_solve_f64.argtypes = [P, i32, i32, i32, u64, i32, u64, i32, P, P, P, P, P, P, P, P]
     lib.oracle_max_threads.restype = i32
+    lib.oracle_reduce_i64.argtypes = [P, i32, i32, P, P, P]
+    lib.oracle_reduce_f64.argtypes = [P, i32, i32, P, P, P]
     _lib = lib
     return lib
 
@@ -160,6 +162,30 @@ def solve(Q, method: int = GRAY, topk: int = 0, cap: int = 1 << 16, fix_bits: in
         raise RuntimeError(f"oracle solve failed with status {rc}")
     k = int(nk[0])
     return OracleResult(mval, int(nties[0]), ties[: int(nw[0])].copy(), tk[:k].copy(), tkE[:k].copy(), nc)
+
+
+def reduce(Q, m: int, fixed):
+    """Sub-problem over variables 0..m-1 with variables m..n-1 fixed (``fixed``: an int whose
+    bit f is variable m + f, or a sequence of 0/1).  Returns (R, c): R is an m x m
+    upper-triangular matrix and E_Q(x) = E_R(x_0..x_{m-1}) + c for every x with that fixed part
+    (oracle.c states the split)."""
+    U = fold(Q)
+    n = U.shape[0]
+    if isinstance(fixed, (int, np.integer)):
+        xf = np.array([(int(fixed) >> f) & 1 for f in range(n - m)], dtype=np.uint8)
+    else:
+        xf = np.ascontiguousarray(fixed, dtype=np.uint8)
+    if xf.shape != (n - m,):
+        raise ValueError("fixed must give the n - m fixed variables")
+    R = np.zeros((m, m), dtype=U.dtype)
+    lib = _load()
+    if U.dtype == np.float64:
+        c = ctypes.c_double()
+        lib.oracle_reduce_f64(_ptr(U), n, m, _ptr(xf), _ptr(R), ctypes.byref(c))
+        return R, float(c.value)
+    c = ctypes.c_int64()
+    lib.oracle_reduce_i64(_ptr(U), n, m, _ptr(xf), _ptr(R), ctypes.byref(c))
+    return R, int(c.value)
 
 
 def max_threads() -> int:

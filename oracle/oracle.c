@@ -631,4 +631,52 @@ int oracle_solve_f64(const double *Q, int n, int method, int fix_bits, uint64_t 
 }
 
 /* Number of threads OpenMP would use by default (the host cores the oracle runs on). */
+/* ------------------------------------------------------------------------------------ */
+/* Sub-problem with fixed variables (Sec. 3.3.1, x = (x_r, x_f); Sec. 4.3 applies it to    */
+/* instances wider than one scan).                                                        */
+/* ------------------------------------------------------------------------------------ */
+
+/*
+ * Variables m..n-1 are fixed to xf[0..n-m-1] (one byte per variable, 0 or 1); n may exceed 64.
+ * Splitting the folded objective sum_{i<=j} U_ij x_i x_j by where i and j lie:
+ *   both free (i <= j < m)        -> R_ij = U_ij, kept as a QUBO over x_0..x_{m-1};
+ *   i free, j fixed (i < m <= j)  -> x_i * U_ij * xf_j: linear in x_i, so R_ii gains U_ij xf_j;
+ *   both fixed (m <= i <= j)      -> U_ij xf_i xf_j, summed into the constant c.
+ * Then E(x) = sum_{i<=j<m} R_ij x_i x_j + c for every x whose fixed part is xf.
+ * U is the folded n x n matrix; R is m x m (upper-triangular, zeros below the diagonal).
+ */
+void oracle_reduce_i64(const int64_t *U, int n, int m, const uint8_t *xf, int64_t *R, int64_t *c)
+{
+    int64_t cc = 0;
+    memset(R, 0, sizeof(int64_t) * (size_t)m * m);
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) {
+            const int64_t u = U[(size_t)i * n + j];
+            if (j < m)
+                R[(size_t)i * m + j] += u;
+            else if (i < m)
+                R[(size_t)i * m + i] += xf[j - m] ? u : 0;
+            else
+                cc += (xf[i - m] && xf[j - m]) ? u : 0;
+        }
+    *c = cc;
+}
+
+void oracle_reduce_f64(const double *U, int n, int m, const uint8_t *xf, double *R, double *c)
+{
+    double cc = 0.0;
+    memset(R, 0, sizeof(double) * (size_t)m * m);
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) {
+            const double u = U[(size_t)i * n + j];
+            if (j < m)
+                R[(size_t)i * m + j] += u;
+            else if (i < m)
+                R[(size_t)i * m + i] += xf[j - m] ? u : 0.0;
+            else
+                cc += (xf[i - m] && xf[j - m]) ? u : 0.0;
+        }
+    *c = cc;
+}
+
 int oracle_max_threads(void) { return omp_get_max_threads(); }

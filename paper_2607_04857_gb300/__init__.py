@@ -32,8 +32,9 @@ EXPORTS = (
     "qubo_problem_fetch", "qubo_problem_destroy", "qubo_merge", "qubo_strerror", "qubo_abort",
     "qubo_abort_clear", "qubo_device_sm_count", "qubo_version", "qubo_solve_noalloc",
     "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_batch_destroy",
-    "qubo_autotune", "qubo_autotune_batched", "qubo_autotune_clear", "qubo_solve_window",
+    "qubo_autotune", "qubo_autotune_batched", "qubo_autotune_clear", "qubo_solve_window", "qubo_solve_wide",
 )
+WIDE_MAX_N = 128
 NOALLOC_MAX_N = 40
 NOALLOC_MAX_TIES = 4096
 
@@ -117,6 +118,7 @@ def load_library(path: str = LIB_PATH):
     lib.qubo_autotune.argtypes = [P, I, I, I, P]
     lib.qubo_solve_window.argtypes = [P, I, I, ctypes.c_double, P, P, P, SZ, P, P, P]
     lib.qubo_autotune_batched.argtypes = [P, P, P, I, I, P]
+    lib.qubo_solve_wide.argtypes = [P, I, I, I, U64, U64, P, P, P, SZ, P, P, P, P, P]
     lib.qubo_autotune_clear.restype = None
     lib.qubo_strerror.argtypes = [I]
     lib.qubo_strerror.restype = ctypes.c_char_p
@@ -126,7 +128,7 @@ def load_library(path: str = LIB_PATH):
     for name in ("qubo_solve", "qubo_solve_ex", "qubo_solve_batched", "qubo_problem_create", "qubo_problem_run",
                  "qubo_problem_fetch", "qubo_merge", "qubo_device_sm_count", "qubo_solve_noalloc",
                  "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_autotune",
-                 "qubo_autotune_batched", "qubo_solve_window"):
+                 "qubo_autotune_batched", "qubo_solve_window", "qubo_solve_wide"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -354,6 +356,35 @@ class Batch:
 
     def __del__(self):
         self.close()
+
+
+def solve_wide(Q, n_inner: int, outer_begin: int = 0, outer_count: int | None = None, topk: int = 0,
+               states_cap: int = 64, plain: bool = False, margin: float = 0.0, time_limit: float = 0.0,
+               stream=None) -> Result:
+    """Minimum over the sub-problems of a wide instance (qubo_solve_wide): variables
+    0..n_inner-1 scanned, variables n_inner..n-1 fixed to each outer value in
+    [outer_begin, outer_begin + outer_count) (all 2^(n - n_inner) values by default).  State
+    codes are Python ints (bit i = variable i); ties and topk are lists of them."""
+    lib = load_library()
+    Qm, dt = as_qubo_matrix(Q)
+    n = Qm.shape[0]
+    if outer_count is None:
+        outer_count = (1 << (n - n_inner)) - outer_begin
+    isf = dt in (QUBO_F32, QUBO_F64)
+    o = Options(topk=topk, flags=QUBO_FLAG_PLAIN if plain else 0, margin=margin, time_limit_s=time_limit)
+    mn = np.zeros(1, dtype=np.float64 if isf else np.int64)
+    st_codes = np.zeros(2 * max(states_cap, 1), dtype=np.uint64)
+    nt = np.zeros(1, dtype=np.uint64)
+    tk = np.zeros(2 * max(topk, 1), dtype=np.uint64)
+    tkE = np.zeros(max(topk, 1), dtype=np.float64 if isf else np.int64)
+    info = ResultInfo()
+    st = _check(lib.qubo_solve_wide(_ptr(Qm), n, dt, n_inner, outer_begin, outer_count, ctypes.byref(o), _ptr(mn),
+                                    _ptr(st_codes), states_cap, _ptr(nt), _ptr(tk), _ptr(tkE), ctypes.byref(info),
+                                    _stream_ptr(stream)), "qubo_solve_wide")
+    wide = lambda a, k: [int(a[2 * t]) | (int(a[2 * t + 1]) << 64) for t in range(k)]  # noqa: E731
+    k = int(info.n_topk)
+    return Result(float(mn[0]) if isf else int(mn[0]), int(nt[0]), wide(st_codes, int(info.n_written)),
+                  wide(tk, k), tkE[:k].copy(), st, info.as_dict())
 
 
 def solve_window(Q, window: float, cap: int = 1 << 16, fix_bits: int = 0, fix_value: int = 0, plain: bool = False,

@@ -1414,6 +1414,8 @@ void fill_plan_info(const HostInst &h, const SolveStats &stats, double t0, qubo_
     info->passes = stats.passes;
 }
 
+int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order);
+
 // Fold, bound, plan and threshold every instance of a batch (in parallel on the host), one
 // accumulator for all, and the launch order (longest work first, so the persistent launch's
 // tail is short).
@@ -1446,6 +1448,24 @@ int batch_prepare(const void *Q_packed, const int *n, const size_t *offsets, int
     for (int i = 0; i < count; ++i)
         if (pst[i])
             return pst[i];
+    return batch_plan(hs, topk, order);
+}
+
+// Plan every prepared instance of a batch (in parallel on the host): one accumulator for all,
+// thresholds, and the launch order (longest work first, so the persistent launch's tail is
+// short).
+int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
+{
+    const int count = (int)hs.size();
+    std::vector<int> pst(count, QUBO_OK);
+    auto parallel = [&](auto &&fn) {
+        const int nt = std::max(1, std::min<int>(count / 64 + 1, (int)std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back(fn, (int)((int64_t)count * t / nt), (int)((int64_t)count * (t + 1) / nt));
+        for (auto &x : th)
+            x.join();
+    };
     // one accumulator for the whole batch: the widest any instance needs
     Acc acc = hs[0].acc;
     for (auto &h : hs)
@@ -1519,6 +1539,149 @@ int batch_prepare(const void *Q_packed, const int *n, const size_t *offsets, int
         order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a].states > hs[b].states; });
     return QUBO_OK;
+}
+
+// Solve a planned batch in one persistent launch; parts[i] is instance i's result.  An instance
+// that overflowed the shared candidate buffer (or whose FP32 drift used up the margin) is solved
+// again alone.
+int batch_parts(Workspace &ws, std::vector<HostInst> &hs, const std::vector<int> &order, int topk, size_t cap,
+                cudaStream_t stream, std::vector<Part> &parts, SolveStats &stats)
+{
+    const int count = (int)hs.size();
+    Job j;
+    for (int i : order)
+        j.insts.push_back(&hs[i]);
+    j.acc = hs[0].acc;
+    j.K = topk;
+    j.cap = cap;
+    j.margin = kDefaultMargin;
+    j.variant = hs[0].variant;
+    j.stream = stream;
+    int st;
+    if ((st = job_launch(ws, j)))
+        return st;
+    std::vector<Part> run_parts;
+    double gs = 0.0;
+    if ((st = job_finish(ws, j, run_parts, &gs)))
+        return st;
+    stats.add(j, gs);
+    SolveCfg c;
+    c.K = topk;
+    c.cap = cap;
+    c.variant = j.variant;
+    parts.assign(count, Part());
+    for (int r = 0; r < count; ++r) {
+        const int i = order[r];
+        Part &p = run_parts[r];
+        HostInst &h = hs[i];
+        if (p.overflow || !float_margin_ok(h, p, c.margin)) {
+            // rare: this instance overflowed the shared candidate buffer; solve it alone
+            if (!float_margin_ok(h, p, c.margin))
+                h.acc = ACC_F64;
+            p = Part();
+            if ((st = solve_range(ws, h, 0, 0, c, stream, p, stats, 0.0)))
+                return st;
+        }
+        if (p.scanned != (1ull << h.n) || !p.has)
+            return QUBO_ERR_INTERNAL;
+        parts[i] = std::move(p);
+    }
+    return QUBO_OK;
+}
+
+// Prepare an instance given directly as its folded upper-triangular matrix (a sub-problem of a
+// larger instance): bound check and accumulator as in prepare().
+int prepare_folded(std::vector<int64_t> *Ui, std::vector<double> *Uf, int n, uint32_t flags, HostInst &h)
+{
+    h = HostInst();
+    h.n = n;
+    h.is_float = Uf != nullptr;
+    if (h.is_float) {
+        h.Uf = std::move(*Uf);
+        for (double v : h.Uf)
+            h.beta += std::fabs(v);
+        h.acc = (flags & QUBO_FLAG_PLAIN) ? ACC_F64 : ACC_F32;
+        return QUBO_OK;
+    }
+    h.Ui = std::move(*Ui);
+    int64_t beta = 0;
+    for (int64_t v : h.Ui) {
+        beta += v < 0 ? -v : v;
+        if (beta >= (1ll << 62))
+            return QUBO_ERR_OVERFLOW;
+    }
+    h.beta = (double)beta;
+    h.acc = ((flags & QUBO_FLAG_PLAIN) || beta >= (1ll << 30)) ? ACC_I64 : ACC_I32;
+    return QUBO_OK;
+}
+
+// Result over many sub-problems of a wide instance, with 128-bit state codes (lo, hi words).
+struct WideAcc {
+    bool has = false;
+    bool is_float = false;
+    int64_t min_i = 0;
+    double min_f = 0.0;
+    uint64_t n_ties = 0, scanned = 0, candidates = 0;
+    std::vector<std::pair<uint64_t, uint64_t>> ties;  // (hi, lo), ascending
+    std::vector<std::tuple<double, uint64_t, uint64_t>> topf;  // (E, hi, lo)
+    std::vector<std::tuple<int64_t, uint64_t, uint64_t>> topi;
+};
+
+// Fold a sub-problem result (inner codes, energies without the constant c) into the wide result.
+// Sub-problems must arrive in ascending outer value so that the tie codes stay ascending.
+void wide_add(WideAcc &w, const Part &p, int n_in, uint64_t outer, int64_t ci, double cf, size_t cap, int K)
+{
+    auto code = [&](uint64_t inner) {
+        const uint64_t lo = n_in == 64 ? inner : (inner | (outer << n_in));
+        const uint64_t hi = n_in == 0 ? 0 : (n_in == 64 ? outer : (outer >> (64 - n_in)));
+        return std::make_pair(hi, lo);
+    };
+    const bool fl = p.is_float;
+    const int64_t Ei = p.min_i + ci;
+    const double Ef = p.min_f + cf;
+    w.is_float = fl;
+    w.scanned += p.scanned;
+    w.candidates += p.candidates;
+    const bool lower = !w.has || (fl ? Ef < w.min_f : Ei < w.min_i);
+    const bool equal = w.has && (fl ? Ef == w.min_f : Ei == w.min_i);
+    if (lower) {
+        w.has = true;
+        w.min_i = Ei;
+        w.min_f = Ef;
+        w.n_ties = 0;
+        w.ties.clear();
+    }
+    if (lower || equal) {
+        w.n_ties += p.n_ties;
+        for (uint64_t t : p.ties) {
+            if (w.ties.size() >= cap)
+                break;
+            w.ties.push_back(code(t));
+        }
+    }
+    if (K <= 0)
+        return;
+    if (fl) {
+        std::vector<std::tuple<double, uint64_t, uint64_t>> add, out;
+        for (auto &e : p.topf) {
+            const auto c = code(e.second);
+            add.emplace_back(e.first + cf, c.first, c.second);
+        }
+        std::merge(w.topf.begin(), w.topf.end(), add.begin(), add.end(), std::back_inserter(out));
+        if ((int)out.size() > K)
+            out.resize(K);
+        w.topf.swap(out);
+    } else {
+        std::vector<std::tuple<int64_t, uint64_t, uint64_t>> add, out;
+        for (auto &e : p.topi) {
+            const auto c = code(e.second);
+            add.emplace_back(e.first + ci, c.first, c.second);
+        }
+        std::merge(w.topi.begin(), w.topi.end(), add.begin(), add.end(), std::back_inserter(out));
+        if ((int)out.size() > K)
+            out.resize(K);
+        w.topi.swap(out);
+    }
 }
 
 }  // namespace
@@ -1726,8 +1889,6 @@ int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets
     int st = batch_prepare(Q_packed, n, offsets, count, dtype, topk, hs, order);
     if (st)
         return st;
-    const int variant = hs[0].variant;
-    const Acc acc = hs[0].acc;
     Workspace *ws = nullptr;
     if ((st = resolve_device(&ws)))
         return st;
@@ -1736,42 +1897,14 @@ int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets
     cudaGetDevice(&dev);
     if ((st = ws->init(dev)))
         return st;
-    Job j;
-    for (int i : order)
-        j.insts.push_back(&hs[i]);
-    j.acc = acc;
-    j.K = topk;
-    j.cap = states_cap_per_inst;
-    j.margin = kDefaultMargin;
-    j.variant = variant;
-    j.stream = (cudaStream_t)stream;
-    if ((st = job_launch(*ws, j)))
-        return st;
     std::vector<Part> parts;
-    double gs = 0.0;
-    if ((st = job_finish(*ws, j, parts, &gs)))
+    SolveStats stats;
+    if ((st = batch_parts(*ws, hs, order, topk, states_cap_per_inst, (cudaStream_t)stream, parts, stats)))
         return st;
     int worst = QUBO_OK;
-    SolveCfg c;
-    c.K = topk;
-    c.cap = states_cap_per_inst;
-    c.variant = j.variant;
-    for (int r = 0; r < count; ++r) {
-        const int i = order[r];
-        Part &p = parts[r];
+    for (int i = 0; i < count; ++i) {
+        Part &p = parts[i];
         HostInst &h = hs[i];
-        SolveStats stats;
-        stats.add(j, gs);
-        if (p.overflow || !float_margin_ok(h, p, c.margin)) {
-            // rare: this instance overflowed the shared candidate buffer; solve it alone
-            if (!float_margin_ok(h, p, c.margin))
-                h.acc = ACC_F64;
-            p = Part();
-            if ((st = solve_range(*ws, h, 0, 0, c, (cudaStream_t)stream, p, stats, 0.0)))
-                return st;
-        }
-        if (p.scanned != (1ull << h.n) || !p.has)
-            return QUBO_ERR_INTERNAL;
         void *om = h.is_float ? (void *)((double *)out_min + i) : (void *)((int64_t *)out_min + i);
         void *otke = nullptr;
         if (out_topk_E)
@@ -1788,6 +1921,180 @@ int qubo_solve_batched(const void *Q_packed, const int *n, const size_t *offsets
             worst = std::max(worst, (int)QUBO_TRUNCATED);
     }
     return worst;
+}
+
+int qubo_solve_wide(const void *Q_host, int n, qubo_dtype dtype, int n_inner, uint64_t outer_begin,
+                    uint64_t outer_count, const qubo_options *opt, void *out_min, uint64_t *out_states,
+                    size_t states_cap, uint64_t *out_n_ties, uint64_t *out_topk, void *out_topk_E, qubo_result *info,
+                    void *stream)
+{
+    const double t0 = now_s();
+    qubo_options o{};
+    if (opt)
+        o = *opt;
+    if (!Q_host || !out_min || !dtype_ok(dtype) || n_inner < 1 || n_inner > 64 || n < n_inner ||
+        n - n_inner > 64 || n > QUBO_WIDE_MAX_N || outer_count < 1 || o.fix_bits != 0)
+        return QUBO_ERR_ARG;
+    const int n_out = n - n_inner;
+    if (n_out < 64 && (outer_begin >> n_out != 0 || outer_count > (1ull << n_out) - outer_begin))
+        return QUBO_ERR_ARG;
+    if (n_out == 64 && outer_begin + outer_count < outer_begin && outer_begin + outer_count != 0)
+        return QUBO_ERR_ARG;
+    if (o.topk < 0 || o.topk > QUBO_MAX_TOPK || (o.topk > 0 && !out_topk) || (states_cap > 0 && !out_states))
+        return QUBO_ERR_ARG;
+    if (n_inner < 62 && (uint64_t)o.topk > (1ull << n_inner))
+        return QUBO_ERR_ARG;
+    // fold the whole instance: U_ii = Q_ii, U_ij = Q_ij + Q_ji (i < j)
+    const bool fl = dtype_float(dtype);
+    std::vector<int64_t> Ui;
+    std::vector<double> Uf;
+    (fl ? Uf.assign((size_t)n * n, 0.0) : Ui.assign((size_t)n * n, 0));
+    {
+        int64_t beta = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i; j < n; ++j) {
+                const size_t a = (size_t)i * n + j, b = (size_t)j * n + i;
+                if (fl) {
+                    auto q = [&](size_t k) {
+                        return dtype == QUBO_F32 ? (double)((const float *)Q_host)[k] : ((const double *)Q_host)[k];
+                    };
+                    const double v = i == j ? q(a) : q(a) + q(b);
+                    if (!std::isfinite(v))
+                        return QUBO_ERR_ARG;
+                    Uf[a] = v;
+                } else {
+                    auto q = [&](size_t k) {
+                        return dtype == QUBO_I16 ? (int64_t)((const int16_t *)Q_host)[k]
+                                                 : (int64_t)((const int32_t *)Q_host)[k];
+                    };
+                    const int64_t v = i == j ? q(a) : q(a) + q(b);
+                    Ui[a] = v;
+                    beta += v < 0 ? -v : v;
+                }
+            }
+        if (beta >= (1ll << 62))
+            return QUBO_ERR_OVERFLOW;
+    }
+    Workspace *ws = nullptr;
+    int st;
+    if ((st = resolve_device(&ws)))
+        return st;
+    std::lock_guard<std::mutex> lk(ws->mu);
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if ((st = ws->init(dev)))
+        return st;
+    // Sub-problem of outer value v (variable n_inner + f = bit f of v): the inner variables keep
+    // their couplings, each inner diagonal gains the couplings to the set outer variables, and the
+    // set outer variables contribute the constant c(v) (Sec. 3.3.1; the scaling by fixed bits of
+    // Sec. 4.3).
+    auto reduce = [&](uint64_t v, HostInst &h, int64_t &ci, double &cf) {
+        const int m = n_inner;
+        std::vector<int64_t> ri;
+        std::vector<double> rf;
+        (fl ? rf.assign((size_t)m * m, 0.0) : ri.assign((size_t)m * m, 0));
+        for (int i = 0; i < m; ++i)
+            for (int j = i; j < m; ++j) {
+                if (fl)
+                    rf[(size_t)i * m + j] = Uf[(size_t)i * n + j];
+                else
+                    ri[(size_t)i * m + j] = Ui[(size_t)i * n + j];
+            }
+        ci = 0;
+        cf = 0.0;
+        for (int f = 0; f < n_out; ++f) {
+            if (!((v >> f) & 1))
+                continue;
+            const int vf = n_inner + f;
+            for (int i = 0; i < m; ++i) {
+                if (fl)
+                    rf[(size_t)i * m + i] += Uf[(size_t)i * n + vf];
+                else
+                    ri[(size_t)i * m + i] += Ui[(size_t)i * n + vf];
+            }
+            for (int g = f; g < n_out; ++g) {
+                if (!((v >> g) & 1))
+                    continue;
+                if (fl)
+                    cf += Uf[(size_t)vf * n + n_inner + g];
+                else
+                    ci += Ui[(size_t)vf * n + n_inner + g];
+            }
+        }
+        return prepare_folded(fl ? nullptr : &ri, fl ? &rf : nullptr, m, o.flags, h);
+    };
+    const double deadline = o.time_limit_s > 0 ? t0 + o.time_limit_s : 0.0;
+    const int K = o.topk;
+    WideAcc w;
+    SolveStats stats;
+    HostInst last;
+    const bool batched = n_inner <= kMaxBatchedN && outer_count > 1;
+    const uint64_t chunk = batched ? 4096 : 1;
+    for (uint64_t done = 0; done < outer_count; done += chunk) {
+        if (deadline > 0 && now_s() > deadline)
+            return QUBO_ERR_TIMEOUT;
+        const int cnt = (int)std::min<uint64_t>(chunk, outer_count - done);
+        std::vector<HostInst> hs(cnt);
+        std::vector<int64_t> ci(cnt);
+        std::vector<double> cf(cnt);
+        for (int t = 0; t < cnt; ++t)
+            if ((st = reduce(outer_begin + done + t, hs[t], ci[t], cf[t])))
+                return st;
+        std::vector<Part> parts;
+        if (batched) {
+            std::vector<int> order;
+            if ((st = batch_plan(hs, K, order)))
+                return st;
+            if ((st = batch_parts(*ws, hs, order, K, states_cap, (cudaStream_t)stream, parts, stats)))
+                return st;
+        } else {
+            qubo_options so = o;
+            if (deadline > 0)
+                so.time_limit_s = std::max(1e-3, deadline - now_s());
+            parts.resize(1);
+            if ((st = solve_one(*ws, hs[0], so, states_cap, (cudaStream_t)stream, parts[0], stats)))
+                return st;
+        }
+        for (int t = 0; t < cnt; ++t)
+            wide_add(w, parts[t], n_inner, outer_begin + done + t, ci[t], cf[t], states_cap, K);
+        last = hs[cnt - 1];
+    }
+    if (fl)
+        *(double *)out_min = w.min_f;
+    else
+        *(int64_t *)out_min = w.min_i;
+    for (size_t t = 0; t < w.ties.size(); ++t) {
+        out_states[2 * t] = w.ties[t].second;
+        out_states[2 * t + 1] = w.ties[t].first;
+    }
+    if (out_n_ties)
+        *out_n_ties = w.n_ties;
+    const int nk = fl ? (int)w.topf.size() : (int)w.topi.size();
+    for (int t = 0; t < nk; ++t) {
+        out_topk[2 * t] = fl ? std::get<2>(w.topf[t]) : std::get<2>(w.topi[t]);
+        out_topk[2 * t + 1] = fl ? std::get<1>(w.topf[t]) : std::get<1>(w.topi[t]);
+        if (out_topk_E) {
+            if (fl)
+                ((double *)out_topk_E)[t] = std::get<0>(w.topf[t]);
+            else
+                ((int64_t *)out_topk_E)[t] = std::get<0>(w.topi[t]);
+        }
+    }
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        info->min_i = fl ? 0 : w.min_i;
+        info->min_f = fl ? w.min_f : (double)w.min_i;
+        info->n_ties = w.n_ties;
+        info->n_written = w.ties.size();
+        info->truncated = w.n_ties > states_cap ? 1 : 0;
+        info->acc = (int32_t)last.acc;
+        info->n_topk = nk;
+        info->states_scanned = w.scanned;
+        info->candidates = w.candidates;
+        fill_plan_info(last, stats, t0, info);
+        info->n = n;
+    }
+    return w.n_ties > states_cap ? QUBO_TRUNCATED : QUBO_OK;
 }
 
 int qubo_problem_create(const void *Q_host, int n, qubo_dtype dtype, const qubo_options *opt, qubo_problem **out)

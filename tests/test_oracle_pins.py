@@ -259,3 +259,52 @@ def test_rate_convention_from_paper_tables():
     state-rate table (7.47e12) agree under this reading (Sec. 5.3, Tables 1 and 3)."""
     assert 2**50 / 151.2 == pytest.approx(7.45e12, rel=2e-3)
     assert 2**46 / 13690 == pytest.approx(5.1e9, rel=1e-2)
+
+
+# --- sub-problems with fixed variables (Sec. 3.3.1; Sec. 4.3 for instances wider than a scan) ---
+
+def bigint_energy(Q, x: int) -> int:
+    """E(x) = sum_ij Q_ij x_i x_j over the unfolded matrix in exact Python integers (any n)."""
+    on = [i for i in range(Q.shape[0]) if (x >> i) & 1]
+    return sum(int(Q[i, j]) for i in on for j in on)
+
+
+@pytest.mark.parametrize("n,m", [(70, 30), (100, 64), (9, 4), (20, 20)])
+def test_reduce_matches_exact_energy_beyond_64_bits(n, m):
+    rng = np.random.default_rng(n + m)
+    Q = rng.integers(-5000, 5000, size=(n, n))  # full, non-symmetric: the fold is exercised
+    for _ in range(25):
+        x = int.from_bytes(rng.bytes(16), "little") & ((1 << n) - 1)
+        R, c = oracle.reduce(Q, m, x >> m)
+        assert R.shape == (m, m) and np.all(np.tril(R, -1) == 0)
+        assert oracle.energy(R, x & ((1 << m) - 1)) + c == bigint_energy(Q, x)
+
+
+def test_reduce_float_matches_exact_energy():
+    import math
+
+    n, m = 90, 25
+    Q = wl.sk_float32(n, seed=7).astype(np.float64)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        x = int.from_bytes(rng.bytes(12), "little") & ((1 << n) - 1)
+        on = [i for i in range(n) if (x >> i) & 1]
+        exact = math.fsum(float(Q[i, j]) for i in on for j in on)
+        R, c = oracle.reduce(Q, m, x >> m)
+        got = oracle.energy(R, x & ((1 << m) - 1)) + c
+        assert got == pytest.approx(exact, rel=1e-12, abs=1e-12)
+
+
+def test_reduced_subproblems_equal_subcube_solves():
+    """For n <= 64 the sub-problem of outer value v is the sub-cube whose top bits are v: its
+    minimum plus c, and its tie codes with v above them, equal the sub-cube solve."""
+    n, m = 22, 15
+    Q = wl.upper_int(n, -40, 40, seed=21)
+    for v in (0, 1, 77, (1 << (n - m)) - 1):
+        R, c = oracle.reduce(Q, m, v)
+        r = oracle.solve(R, topk=5)
+        s = oracle.solve(Q, topk=5, fix_bits=n - m, fix_value=v)
+        assert r.min + c == s.min and r.n_ties == s.n_ties
+        assert [int(t) | (v << m) for t in r.ties] == [int(t) for t in s.ties]
+        assert [int(t) | (v << m) for t in r.topk] == [int(t) for t in s.topk]
+        assert [int(e) + c for e in r.topk_E] == [int(e) for e in s.topk_E]
