@@ -38,7 +38,7 @@ PAPER_CONTEXT = "7.47e12 states/s, int16 energies, 1x H100 (paper Tab. 1); other
 PROFILE_JSON = os.path.join(ROOT, "profiles", "scan_kernel_counters.json")
 # arithmetic type of each accumulator the library reports (integer results are exact in all)
 ACC_DTYPE = {"i32": "int32", "i64": "int64", "f32": "f32", "f64": "f64", "i32f": "f32 (integer-valued)",
-             "i16p": "u16x2 (integer-valued, packed)"}
+             "i16p": "u16x2 (integer-valued, packed)", "i32z": "int32 (factored sparse scan)"}
 
 
 def log(*a):
@@ -147,7 +147,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("scan_impl.cuh", "scan_i32.cu", "scan_f32.cu", "scan_i32f.cu", "scan_i16p.cu", "internal.h"):
+    for f in ("scan_impl.cuh", "scan_i32.cu", "scan_f32.cu", "scan_i32f.cu", "scan_i16p.cu", "scan_i32z.cu", "internal.h"):
         with open(os.path.join(ROOT, "paper_2607_04857_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -38,14 +38,19 @@ typedef enum { QUBO_I16 = 1, QUBO_I32 = 2, QUBO_F32 = 3, QUBO_F64 = 4 } qubo_dty
  * held exactly in FP32 lanes, chosen when every partial sum of the run's plan stays below 2^24
  * in magnitude.  QUBO_ACC_I16P: integer energies held as two 16-bit lanes per 32-bit word,
  * chosen (before QUBO_ACC_I32F) when every column value of the run's plan provably lies in
- * [-32768, 32767].  Both give exact integer results, as QUBO_ACC_I32 does. */
+ * [-32768, 32767].  QUBO_ACC_I32Z: int32 energies of a sparse instance, chosen first when the
+ * variables can be ordered so that at least 3 walked prefix variables have no coupling to any
+ * suffix variable: the scan then factors those variables out of the column walk (the minimum
+ * over their patterns separates from the minimum over the columns) and updates the columns
+ * 2^Z times less often.  All give exact integer results, as QUBO_ACC_I32 does. */
 typedef enum {
     QUBO_ACC_I32 = 1,
     QUBO_ACC_I64 = 2,
     QUBO_ACC_F32 = 3,
     QUBO_ACC_F64 = 4,
     QUBO_ACC_I32F = 5,
-    QUBO_ACC_I16P = 6
+    QUBO_ACC_I16P = 6,
+    QUBO_ACC_I32Z = 7
 } qubo_acc;
 
 typedef enum {

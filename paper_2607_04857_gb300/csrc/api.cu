@@ -60,6 +60,8 @@ struct HostInst {
     double thr0 = 0.0;  // initial threshold (a bound on the K-th lowest energy of the range)
     int32_t clampC = 0; // ACC_I32F: threshold clamp
     int32_t col_lo = 0, col_hi = 0;  // ACC_I16P: proven range of every column value
+    int Z = 0;                  // ACC_I32Z: walked rows without suffix couplings
+    std::vector<uint8_t> perm;  // ACC_I32Z: caller's variable at each scan position
 };
 
 bool dtype_ok(qubo_dtype dt) { return dt == QUBO_I16 || dt == QUBO_I32 || dt == QUBO_F32 || dt == QUBO_F64; }
@@ -111,17 +113,21 @@ int prepare(const void *Q, int n, qubo_dtype dt, uint32_t flags, HostInst &h)
     return QUBO_OK;
 }
 
-int acc_bytes(Acc a) { return (a == ACC_I32 || a == ACC_F32 || a == ACC_I32F || a == ACC_I16P) ? 4 : 8; }
+int acc_bytes(Acc a) { return (a == ACC_I64 || a == ACC_F64) ? 8 : 4; }
 
 // Suffix bits (log2 of the columns of one work unit) of an accumulator and kernel variant.
 int acc_suffix_bits(Acc a, int variant)
 {
+    if (a == ACC_I32Z)
+        return zscan_suffix_bits(variant);
     return a == ACC_I16P ? packed_suffix_bits(variant) : suffix_bits(acc_bytes(a), variant);
 }
 
 // Columns held by one thread (two per word in the packed scan).
 int acc_cols_per_thread(Acc a, int variant)
 {
+    if (a == ACC_I32Z)
+        return kZCols[variant == 1 ? 1 : 0];
     return a == ACC_I16P ? 2 * packed_words(variant) : cols_per_thread(acc_bytes(a), variant);
 }
 
@@ -129,6 +135,8 @@ int acc_cols_per_thread(Acc a, int variant)
 int reg_rows_of(Acc a, int variant)
 {
     const int v = variant >= 0 && variant < kScanVariants ? variant : 0;
+    if (a == ACC_I32Z)
+        return 2;  // the factored scan needs at least 3 walked rows
     return a == ACC_I16P ? kPackedRegRows[v] : kVariantRegRows[acc_bytes(a) == 4 ? v : 0];
 }
 
@@ -292,6 +300,80 @@ bool i16p_exact(HostInst &h)
     return true;
 }
 
+// Factored scan of sparse instances: choose up to kZMaxRows walked variables with no coupling
+// to any of the B suffix variables (any order of the variables is allowed, Sec. 2.4), and a
+// scan order: suffix, those zero rows, the other walked rows, the unit's fixed bits, then the
+// sub-cube's fixed top bits in place.  Greedy: candidates by ascending degree join the zero rows
+// while at least B variables remain that neither they nor the zero rows touch.  Returns Z and
+// fills h.perm (h.B, h.L from the plan).
+int zero_rows_search(HostInst &h)
+{
+    const int n = h.n, nf = n - h.fix_bits, B = h.B, L = h.L;
+    if (h.small || nf < B + L)
+        return 0;
+    auto adj = [&](int a, int b) { return a != b && h.Ui[(size_t)std::min(a, b) * n + std::max(a, b)] != 0; };
+    std::vector<int> deg(n, 0);
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b)
+            deg[a] += adj(a, b);
+    std::vector<int> order(nf);
+    for (int v = 0; v < nf; ++v)
+        order[v] = v;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return deg[a] < deg[b]; });
+    std::vector<char> inZ(n, 0), touched(n, 0);
+    std::vector<int> zrows;
+    const int zmax = std::min(kZMaxRows, L);
+    auto pool_size = [&](int extra) {
+        int c = 0;
+        for (int u = 0; u < nf; ++u)
+            if (!inZ[u] && u != extra && !touched[u] && !adj(u, extra))
+                ++c;
+        return c;
+    };
+    for (int v : order) {
+        if ((int)zrows.size() >= zmax)
+            break;
+        if (pool_size(v) < B)
+            continue;
+        inZ[v] = 1;
+        zrows.push_back(v);
+        for (int u = 0; u < n; ++u)
+            if (adj(u, v))
+                touched[u] = 1;
+    }
+    const int Z = (int)zrows.size();
+    if (Z == 0 || L - Z > kZMaxBlocksLog2)
+        return 0;
+    std::vector<int> suf, rest;
+    for (int v : order) {
+        if (inZ[v])
+            continue;
+        if ((int)suf.size() < B && !touched[v])
+            suf.push_back(v);
+        else
+            rest.push_back(v);
+    }
+    if ((int)suf.size() < B)
+        return 0;
+    h.perm.assign(n, 0);
+    int pos = 0;
+    for (int v : suf)
+        h.perm[pos++] = (uint8_t)v;
+    for (int v : zrows)
+        h.perm[pos++] = (uint8_t)v;
+    for (int v : rest)
+        h.perm[pos++] = (uint8_t)v;
+    for (int v = nf; v < n; ++v)
+        h.perm[pos++] = (uint8_t)v;
+    return Z;
+}
+
+bool i32z_allowed()
+{
+    const char *v = std::getenv("QUBO_NO_I32Z");
+    return !(v && v[0] == '1');
+}
+
 bool i16p_allowed()
 {
     const char *v = std::getenv("QUBO_NO_I16P");
@@ -304,8 +386,24 @@ bool i16p_allowed()
 int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bits, int variant_req,
              uint32_t flags)
 {
-    if ((h.acc == ACC_I32 || h.acc == ACC_I32F || h.acc == ACC_I16P) && !(flags & QUBO_FLAG_PLAIN)) {
+    if ((h.acc == ACC_I32 || h.acc == ACC_I32F || h.acc == ACC_I16P || h.acc == ACC_I32Z) &&
+        !(flags & QUBO_FLAG_PLAIN)) {
         Acc chosen = ACC_I32;
+        // sparse instances: at least 3 walked rows factored out (8x fewer column updates)
+        if (i32z_allowed()) {
+            for (int zv = 0; zv < kZVariants && chosen == ACC_I32; ++zv) {
+                h.acc = ACC_I32Z;
+                h.variant = zv;
+                if (plan(h, fix_bits, fix_value, split_k, walk_bits) == QUBO_OK && (h.Z = zero_rows_search(h)) >= 3)
+                    chosen = ACC_I32Z;
+            }
+            if (chosen == ACC_I32Z) {
+                h.acc = ACC_I32Z;
+                return QUBO_OK;
+            }
+            h.Z = 0;
+            h.perm.clear();
+        }
         if (i16p_allowed()) {
             h.acc = ACC_I16P;
             h.variant = pick_variant(h.acc, variant_req);
@@ -439,7 +537,8 @@ unsigned long long encode_thr(Acc acc, double t)
     switch (acc) {
     case ACC_I32:
     case ACC_I32F:
-    case ACC_I16P: return (unsigned long long)(uint32_t)(int32_t)t;
+    case ACC_I16P:
+    case ACC_I32Z: return (unsigned long long)(uint32_t)(int32_t)t;
     case ACC_I64: return (unsigned long long)(int64_t)t;
     case ACC_F32: {
         float f = (float)t;
@@ -457,7 +556,8 @@ unsigned long long encode_max(Acc acc)
     switch (acc) {
     case ACC_I32:
     case ACC_I32F:
-    case ACC_I16P: return (unsigned long long)(uint32_t)INT32_MAX;
+    case ACC_I16P:
+    case ACC_I32Z: return (unsigned long long)(uint32_t)INT32_MAX;
     case ACC_I64: return (unsigned long long)INT64_MAX;
     case ACC_F32: return ord32h(INFINITY);
     case ACC_F64: return ord64h(INFINITY);
@@ -795,7 +895,7 @@ struct Job {
     size_t off_inst = 0, off_state = 0, off_items = 0, up_bytes = 0;
     size_t off_res = 0, off_ties = 0, off_topk = 0, off_topke = 0, off_starts = 0, off_ctr = 0;
     size_t arena_bytes = 0, down_bytes = 0;
-    std::vector<size_t> off_W, off_W64, off_U64, off_Es, off_M, off_EL;
+    std::vector<size_t> off_W, off_W64, off_U64, off_Es, off_M, off_EL, off_perm;
     int max_entries = 0;
     int blocks = 0;
     unsigned long long rec_cap = 0;
@@ -826,6 +926,7 @@ int job_layout(Job &j)
     j.off_Es.resize(ni);
     j.off_M.resize(ni);
     j.off_EL.resize(ni);
+    j.off_perm.assign(ni, 0);
     for (int i = 0; i < ni; ++i) {
         const HostInst &h = *j.insts[i];
         const size_t nn = (size_t)h.n * h.n;
@@ -839,6 +940,10 @@ int job_layout(Job &j)
         } else {
             j.off_W[i] = o;
             o = align_up(o + (size_t)eb * nn, 256);
+        }
+        if (j.acc == ACC_I32Z && !h.small) {  // scan order of the variables
+            j.off_perm[i] = o;
+            o = align_up(o + 64, 256);
         }
     }
     j.up_bytes = o;
@@ -924,7 +1029,16 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
             d.W64 = (const double *)(dev + j.off_W64[i]);
             d.U64 = (const double *)(dev + j.off_U64[i]);
         } else {
-            if (j.acc == ACC_I32 || j.acc == ACC_I32F || j.acc == ACC_I16P) {
+            if (j.acc == ACC_I32Z && !h.small) {
+                // the couplings in scan order: W[a][b] couples the variables perm[a] and perm[b]
+                int32_t *W = (int32_t *)(up + j.off_W[i]);
+                for (int a = 0; a < h.n; ++a)
+                    for (int b = 0; b < h.n; ++b) {
+                        const int va = h.perm[a], vb = h.perm[b];
+                        W[(size_t)a * h.n + b] = (int32_t)h.Ui[(size_t)std::min(va, vb) * h.n + std::max(va, vb)];
+                    }
+                std::memcpy(up + j.off_perm[i], h.perm.data(), h.n);
+            } else if (j.acc == ACC_I32 || j.acc == ACC_I32F || j.acc == ACC_I16P || j.acc == ACC_I32Z) {
                 int32_t *W = (int32_t *)(up + j.off_W[i]);
                 for (int a = 0; a < h.n; ++a)
                     for (int b = 0; b < h.n; ++b)
@@ -944,6 +1058,8 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
         d.M = h.small ? nullptr : dev + j.off_M[i];
         d.EL = h.small ? nullptr : dev + j.off_EL[i];
         d.thr0 = 0;
+        d.Z = h.Z;
+        d.perm = (j.acc == ACC_I32Z && !h.small) ? (const uint8_t *)(dev + j.off_perm[i]) : nullptr;
         hi[i] = d;
         InstState s{};
         s.thr = encode_thr(j.acc, h.thr0);

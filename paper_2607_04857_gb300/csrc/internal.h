@@ -8,7 +8,9 @@ namespace qubo {
 
 // ACC_I32F: integer energies scanned exactly in FP32 lanes (partial sums below 2^24).
 // ACC_I16P: integer energies whose column values fit 16 bits, two columns per 32-bit word.
-enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4, ACC_I32F = 5, ACC_I16P = 6 };
+// ACC_I32Z: int32 energies, sparse instances: walked rows without couplings to the suffix
+// variables are factored out of the column walk (zscan_kernel).
+enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4, ACC_I32F = 5, ACC_I16P = 6, ACC_I32Z = 7 };
 
 // Walked prefix rows kept in registers by the scan kernel (the largest of the compiled
 // variants); the inner loop is unrolled over 2^(RC+1) Gray steps so that every register-row
@@ -74,6 +76,9 @@ struct Inst {
     void *M;              // L x 2^B interaction rows (M_int restricted to the walked rows)
     void *EL;             // 2^L walked-prefix energies in Gray-walk order
     int64_t thr0;         // initial threshold (int64 value or double bits)
+    int32_t Z;            // ACC_I32Z: walked rows 0..Z-1 have no coupling to a suffix variable
+    int32_t pad;
+    const uint8_t *perm;  // ACC_I32Z: variable of the caller's order at each scan position
 };
 
 // Mutable per-instance state, updated with atomics.
@@ -136,6 +141,14 @@ constexpr int packed_suffix_bits(int variant) { return packed_words(variant) == 
 struct i32f;  // tag of the integer-in-FP32 accumulator (scan_impl.cuh)
 struct i16p;  // tag of the packed 16-bit accumulator (scan_impl.cuh)
 
+// Factored scan of sparse instances (scan_i32z.cu): columns per thread of each variant, the
+// most zero rows (walked rows without suffix couplings) and the most column-walk blocks.
+constexpr int kZVariants = 2;
+constexpr int kZCols[kZVariants] = {32, 16};
+constexpr int kZMaxRows = 8;
+constexpr int kZMaxBlocksLog2 = 10;
+constexpr int zscan_suffix_bits(int variant) { return kZCols[(variant >= 0 && variant < kZVariants) ? variant : 0] == 32 ? 10 : 9; }
+
 // ---- launchers (scan_*.cu, one translation unit per accumulator type) -------------------------
 template <class T>
 cudaError_t launch_tables_t(const Inst *d_inst, int n_inst, int max_entries, cudaStream_t s);
@@ -143,6 +156,9 @@ template <class T>
 cudaError_t launch_scan_t(const ScanArgs &a, int blocks, int variant, cudaStream_t s);
 template <class T>
 int scan_blocks_per_sm_t(bool k1, int variant);
+
+cudaError_t launch_zscan(const ScanArgs &a, int blocks, int variant, cudaStream_t s);
+int zscan_blocks_per_sm(bool k1, int variant);
 
 // ---- dispatch and finalize (finalize.cu) -----------------------------------------------------
 cudaError_t launch_tables(Acc acc, const Inst *d_inst, int n_inst, int max_entries, cudaStream_t s);

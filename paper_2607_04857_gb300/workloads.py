@@ -60,6 +60,22 @@ def maxcut_qubo(n: int, p: float, seed: int, dtype=np.int16) -> np.ndarray:
     return Q.astype(dtype)
 
 
+def sparse_int(n: int, density: float, lo: int, hi: int, seed: int, dtype=np.int32) -> np.ndarray:
+    """Upper-triangular integer Q: diagonal entries uniform in [lo, hi] (a drawn 0 becomes lo),
+    each off-diagonal entry present with probability `density`, its value uniform in [lo, hi]
+    (a drawn 0 becomes hi)."""
+    rng = _rng(seed)
+    iu = np.triu_indices(n, k=1)
+    present = rng.random(len(iu[0])) < density
+    vals = rng.integers(lo, hi, size=len(iu[0]), endpoint=True, dtype=np.int64)
+    vals = np.where(vals == 0, hi, vals) * present
+    Q = np.zeros((n, n), dtype=np.int64)
+    Q[iu] = vals
+    d = rng.integers(lo, hi, size=n, endpoint=True, dtype=np.int64)
+    Q[np.arange(n), np.arange(n)] = np.where(d == 0, lo, d)
+    return Q.astype(dtype)
+
+
 def planted(n: int, seed: int, x_star: int | None = None, dtype=np.int32):
     """Diagonal Q = diag(w * (1 - 2 x*)) with w > 0, whose unique minimiser is x*.
     Returns (Q, x*)."""

@@ -27,6 +27,12 @@ def q():
     return q
 
 
+@pytest.fixture(autouse=True)
+def dense_kernels_only(monkeypatch):
+    """These instances test the packed scan; keep the factored sparse scan out of the way."""
+    monkeypatch.setenv("QUBO_NO_I32Z", "1")
+
+
 def check_int(r, o):
     assert r.min == o.min, (r.min, o.min)
     assert r.n_ties == o.n_ties, (r.n_ties, o.n_ties)

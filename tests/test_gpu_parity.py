@@ -61,7 +61,8 @@ def test_direct_path_small_n(q, n):
 
 
 # Integer kernels: packed 16-bit lanes (chosen first for these small entries), FP32 lanes, int32.
-LANES = {"i16p": {}, "i32f": {"QUBO_NO_I16P": "1"}, "i32": {"QUBO_NO_I16P": "1", "QUBO_NO_I32F": "1"}}
+LANES = {"i16p": {"QUBO_NO_I32Z": "1"}, "i32f": {"QUBO_NO_I32Z": "1", "QUBO_NO_I16P": "1"},
+         "i32": {"QUBO_NO_I32Z": "1", "QUBO_NO_I16P": "1", "QUBO_NO_I32F": "1"}}
 
 
 @pytest.mark.parametrize("n", [14, 15, 16, 19, 22, 26])

@@ -1,0 +1,115 @@
+"""Factored scan of sparse integer instances against the CPU oracle.
+
+Instances whose variables can be ordered so that at least three walked prefix variables have no
+coupling to any suffix variable run the factored scan (accumulator "i32z"): the minimum over
+those variables' patterns separates from the minimum over the columns.  Results must be
+bit-exact with the oracle in the caller's variable order: minimum, exact tie count, tie codes,
+K lowest states and energies.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_04857_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def q():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_04857_gb300 import build as qbuild
+
+    qbuild.build()
+    import paper_2607_04857_gb300 as q
+
+    q.load_library()
+    return q
+
+
+def check_int(r, o):
+    assert r.min == o.min, (r.min, o.min)
+    assert r.n_ties == o.n_ties, (r.n_ties, o.n_ties)
+    assert np.array_equal(r.ties, o.ties), (r.ties[:8], o.ties[:8])
+    assert np.array_equal(r.topk, o.topk), (r.topk, o.topk)
+    assert np.array_equal(r.topk_E, o.topk_E), (r.topk_E, o.topk_E)
+
+
+@pytest.mark.parametrize("n", [16, 20, 25, 30])
+@pytest.mark.parametrize("topk", [0, 1, 16])
+def test_sparse_parity(q, n, topk):
+    for seed in range(2):
+        Q = wl.sparse_int(n, 0.1, -500, 500, seed=100 * n + seed)
+        r = q.solve(Q, topk=topk)
+        assert r.info["acc"] == "i32z", r.info
+        check_int(r, oracle.solve(Q, topk=topk))
+
+
+def test_sparse_maxcut_tie_pairs(q):
+    """Sparse Max-Cut: complementing every variable keeps the cut, so ties come in pairs."""
+    Q = wl.maxcut_qubo(30, 0.1, seed=3, dtype=np.int32)
+    r = q.solve(Q, topk=8, states_cap=4096)
+    assert r.info["acc"] == "i32z"
+    o = oracle.solve(Q, topk=8, cap=4096)
+    check_int(r, o)
+    assert r.n_ties % 2 == 0
+
+
+@pytest.mark.parametrize("walk_bits", [3, 5, 8, 12])
+def test_sparse_plan_shapes(q, walk_bits):
+    Q = wl.sparse_int(28, 0.08, -100, 100, seed=7)
+    r = q.solve(Q, topk=12, walk_bits=walk_bits)
+    assert r.info["acc"] == "i32z" and r.info["walk_bits"] == walk_bits
+    check_int(r, oracle.solve(Q, topk=12))
+
+
+def test_sparse_subcubes(q):
+    Q = wl.sparse_int(40, 0.06, -1000, 1000, seed=40)
+    for v in (0, 3, 1000, (1 << 14) - 1):
+        r = q.solve(Q, topk=4, fix_bits=14, fix_value=v)
+        assert r.info["acc"] == "i32z"
+        check_int(r, oracle.solve(Q, topk=4, fix_bits=14, fix_value=v))
+
+
+def test_sparse_window(q):
+    Q = wl.sparse_int(22, 0.1, -20, 20, seed=5)
+    o = oracle.solve(Q, topk=4096, cap=1)
+    sel = o.topk_E <= o.min + 12
+    assert not sel.all()
+    cnt, codes, E, info = q.solve_window(Q, 12)
+    assert info["acc"] == "i32z"
+    assert cnt == int(sel.sum())
+    assert np.array_equal(codes, o.topk[sel]) and np.array_equal(E, o.topk_E[sel])
+
+
+def test_sparse_overflow_split(q, monkeypatch):
+    """Nine free variables (no diagonal, no coupling) give 2^9 minimisers, more than a
+    300-record buffer holds: the run splits along the top code bit (free, so each half holds
+    256) and merges; the results stay exact."""
+    Q = wl.sparse_int(24, 0.1, -50, 50, seed=9)
+    Q[15:, :] = 0
+    Q[:, 15:] = 0
+    assert q.solve(Q).info["acc"] == "i32z"
+    monkeypatch.setenv("QUBO_MAX_RECORDS", "300")
+    r = q.solve(Q, states_cap=4096)
+    assert r.info["passes"] > 1 and r.n_ties % 512 == 0
+    check_int(r, oracle.solve(Q, cap=4096))
+
+
+def test_diagonal_instance_uses_every_walked_row(q):
+    """No couplings at all: every walked row is factored out; ties have the closed form."""
+    Q = wl.diagonal(26, seed=4, zeros=5)
+    r = q.solve(Q, states_cap=64)
+    assert r.info["acc"] == "i32z" and r.n_ties == 1 << 5
+    check_int(r, oracle.solve(Q, cap=64))
+
+
+def test_sparse_disabled_falls_back(q, monkeypatch):
+    Q = wl.sparse_int(26, 0.1, -500, 500, seed=11)
+    o = oracle.solve(Q, topk=8)
+    monkeypatch.setenv("QUBO_NO_I32Z", "1")
+    r = q.solve(Q, topk=8)
+    assert r.info["acc"] in ("i16p", "i32f", "i32")
+    check_int(r, o)
