@@ -8,7 +8,8 @@ instance with its top `--fix-bits` code bits fixed (2^(50-fix_bits) states); con
 take consecutive sub-cubes, so 2^fix_bits steps cover the whole instance.  The rate is states
 per second (2^n / total time, the paper's convention, Sec. 5.3).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload n50_int32|n44_fp32|maxcut_n48|batched]
+  python bench.py [--gpus N] [--steps K] [--warmup W]
+                  [--workload n50_int32|n44_fp32|maxcut_n48|sparse_n56|batched]
   python bench.py --impl reference ...   (the CPU oracle on the host cores, same workload)
 
 Under torchrun every rank takes disjoint sub-cubes (no data-path collective; weak scaling).
@@ -72,6 +73,14 @@ def make_workload(name: str, fix_bits: int | None):
                     config={"workload": "maxcut_n48_top16", "n": 48, "topk": 16, "seed": 48,
                             "entries": "Max-Cut of G(48, 0.5), edge weights +-1 (int16)",
                             "step": f"one sub-cube of 2^{48 - fb} states (top {fb} code bits fixed)"})
+    if name == "sparse_n56":
+        fb = 10 if fix_bits is None else fix_bits
+        return dict(name=name, Q=wl.sparse_int(56, 0.05, -1000, 1000, seed=56), n=56, topk=16, fix_bits=fb,
+                    metric="states/s (n=56 sparse int32 QUBO)", unit="states/s", dtype="int32",
+                    config={"workload": "sparse_n56_top16", "n": 56, "topk": 16, "seed": 56,
+                            "entries": "upper-triangular int32: diagonal uniform [-1000, 1000], off-diagonal "
+                                       "present with probability 0.05, uniform [-1000, 1000]",
+                            "step": f"one sub-cube of 2^{56 - fb} states (top {fb} code bits fixed)"})
     if name == "batched":
         return dict(name=name, Qs=wl.config4(), topk=0, metric="instances/s (4096 QUBOs, n uniform in 16..32)",
                     unit="instances/s", dtype="int32",
@@ -145,9 +154,14 @@ class ClockSampler:
 # helpers
 # ---------------------------------------------------------------------------------------------
 
-def kernel_source_hash() -> str:
+ACC_SOURCE = {"i32": "scan_i32.cu", "i64": "scan_i64.cu", "f32": "scan_f32.cu", "f64": "scan_f64.cu",
+              "i32f": "scan_i32f.cu", "i16p": "scan_i16p.cu", "i32z": "scan_i32z.cu"}
+
+
+def kernel_source_hash(acc: str) -> str:
+    """Hash of the sources the accumulator's scan kernel is compiled from."""
     h = hashlib.sha256()
-    for f in ("scan_impl.cuh", "scan_i32.cu", "scan_f32.cu", "scan_i32f.cu", "scan_i16p.cu", "scan_i32z.cu", "internal.h"):
+    for f in ("scan_impl.cuh", "internal.h", ACC_SOURCE.get(acc, "scan_i32.cu")):
         with open(os.path.join(ROOT, "paper_2607_04857_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -162,7 +176,7 @@ def profile_counters(acc: str):
     except (OSError, ValueError):
         return None
     e = d.get(acc)
-    if not e or e.get("kernel_hash") != kernel_source_hash():
+    if not e or e.get("kernel_hash") != kernel_source_hash(acc):
         return None
     return e
 
@@ -266,7 +280,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="n50_int32", choices=["n50_int32", "n44_fp32", "maxcut_n48", "batched"])
+    ap.add_argument("--workload", default="n50_int32",
+                    choices=["n50_int32", "n44_fp32", "maxcut_n48", "sparse_n56", "batched"])
     ap.add_argument("--fix-bits", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-loop", action="store_true",
@@ -432,13 +447,21 @@ def main():
     W["dtype"] = ACC_DTYPE.get(acc, acc)
     # the packed scan holds two 16-bit columns in each 32-bit lane: twice the lane-ops per cycle
     halves = 2 if acc == "i16p" else 1
-    achieved = ALG_OPS_PER_STATE * per_launch_states / mean_scan / 1e9
+    ops_per_state = ALG_OPS_PER_STATE
+    if acc == "i32z":
+        # factored scan: one add and one min per column per block of 2^Z walk steps, and one
+        # add and one min per walk step per 2^B columns (the block minima of E_L)
+        Zr, Bs = infos[0]["zero_rows"], infos[0]["suffix_bits"]
+        ops_per_state = 2.0 / 2 ** Zr + 2.0 / 2 ** Bs
+    achieved = ops_per_state * per_launch_states / mean_scan / 1e9
     clk_max = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = halves * sms * LANES_PER_SM * clk_max * 1e6 / 1e9
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
             "traffic": None, "kernel": "scan_kernel",
             "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes" + (" x 2 packed 16-bit halves" if halves == 2 else "")
-                          + f" x {clk_max:.0f} MHz; 2 ops/state (add + min)"}
+                          + f" x {clk_max:.0f} MHz; {ops_per_state:.4g} ops/state"
+                          + (" (add + min)" if acc != "i32z" else
+                             f" (factored scan: 2/2^Z + 2/2^B, Z = {infos[0]['zero_rows']}, B = {infos[0]['suffix_bits']})")}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (halves * sms * LANES_PER_SM * clocks["sm_mhz"] * 1e-3)
     prof = profile_counters(acc)

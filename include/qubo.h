@@ -120,7 +120,7 @@ typedef struct {
     int32_t cols_per_thread, threads, blocks, passes; /* launch shape; passes > 1 if the
                                  candidate buffer overflowed and the scan was repeated */
     int32_t kernel_launches;  /* kernels this call launched (all passes) */
-    int32_t reserved1;
+    int32_t zero_rows;        /* QUBO_ACC_I32Z: walked variables factored out of the column walk */
     uint64_t h2d_bytes;       /* bytes copied host -> device by this call */
     uint64_t d2h_bytes;       /* bytes copied device -> host by this call */
 } qubo_result;

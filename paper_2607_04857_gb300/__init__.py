@@ -64,7 +64,7 @@ class ResultInfo(ctypes.Structure):
         ("n", ctypes.c_int32),
         ("split_k", ctypes.c_int32), ("walk_bits", ctypes.c_int32), ("suffix_bits", ctypes.c_int32),
         ("cols_per_thread", ctypes.c_int32), ("threads", ctypes.c_int32), ("blocks", ctypes.c_int32),
-        ("passes", ctypes.c_int32), ("kernel_launches", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+        ("passes", ctypes.c_int32), ("kernel_launches", ctypes.c_int32), ("zero_rows", ctypes.c_int32),
         ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
     ]
 

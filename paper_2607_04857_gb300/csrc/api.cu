@@ -33,6 +33,9 @@ constexpr int kDefaultMaxWalkBits = 12;
 // Gray steps keep the measured drift (2.4e-4 on the n=44 SK instance) well inside the budget
 // of the default 1e-3 candidate margin; the drift guard shortens it when it does not.
 constexpr int kFloatMaxWalkBits = 10;
+// The factored sparse scan reads the whole E_L table once per unit: 2^13 entries (32 KB) stay in
+// L1 and amortise the unit set-up best (measured against 2^11..2^14).
+constexpr int kZMaxWalkBits = 13;
 
 double now_s()
 {
@@ -127,7 +130,7 @@ int acc_suffix_bits(Acc a, int variant)
 int acc_cols_per_thread(Acc a, int variant)
 {
     if (a == ACC_I32Z)
-        return kZCols[variant == 1 ? 1 : 0];
+        return kZCols[(variant >= 0 && variant < kZVariants) ? variant : 0];
     return a == ACC_I16P ? 2 * packed_words(variant) : cols_per_thread(acc_bytes(a), variant);
 }
 
@@ -177,7 +180,9 @@ int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bi
     else if (walk_bits > 0)
         L = walk_bits;
     else
-        L = std::max(rc + 1, std::min(h.acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits,
+        L = std::max(rc + 1, std::min(h.acc == ACC_F32   ? kFloatMaxWalkBits
+                                      : h.acc == ACC_I32Z ? kZMaxWalkBits
+                                                          : kDefaultMaxWalkBits,
                                       free_bits - h.B - kTargetUnitsLog2));
     const int k = n - h.B - L;
     if (L < rc + 1 || L > kMaxWalkBits || k < fix_bits || k > 63)
@@ -342,7 +347,7 @@ int zero_rows_search(HostInst &h)
                 touched[u] = 1;
     }
     const int Z = (int)zrows.size();
-    if (Z == 0 || L - Z > kZMaxBlocksLog2)
+    if (Z == 0)
         return 0;
     std::vector<int> suf, rest;
     for (int v : order) {
@@ -391,11 +396,23 @@ int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int wal
         Acc chosen = ACC_I32;
         // sparse instances: at least 3 walked rows factored out (8x fewer column updates)
         if (i32z_allowed()) {
-            for (int zv = 0; zv < kZVariants && chosen == ACC_I32; ++zv) {
+            // QUBO_ZSCAN_VARIANT pins the factored scan's column count (variant index)
+            const char *zenv = std::getenv("QUBO_ZSCAN_VARIANT");
+            const int z0 = zenv ? std::max(0, std::min(kZVariants - 1, std::atoi(zenv))) : 0;
+            const int z1 = zenv ? z0 + 1 : kZVariants;
+            for (int zv = z0; zv < z1 && chosen == ACC_I32; ++zv) {
                 h.acc = ACC_I32Z;
                 h.variant = zv;
-                if (plan(h, fix_bits, fix_value, split_k, walk_bits) == QUBO_OK && (h.Z = zero_rows_search(h)) >= 3)
-                    chosen = ACC_I32Z;
+                if (plan(h, fix_bits, fix_value, split_k, walk_bits) != QUBO_OK || (h.Z = zero_rows_search(h)) < 3)
+                    continue;
+                if (h.L - h.Z > kZMaxBlocksLog2) {
+                    // too many blocks for the per-warp table: a shorter walk, if the plan is ours
+                    if (split_k > 0 || walk_bits > 0 ||
+                        plan(h, fix_bits, fix_value, 0, h.Z + kZMaxBlocksLog2) != QUBO_OK ||
+                        (h.Z = zero_rows_search(h)) < 3 || h.L - h.Z > kZMaxBlocksLog2)
+                        continue;
+                }
+                chosen = ACC_I32Z;
             }
             if (chosen == ACC_I32Z) {
                 h.acc = ACC_I32Z;
@@ -1525,6 +1542,7 @@ void fill_plan_info(const HostInst &h, const SolveStats &stats, double t0, qubo_
     info->walk_bits = h.L;
     info->suffix_bits = h.small ? 0 : h.B;
     info->cols_per_thread = h.small ? 0 : acc_cols_per_thread(h.acc, h.variant);
+    info->zero_rows = h.acc == ACC_I32Z ? h.Z : 0;
     info->threads = kScanThreads;
     info->blocks = stats.blocks;
     info->passes = stats.passes;

@@ -75,12 +75,27 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
         wz[m] = s;
     }
     __syncwarp();
+    // Lanes take consecutive walk steps (coalesced E_L reads); a block's minimum is reduced
+    // across the lanes that hold it (butterfly over aligned groups of min(2^Z, 32) lanes) and,
+    // for blocks longer than a warp, across the warp iterations of the block.
     const int32_t *EL = (const int32_t *)d.EL;
-    for (int kb = lane; kb < nblk; kb += 32) {
-        int32_t mn = INT32_MAX;
-        for (int i = kb << Z; i < (kb + 1) << Z; ++i)
-            mn = min(mn, EL[i] + wz[(i ^ (i >> 1)) & (nz - 1)]);
-        mel[kb] = mn;
+    {
+        const int zl = Z < 5 ? Z : 5;                   // butterfly levels
+        const int per = Z > 5 ? 1 << (Z - 5) : 1;       // warp iterations per block
+        const int total = 1 << L, iters = (total + 31) >> 5;
+        int32_t acc = INT32_MAX;
+        for (int t = 0; t < iters; ++t) {
+            const int i = (t << 5) + lane;
+            if (i < total)
+                acc = min(acc, EL[i] + wz[(i ^ (i >> 1)) & (nz - 1)]);
+            if ((t + 1) % per == 0) {
+                for (int o = 1; o < (1 << zl); o <<= 1)
+                    acc = min(acc, __shfl_xor_sync(kFull, acc, o));
+                if (i < total && (lane & ((1 << zl) - 1)) == 0)
+                    mel[i >> Z] = acc;
+                acc = INT32_MAX;
+            }
+        }
     }
     __syncwarp();
 
@@ -192,7 +207,8 @@ __global__ void __launch_bounds__(kScanThreads, 3) zscan_kernel(const ScanArgs a
 template <bool K1>
 auto zpick(int variant)
 {
-    return variant == 1 ? zscan_kernel<kZCols[1], K1> : zscan_kernel<kZCols[0], K1>;
+    return variant == 2 ? zscan_kernel<kZCols[2], K1>
+           : variant == 1 ? zscan_kernel<kZCols[1], K1> : zscan_kernel<kZCols[0], K1>;
 }
 
 }  // namespace
