@@ -35,6 +35,7 @@ EXPORTS = (
     "qubo_autotune", "qubo_autotune_batched", "qubo_autotune_clear", "qubo_solve_window", "qubo_solve_wide",
 )
 WIDE_MAX_N = 128
+QUBO_MAX_TOPK = 1024
 NOALLOC_MAX_N = 40
 NOALLOC_MAX_TIES = 4096
 
@@ -263,16 +264,7 @@ def _batch_outputs(count, dt, topk, states_cap):
 
 
 def _batch_results(count, dt, topk, states_cap, mn, ties, tk, tkE, infos):
-    isf = dt in (QUBO_F32, QUBO_F64)
-    out = []
-    for i in range(count):
-        inf = infos[i]
-        k = inf.n_topk
-        out.append(Result(float(mn[i]) if isf else int(mn[i]), int(inf.n_ties),
-                          ties[i * states_cap: i * states_cap + inf.n_written].copy(),
-                          tk[i * topk: i * topk + k].copy(), tkE[i * topk: i * topk + k].copy(),
-                          QUBO_TRUNCATED if inf.n_ties > states_cap else QUBO_OK, inf.as_dict()))
-    return out
+    return BatchResults(count, dt, topk, states_cap, mn, ties, tk, tkE, infos)
 
 
 def autotune(Q, fix_bits: int) -> dict:
@@ -405,9 +397,9 @@ def solve_window(Q, window: float, cap: int = 1 << 16, fix_bits: int = 0, fix_va
     return int(cnt[0]), codes[:k].copy(), E[:k].copy(), info.as_dict()
 
 
-def solve_batched(Qs, topk: int = 0, states_cap: int = 64, stream=None) -> list[Result]:
+def solve_batched(Qs, topk: int = 0, states_cap: int = 64, stream=None) -> "BatchResults":
     """Solve many instances in one persistent launch (qubo_solve_batched).  All matrices must
-    share one dtype."""
+    share one dtype.  The results are array-backed; indexing or iterating gives Result objects."""
     lib = load_library()
     packed, ns, offs, dt = _pack(Qs)
     count = len(ns)
