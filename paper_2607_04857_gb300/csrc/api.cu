@@ -1015,8 +1015,13 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
     uint64_t *items = (uint64_t *)(up + j.off_items);
     uint64_t total = 0;
     for (int i = 0; i < ni; ++i) {
+        items[i] = total;
+        total += j.insts[i]->items;
+    }
+    items[ni] = total;
+    // descriptors, initial state and coupling matrices; instances write disjoint regions
+    auto stage_one = [&](int i) {
         HostInst &h = *j.insts[i];
-        const size_t nn = (size_t)h.n * h.n;
         Inst d{};
         d.n = h.n;
         d.B = h.B;
@@ -1070,7 +1075,6 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
             d.W64 = nullptr;
             d.U64 = nullptr;
         }
-        (void)nn;
         d.Es = h.small ? nullptr : dev + j.off_Es[i];
         d.M = h.small ? nullptr : dev + j.off_M[i];
         d.EL = h.small ? nullptr : dev + j.off_EL[i];
@@ -1082,10 +1086,21 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
         s.thr = encode_thr(j.acc, h.thr0);
         s.gmin = encode_max(j.acc);
         hs[i] = s;
-        items[i] = total;
-        total += h.items;
+    };
+    const int nt = ni < 64 ? 1 : std::max(1, std::min<int>(ni / 64, (int)std::thread::hardware_concurrency()));
+    if (nt == 1) {
+        for (int i = 0; i < ni; ++i)
+            stage_one(i);
+    } else {
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back([&, t] {
+                for (int i = (int)((int64_t)ni * t / nt); i < (int)((int64_t)ni * (t + 1) / nt); ++i)
+                    stage_one(i);
+            });
+        for (auto &x : th)
+            x.join();
     }
-    items[ni] = total;
     j.total_items = total;
     j.rec_cap = std::min(ws.rec_cap, record_capacity());
     int bps = scan_blocks_per_sm(j.acc, j.K <= 1, j.variant);

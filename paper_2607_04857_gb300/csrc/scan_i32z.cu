@@ -75,26 +75,47 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
         wz[m] = s;
     }
     __syncwarp();
-    // Lanes take consecutive walk steps (coalesced E_L reads); a block's minimum is reduced
-    // across the lanes that hold it (butterfly over aligned groups of min(2^Z, 32) lanes) and,
-    // for blocks longer than a warp, across the warp iterations of the block.
+    // Lanes take consecutive walk steps (coalesced E_L reads).  The zero-row sum a step needs
+    // depends only on its offset in the block and, through the top Gray bit, on the block's
+    // parity, so each lane keeps the few it needs in registers.  A block's minimum is reduced
+    // over the lanes that hold it (butterfly over aligned groups of min(2^Z, 32) lanes).
     const int32_t *EL = (const int32_t *)d.EL;
-    {
-        const int zl = Z < 5 ? Z : 5;                   // butterfly levels
-        const int per = Z > 5 ? 1 << (Z - 5) : 1;       // warp iterations per block
+    if (Z >= 5) {
+        constexpr int kPer = 1 << (kZMaxRows - 5);  // warp iterations per block, at most
+        const int per = 1 << (Z - 5);
+        int32_t wze[kPer], wzo[kPer];
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) {
+            const int ie = (t << 5) + lane, io = ie | (1 << Z);
+            wze[t] = t < per ? wz[(ie ^ (ie >> 1)) & (nz - 1)] : 0;
+            wzo[t] = t < per ? wz[(io ^ (io >> 1)) & (nz - 1)] : 0;
+        }
+#pragma unroll 4
+        for (int kb = 0; kb < nblk; ++kb) {
+            const int32_t *e = EL + (kb << Z) + lane;
+            const bool odd = kb & 1;
+            int32_t acc = INT32_MAX;
+#pragma unroll
+            for (int t = 0; t < kPer; ++t)
+                if (t < per)
+                    acc = min(acc, __ldg(e + (t << 5)) + (odd ? wzo[t] : wze[t]));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                acc = min(acc, __shfl_xor_sync(kFull, acc, o));
+            if (lane == (kb & 31))
+                mel[kb] = acc;
+        }
+    } else {
+        // blocks shorter than a warp: a lane's step offset, and so its zero-row sum, is fixed
+        const int32_t wl = wz[(lane ^ (lane >> 1)) & (nz - 1)];
         const int total = 1 << L, iters = (total + 31) >> 5;
-        int32_t acc = INT32_MAX;
         for (int t = 0; t < iters; ++t) {
             const int i = (t << 5) + lane;
-            if (i < total)
-                acc = min(acc, EL[i] + wz[(i ^ (i >> 1)) & (nz - 1)]);
-            if ((t + 1) % per == 0) {
-                for (int o = 1; o < (1 << zl); o <<= 1)
-                    acc = min(acc, __shfl_xor_sync(kFull, acc, o));
-                if (i < total && (lane & ((1 << zl) - 1)) == 0)
-                    mel[i >> Z] = acc;
-                acc = INT32_MAX;
-            }
+            int32_t acc = i < total ? __ldg(EL + i) + wl : INT32_MAX;
+            for (int o = 1; o < nz; o <<= 1)
+                acc = min(acc, __shfl_xor_sync(kFull, acc, o));
+            if (i < total && (lane & (nz - 1)) == 0)
+                mel[i >> Z] = acc;
         }
     }
     __syncwarp();
