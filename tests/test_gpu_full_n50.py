@@ -1,0 +1,67 @@
+"""The whole n=50 configuration (2^50 states), cross-checked without a full oracle run.
+
+A full oracle run of 2^50 states takes weeks on the host cores, so this check pins the GPU result
+in the other ways open at full size: the FP32-lane scan and the int32 kernel (two different
+kernels) and, with QUBO_FULL_N50_PLAIN=1, the plain int64 scan must return the same minimum, tie
+set and 16 lowest states; the oracle's direct evaluator must reproduce every returned energy;
+no randomly drawn state may lie below the minimum or below the 16th lowest energy unless it is
+among the returned states.  It takes minutes of GPU time, so it runs only when asked:
+
+    QUBO_FULL_N50=1 python -m pytest tests/test_gpu_full_n50.py -q -s
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2607_04857_gb300 import workloads as wl
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow,
+              pytest.mark.skipif(os.environ.get("QUBO_FULL_N50") != "1", reason="set QUBO_FULL_N50=1 to run")]
+
+
+def test_full_n50_crosscheck():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_04857_gb300 import build as qbuild
+
+    qbuild.build()
+    import paper_2607_04857_gb300 as q
+
+    q.load_library()
+    Q = wl.config5()
+    runs = {}
+    for name, env in (("i32f", {}), ("i32", {"QUBO_NO_I16P": "1", "QUBO_NO_I32F": "1", "QUBO_NO_I32Z": "1"})):
+        saved = {k: os.environ.get(k) for k in env}
+        os.environ.update(env)
+        try:
+            runs[name] = q.solve(Q, topk=16, states_cap=1024)
+        finally:
+            for k, v in saved.items():
+                os.environ.pop(k, None) if v is None else os.environ.__setitem__(k, v)
+    if os.environ.get("QUBO_FULL_N50_PLAIN") == "1":
+        runs["i64"] = q.solve(Q, topk=16, states_cap=1024, plain=True)
+    base = runs["i32f"]
+    for name, r in runs.items():
+        print(name, r.info["acc"], "min", r.min, "ties", r.n_ties, "seconds %.1f" % r.info["seconds"],
+              "states/s %.3e" % r.info["states_per_s"])
+        assert r.info["states_scanned"] == 1 << 50
+        assert r.min == base.min and r.n_ties == base.n_ties
+        assert np.array_equal(r.ties, base.ties)
+        assert np.array_equal(r.topk, base.topk) and np.array_equal(r.topk_E, base.topk_E)
+    # every returned energy, re-evaluated by the oracle's direct O(n^2) evaluator
+    for c, e in zip(base.topk, base.topk_E):
+        assert oracle.energy(Q, int(c)) == int(e)
+    for c in base.ties:
+        assert oracle.energy(Q, int(c)) == base.min
+    assert list(base.topk_E) == sorted(base.topk_E) and int(base.topk_E[0]) == base.min
+    # random states: none below the minimum; none below the 16th lowest unless returned
+    rng = np.random.default_rng(2050)
+    top = {int(c) for c in base.topk}
+    kth = int(base.topk_E[-1])
+    for x in rng.integers(0, 1 << 50, size=200_000, dtype=np.int64):
+        e = oracle.energy(Q, int(x))
+        assert e >= base.min
+        assert int(x) in top or (e, int(x)) > (kth, int(base.topk[-1]))

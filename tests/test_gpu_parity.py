@@ -255,10 +255,10 @@ def test_batched_float(q):
 
 def test_n50_sampled_subcubes(q):
     """The n=50 instance with the plan the benchmark uses (the default variant, 12 walked bits):
-    sub-cubes of 2^24 states at sampled prefixes, each checked against the oracle."""
+    sub-cubes of 2^24 states at 64 sampled prefixes, each checked against the oracle."""
     Q = wl.config5()
     rng = np.random.default_rng(50)
-    for v in rng.integers(0, 1 << 26, size=6):
+    for v in rng.integers(0, 1 << 26, size=64):
         r = q.solve(Q, topk=16, fix_bits=26, fix_value=int(v), walk_bits=12)
         i = r.info
         # the benchmark's 2^43-state steps plan 12 walked bits with the default variant too
