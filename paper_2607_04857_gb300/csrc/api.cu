@@ -33,9 +33,9 @@ constexpr int kDefaultMaxWalkBits = 12;
 // Gray steps keep the measured drift (2.4e-4 on the n=44 SK instance) well inside the budget
 // of the default 1e-3 candidate margin; the drift guard shortens it when it does not.
 constexpr int kFloatMaxWalkBits = 10;
-// The factored sparse scan reads the whole E_L table once per unit: 2^13 entries (32 KB) stay in
-// L1 and amortise the unit set-up best (measured against 2^11..2^14).
-constexpr int kZMaxWalkBits = 13;
+// The factored sparse scan reads the whole E_L table once per unit: 2^14 entries (64 KB) stay in
+// L1 and amortise the unit set-up (measured against 2^11..2^16).
+constexpr int kZMaxWalkBits = 14;
 
 double now_s()
 {
@@ -1147,7 +1147,6 @@ int job_enqueue_scan(Workspace &ws, Job &j, const void *state_init = nullptr)
     a.margin = (j.acc == ACC_F32 || j.acc == ACC_F64) ? j.margin : 0.0;
     if (j.window >= 0.0)  // record everything within the window of the running minimum
         a.margin += (j.acc == ACC_F32 || j.acc == ACC_F64) ? j.window : std::floor(j.window);
-    a.one = 1;
     a.zero = 0;
     CK(launch_scan(j.acc, a, j.blocks, j.variant, s));
     CK(record_event(ws.ev[1], s));

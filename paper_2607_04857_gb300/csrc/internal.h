@@ -17,11 +17,10 @@ enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4, ACC_I32
 // flip has a compile-time sign.  A plan needs walk_bits >= kRegRows + 1.
 constexpr int kRegRows = 4;
 // Compiled scan variants of the 4-byte accumulators: columns per thread S, register rows,
-// minimum resident blocks per SM, how the adds are issued (0: compiler's choice, 1: integer adds
-// as multiply-adds by a runtime 1 on the FMA pipe, 2: a quarter of the integer adds as 3-input
-// adds with a runtime 0 on the ALU pipe, 4: FP32 adds as paired f32x2 operations, two columns
-// per instruction, 5, 6, 7: a half, a quarter or three quarters of them paired; a mode that
-// does not apply to the column type leaves the choice to the compiler), 2- or 3-input mins.  The 8-byte accumulators
+// minimum resident blocks per SM, how the adds are issued (0: compiler's choice, 4: FP32 adds as
+// paired f32x2 operations, two columns per instruction, 5, 6, 7: a half, a quarter or three
+// quarters of them paired; the paired modes do not apply to integer columns, whose adds are
+// left to the compiler), 2- or 3-input mins.  The 8-byte accumulators
 // compile one variant: S = 16 with variant 0's register rows, blocks and min inputs.
 constexpr int kScanVariants = 8;
 constexpr int kVariantCols[kScanVariants] = {32, 16, 16, 16, 16, 16, 32, 16};
@@ -117,8 +116,8 @@ struct ScanArgs {
     unsigned long long *nrec;    // total candidates offered
     const volatile int *abort_flag;
     double margin;               // float scans: candidate margin above the threshold
-    int32_t one;                 // the constant 1, passed at run time (multiply-add variants)
-    int32_t zero;                // the constant 0, passed at run time (3-input-add variants)
+    int32_t zero;                // the constant 0, passed at run time (packed 3-input-add variants)
+    int32_t pad;
 };
 
 // Columns per thread (S) of the scan kernel for an accumulator of `bytes` bytes and a variant;
@@ -145,7 +144,7 @@ struct i16p;  // tag of the packed 16-bit accumulator (scan_impl.cuh)
 // most zero rows (walked rows without suffix couplings) and the most column-walk blocks.
 constexpr int kZVariants = 3;
 constexpr int kZCols[kZVariants] = {64, 32, 16};
-constexpr int kZMaxRows = 8;
+constexpr int kZMaxRows = 14;
 constexpr int kZMaxBlocksLog2 = 9;
 constexpr int zscan_suffix_bits(int variant)
 {

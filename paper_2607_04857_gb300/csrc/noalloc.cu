@@ -260,7 +260,6 @@ extern "C" int qubo_solve_noalloc(const void *Q_host, int n, qubo_dtype dtype, i
     a.nrec = (unsigned long long *)(base + lo.ctr) + 1;
     a.abort_flag = (const volatile int *)(base + lo.abort);
     a.margin = 0.0;
-    a.one = 1;
     a.zero = 0;
     int sms = 0;
     NA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -30,7 +30,20 @@ __device__ __forceinline__ uint64_t unpermute(uint64_t c, const uint8_t *perm)
     return o;
 }
 
-constexpr int kZWarpScratch = (1 << kZMaxRows) + (1 << kZMaxBlocksLog2);
+// Per-warp scratch: the (parity, t) table of zero-row sums (at most 2^(16-4) entries would be
+// needed for 16 zero rows; the host keeps Z <= kZMaxRows) and the block minima.
+constexpr int kZTableEntries = 1 << (kZMaxRows - 4);
+constexpr int kZWarpScratch = 1 << kZMaxBlocksLog2;
+
+// Sum of the couplings w_r of the zero rows r set in the pattern m (slow path only).
+__device__ __forceinline__ int32_t zero_row_sum(int m, const int32_t *wsm, int Z)
+{
+    int32_t s = 0;
+    for (int r = 0; r < Z; ++r)
+        if ((m >> r) & 1)
+            s += wsm[r];
+    return s;
+}
 
 template <int S, bool K1>
 __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t unit, int32_t &Treg, int lane,
@@ -42,8 +55,6 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
     constexpr int NB = 1 << B;
     const int n = d.n, L = d.L, k = d.k, BL = B + L, Z = d.Z;
     const int nz = 1 << Z, nblk = 1 << (L - Z);
-    int32_t *wz = scratch;                        // 2^Z sums of zero-row couplings w_r
-    int32_t *mel = scratch + (1 << kZMaxRows);    // per block: min_i e(i)
     InstState *st = a.state + inst;
     const int32_t *W = (const int32_t *)d.W;
 
@@ -66,39 +77,58 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
             E[g * V + e] = ev[e] + lin_e[e] + lin_t + lin_g[g];
     }
 
-    // Per-unit tables: w sums of the zero rows, then the minimum of e(i) over every block.
-    for (int m = lane; m < nz; m += 32) {
-        int32_t s = 0;
-        for (int r = 0; r < Z; ++r)
-            if ((m >> r) & 1)
-                s += wsm[r];
-        wz[m] = s;
-    }
-    __syncwarp();
-    // Lanes take consecutive walk steps (coalesced E_L reads).  The zero-row sum a step needs
-    // depends only on its offset in the block and, through the top Gray bit, on the block's
-    // parity, so each lane keeps the few it needs in registers.  A block's minimum is reduced
-    // over the lanes that hold it (butterfly over aligned groups of min(2^Z, 32) lanes).
+    // Per-unit minimum of e(i) over every block (lanes take consecutive walk steps: coalesced
+    // E_L reads).  The zero-row sum of step i is linear in the bits of g(i) = i ^ (i >> 1):
+    // bits 0-3 of g come from the lane, bit 4 from the lane and the warp iteration t, bits
+    // 5..Z-1 from t and, at the top, the block's parity.  So a lane adds its own part after its
+    // running minimum, and the t part comes from a small per-warp table (a broadcast read).
+    // A block's minimum is then reduced over the lanes that hold it.
     const int32_t *EL = (const int32_t *)d.EL;
+    int32_t *wt = stage;                         // Z >= 5: 2^(Z-4) entries (parity, t); the slow
+                                                 // path's staging reuses it after the table
+    int32_t *mel = scratch;                      // per block: min_i e(i)
     if (Z >= 5) {
-        constexpr int kPer = 1 << (kZMaxRows - 5);  // warp iterations per block, at most
-        const int per = 1 << (Z - 5);
-        int32_t wze[kPer], wzo[kPer];
-#pragma unroll
-        for (int t = 0; t < kPer; ++t) {
-            const int ie = (t << 5) + lane, io = ie | (1 << Z);
-            wze[t] = t < per ? wz[(ie ^ (ie >> 1)) & (nz - 1)] : 0;
-            wzo[t] = t < per ? wz[(io ^ (io >> 1)) & (nz - 1)] : 0;
+        const int zt = Z - 5;
+        // subset sums of w_5..w_{Z-1} by doubling (mel is free until the block minima), then
+        // wt[e] for e = (parity << zt) | t, the bits 5..Z of the step index: the Gray bits
+        // g_5..g_{Z-1} of the step are the Gray code of e cut to zt bits.
+        int32_t *gs = mel;
+        if (lane == 0)
+            gs[0] = 0;
+        __syncwarp();
+        for (int b = 0; b < zt; ++b) {
+            const int32_t wb = wsm[5 + b];
+            for (int m = lane; m < (1 << b); m += 32)
+                gs[m + (1 << b)] = gs[m] + wb;
+            __syncwarp();
         }
-#pragma unroll 4
+        for (int e = lane; e < (2 << zt); e += 32)
+            wt[e] = gs[(e ^ (e >> 1)) & ((1 << zt) - 1)];
+        int32_t a = 0;
+        for (int r = 0; r < 4; ++r)
+            if (((lane >> r) ^ (lane >> (r + 1))) & 1)
+                a += wsm[r];
+        const bool l4 = (lane >> 4) & 1;
+        const int32_t a0 = a + (l4 ? wsm[4] : 0);  // even t: bit 5 of the step index is 0
+        const int32_t a1 = a + (l4 ? 0 : wsm[4]);  // odd t
+        __syncwarp();
+        const int nt = 1 << zt;
+#pragma unroll 2
         for (int kb = 0; kb < nblk; ++kb) {
             const int32_t *e = EL + (kb << Z) + lane;
-            const bool odd = kb & 1;
-            int32_t acc = INT32_MAX;
-#pragma unroll
-            for (int t = 0; t < kPer; ++t)
-                if (t < per)
-                    acc = min(acc, __ldg(e + (t << 5)) + (odd ? wzo[t] : wze[t]));
+            const int32_t *w = wt + ((kb & 1) << zt);
+            int32_t acc;
+            if (nt == 1) {  // Z == 5: bit 5 of the step index is the block's parity
+                acc = __ldg(e) + ((kb & 1) ? a1 : a0);
+            } else {
+                int32_t ae = INT32_MAX, ao = INT32_MAX;
+#pragma unroll 4
+                for (int t = 0; t < nt; t += 2) {
+                    ae = min(ae, __ldg(e + (t << 5)) + w[t]);
+                    ao = min(ao, __ldg(e + ((t + 1) << 5)) + w[t + 1]);
+                }
+                acc = min(ae + a0, ao + a1);
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
                 acc = min(acc, __shfl_xor_sync(kFull, acc, o));
@@ -106,8 +136,11 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
                 mel[kb] = acc;
         }
     } else {
-        // blocks shorter than a warp: a lane's step offset, and so its zero-row sum, is fixed
-        const int32_t wl = wz[(lane ^ (lane >> 1)) & (nz - 1)];
+        // blocks shorter than a warp: the whole zero-row sum of a step follows from its lane
+        int32_t wl = 0;
+        for (int r = 0; r < Z; ++r)
+            if (((lane >> r) ^ (lane >> (r + 1))) & 1)
+                wl += wsm[r];
         const int total = 1 << L, iters = (total + 31) >> 5;
         for (int t = 0; t < iters; ++t) {
             const int i = (t << 5) + lane;
@@ -146,32 +179,65 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
             P = neg ? P - wsm[r] : P + wsm[r];
         }
         const int32_t cm = tree_min<int32_t, 3, S>(E);
-        if (cm + mel[kb] <= Treg + mu - P) {
-            // rare: every state of the block, 2^Z zero-row patterns x the thread's columns
+        if (__any_sync(kFull, cm + mel[kb] <= Treg + mu - P)) {
+            // rare: the warp enumerates the block together.  Lanes take consecutive walk steps
+            // (coalesced E_L reads); a step whose e(i) plus the smallest column of any lane
+            // reaches the largest threshold of any lane is broadcast, and every lane checks its
+            // own columns at that step.
 #pragma unroll
             for (int q = 0; q < S; ++q)
                 stage[q * 32 + lane] = E[q];
-            for (int i = kb << Z; i < (kb + 1) << Z; ++i) {
-                const int g = i ^ (i >> 1);
-                const int32_t el = EL[i] + wz[g & (nz - 1)];
-                int32_t tp = Treg + mu - P - el;
-                if (cm > tp)
-                    continue;
-                const uint64_t cb = cbase | ((uint64_t)g << B);
-                for (int q = 0; q < S; ++q) {
-                    const int32_t ev = stage[q * 32 + lane];
-                    if (ev <= tp) {
-                        const int32_t Et = ev + el + P;
-                        const uint32_t j = (uint32_t)(((q / V) * 32 + lane) * V + (q % V));
-                        record<T>(a, inst, Et, unpermute(cb | j, d.perm));
-                        if (K1 && Et < Treg) {
-                            Treg = Et;
-                            tp = Treg + mu - P - el;
-                            Tr<T>::thr_min(st, Et);
+            int32_t cmin = cm, tmax = Treg;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                cmin = min(cmin, __shfl_xor_sync(kFull, cmin, o));
+                tmax = max(tmax, __shfl_xor_sync(kFull, tmax, o));
+            }
+            const int32_t umax = tmax + mu - P;
+            const int i0 = kb << Z;
+            int ii = i0 + lane;
+            int gi = ii ^ (ii >> 1);
+            int32_t zs = zero_row_sum(gi & (nz - 1), wsm, Z);
+            for (int off = 0; off < nz; off += 32) {
+                if (off > 0) {  // ii advances by 32: refresh the zero-row bits that changed
+                    ii += 32;
+                    const int gn = ii ^ (ii >> 1);
+                    int diff = (gi ^ gn) & (nz - 1);
+                    while (diff) {
+                        const int r = __ffs(diff) - 1;
+                        diff &= diff - 1;
+                        zs = ((gn >> r) & 1) ? zs + wsm[r] : zs - wsm[r];
+                    }
+                    gi = gn;
+                }
+                const bool valid = off + lane < nz;
+                const int32_t el = valid ? __ldg(EL + ii) + zs : 0;
+                unsigned m = __ballot_sync(kFull, valid && cmin + el <= umax);
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int32_t els = __shfl_sync(kFull, el, src);
+                    const int is = i0 + off + src;
+                    int32_t tp = Treg + mu - P - els;
+                    if (cm > tp)
+                        continue;
+                    const uint64_t cb = cbase | ((uint64_t)(is ^ (is >> 1)) << B);
+                    for (int q = 0; q < S; ++q) {
+                        const int32_t ev = stage[q * 32 + lane];
+                        if (ev <= tp) {
+                            const int32_t Et = ev + els + P;
+                            const uint32_t j = (uint32_t)(((q / V) * 32 + lane) * V + (q % V));
+                            record<T>(a, inst, Et, unpermute(cb | j, d.perm));
+                            if (K1 && Et < Treg) {
+                                Treg = Et;
+                                tp = Treg + mu - P - els;
+                                Tr<T>::thr_min(st, Et);
+                            }
                         }
                     }
                 }
             }
+            __syncwarp();
         }
     }
     if (lane == 0)
@@ -181,19 +247,22 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
 template <int S, bool K1>
 __global__ void __launch_bounds__(kScanThreads, 3) zscan_kernel(const ScanArgs a)
 {
-    __shared__ int32_t stage_all[kScanThreads / 32][S * 32];
+    __shared__ int32_t stage_all[kScanThreads / 32][S * 32 > kZTableEntries ? S * 32 : kZTableEntries];
     __shared__ int32_t wsm_all[kScanThreads / 32][kMaxWalkBits];
     __shared__ int32_t scratch_all[kScanThreads / 32][kZWarpScratch];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int cur = -1;
     int32_t Treg = 0;
+    // The next work item is claimed before the current one is scanned, hiding the atomic.
+    unsigned long long next = lane == 0 ? atomicAdd(a.queue, 1ull) : 0ull;
     for (;;) {
         unsigned long long item = 0;
         int stop = 0;
         if (lane == 0) {
             stop = *a.abort_flag != 0;
-            if (!stop)
-                item = atomicAdd(a.queue, 1ull);
+            item = next;
+            if (!stop && item < a.total_items)
+                next = atomicAdd(a.queue, 1ull);
         }
         stop = __shfl_sync(kFull, stop, 0);
         item = __shfl_sync(kFull, item, 0);

@@ -493,10 +493,9 @@ __device__ __forceinline__ void column_fields(F f0, int lane, F &lin_t, F (&lin_
 }
 
 // ---- one work unit: all 2^(B+L) states with fixed bits x_f = unit --------------------------------
-// ADDM == 4 issues FP32 column adds as paired f32x2 operations (two columns per instruction).
-// ADDM == 1 issues the integer adds as multiply-adds by a runtime +-1 (fused multiply-add
-// pipe) so that the integer ALU pipe is left to the mins; ADDM == 2 sends a quarter of them to
-// the ALU pipe as 3-input adds; MINM selects 2- or 3-input mins.
+// ADDM >= 4 issues some or all FP32 column adds as paired f32x2 operations (two columns per
+// instruction; 4: all pairs, 5: every second, 6: every fourth, 7: three in four); other modes
+// leave the adds to the compiler.  MINM selects 2- or 3-input mins.
 template <class T, int S, int RC, bool K1, int ADDM, int MINM>
 __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t unit,
                                           typename Tr<T>::TP &Treg, int lane, typename Tr<T>::TC *stage,
@@ -628,21 +627,6 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
                                 E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
                                 E[q + 1] = neg ? E[q + 1] - Mr[kk][q + 1] : E[q + 1] + Mr[kk][q + 1];
                             }
-                        }
-                    } else if constexpr (ADDM == 1 && kIntCols) {
-                        const TC mul = neg ? -(TC)a.one : (TC)a.one;
-#pragma unroll
-                        for (int q = 0; q < S; ++q)
-                            E[q] = E[q] + Mr[kk][q] * mul;
-                    } else if constexpr (ADDM == 2 && kIntCols) {
-                        const TC mul = neg ? -(TC)a.one : (TC)a.one;
-                        const TC z = (TC)a.zero;
-#pragma unroll
-                        for (int q = 0; q < S; ++q) {
-                            if (q % 4 == 0)
-                                E[q] = neg ? (E[q] - Mr[kk][q]) + z : (E[q] + Mr[kk][q]) + z;
-                            else
-                                E[q] = E[q] + Mr[kk][q] * mul;
                         }
                     } else {
 #pragma unroll
@@ -976,13 +960,16 @@ __global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs
     TP *wsm = wsm_all[warp];
     int cur = -1;
     TP Treg = (TP)0;
+    // The next work item is claimed before the current one is scanned, hiding the atomic.
+    unsigned long long next = lane == 0 ? atomicAdd(a.queue, 1ull) : 0ull;
     for (;;) {
         unsigned long long item = 0;
         int stop = 0;
         if (lane == 0) {
             stop = *a.abort_flag != 0;
-            if (!stop)
-                item = atomicAdd(a.queue, 1ull);
+            item = next;
+            if (!stop && item < a.total_items)
+                next = atomicAdd(a.queue, 1ull);
         }
         stop = __shfl_sync(kFull, stop, 0);
         item = __shfl_sync(kFull, item, 0);
