@@ -113,3 +113,57 @@ def test_sparse_disabled_falls_back(q, monkeypatch):
     r = q.solve(Q, topk=8)
     assert r.info["acc"] in ("i16p", "i32f", "i32")
     check_int(r, o)
+
+
+def test_sparse_relabelled_instance(q):
+    """Relabelling the variables (Sec. 2.4) changes the scan order the host picks; the minimum and
+    tie count stay, and the codes map through the relabelling."""
+    n = 28
+    Q = wl.sparse_int(n, 0.08, -300, 300, seed=21)
+    perm = np.random.default_rng(5).permutation(n)
+    Qp = Q[np.ix_(perm, perm)]  # variable a of Qp is variable perm[a] of Q
+    r, rp = q.solve(Q, topk=6), q.solve(Qp, topk=6)
+    assert r.info["acc"] == rp.info["acc"] == "i32z"
+    assert r.min == rp.min and r.n_ties == rp.n_ties
+
+    def to_q(c):
+        return sum(1 << int(perm[a]) for a in range(n) if (int(c) >> a) & 1)
+
+    assert sorted(to_q(c) for c in rp.ties) == [int(c) for c in r.ties]
+    check_int(rp, oracle.solve(Qp, topk=6))
+
+
+def test_sparse_large_k_and_subcube_with_fixed_top_bits(q):
+    Q = wl.sparse_int(36, 0.07, -50, 50, seed=36)
+    r = q.solve(Q, topk=1024, fix_bits=6, fix_value=37, states_cap=4096)
+    assert r.info["acc"] == "i32z"
+    check_int(r, oracle.solve(Q, topk=1024, fix_bits=6, fix_value=37, cap=4096))
+
+
+def test_sparse_problem_api_and_merge(q):
+    """Device-resident problem, two halves of the cube, merged on the host."""
+    Q = wl.sparse_int(30, 0.08, -200, 200, seed=30)
+    p = q.Problem(Q, topk=8)
+    parts = []
+    for v in (0, 1):
+        p.run(1, v)
+        parts.append(p.fetch(states_cap=1024))
+    p.close()
+    assert parts[0].info["acc"] == "i32z"
+    m = q.merge_all(parts, 1024, 8)
+    check_int(m, oracle.solve(Q, topk=8, cap=1024))
+
+
+def test_sparse_wide_subproblem(q):
+    """A 70-variable sparse instance: one outer value's 28-variable sub-problem (solved alone,
+    in the factored scan), against the oracle's reduction."""
+    Q = wl.sparse_int(70, 0.05, -500, 500, seed=70)
+    v = 123456789
+    r = q.solve_wide(Q, 28, outer_begin=v, outer_count=1, topk=4)
+    assert r.info["acc"] == "i32z" and r.info["states_scanned"] == 1 << 28
+    R, c = oracle.reduce(Q, 28, v)
+    o = oracle.solve(R, topk=4)
+    assert r.min == o.min + c and r.n_ties == o.n_ties
+    assert r.ties == [int(t) | (v << 28) for t in o.ties]
+    assert r.topk == [int(t) | (v << 28) for t in o.topk]
+    assert r.topk_E.tolist() == [int(e) + c for e in o.topk_E]
