@@ -154,14 +154,14 @@ class ClockSampler:
 # helpers
 # ---------------------------------------------------------------------------------------------
 
-ACC_SOURCE = {"i32": "scan_i32.cu", "i64": "scan_i64.cu", "f32": "scan_f32.cu", "f64": "scan_f64.cu",
-              "i32f": "scan_i32f.cu", "i16p": "scan_i16p.cu", "i32z": "scan_i32z.cu"}
+ACC_SOURCE = {"i32": ["scan_i32.cu"], "i64": ["scan_i64.cu"], "f32": ["scan_f32.cu"], "f64": ["scan_f64.cu"],
+              "i32f": ["scan_i32f.cu"], "i16p": ["scan_i16p.cu"], "i32z": ["scan_i32z.cu", "zscan.h"]}
 
 
 def kernel_source_hash(acc: str) -> str:
     """Hash of the sources the accumulator's scan kernel is compiled from."""
     h = hashlib.sha256()
-    for f in ("scan_impl.cuh", "internal.h", ACC_SOURCE.get(acc, "scan_i32.cu")):
+    for f in ["scan_impl.cuh", "internal.h"] + ACC_SOURCE.get(acc, ["scan_i32.cu"]):
         with open(os.path.join(ROOT, "paper_2607_04857_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -416,6 +416,9 @@ int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int wal
             }
             if (chosen == ACC_I32Z) {
                 h.acc = ACC_I32Z;
+                // every walked row factored: one block per unit, the kernel without column registers
+                if (!zenv && h.variant == 0 && h.Z == h.L && h.Z >= 7)
+                    h.variant = 3;
                 return QUBO_OK;
             }
             h.Z = 0;

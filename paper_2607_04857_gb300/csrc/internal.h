@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "zscan.h"
+
 namespace qubo {
 
 // ACC_I32F: integer energies scanned exactly in FP32 lanes (partial sums below 2^24).
@@ -139,18 +141,6 @@ constexpr int packed_suffix_bits(int variant) { return packed_words(variant) == 
 
 struct i32f;  // tag of the integer-in-FP32 accumulator (scan_impl.cuh)
 struct i16p;  // tag of the packed 16-bit accumulator (scan_impl.cuh)
-
-// Factored scan of sparse instances (scan_i32z.cu): columns per thread of each variant, the
-// most zero rows (walked rows without suffix couplings) and the most column-walk blocks.
-constexpr int kZVariants = 3;
-constexpr int kZCols[kZVariants] = {64, 32, 16};
-constexpr int kZMaxRows = 14;
-constexpr int kZMaxBlocksLog2 = 9;
-constexpr int zscan_suffix_bits(int variant)
-{
-    return kZCols[(variant >= 0 && variant < kZVariants) ? variant : 0] == 64 ? 11
-           : kZCols[(variant >= 0 && variant < kZVariants) ? variant : 0] == 32 ? 10 : 9;
-}
 
 // ---- launchers (scan_*.cu, one translation unit per accumulator type) -------------------------
 template <class T>

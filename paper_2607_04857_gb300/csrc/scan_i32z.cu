@@ -87,7 +87,71 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
     int32_t *wt = stage;                         // Z >= 5: 2^(Z-4) entries (parity, t); the slow
                                                  // path's staging reuses it after the table
     int32_t *mel = scratch;                      // per block: min_i e(i)
-    if (Z >= 5) {
+    if (Z >= 7) {
+        // Lanes take 4 consecutive steps each (one 16-byte E_L read), a warp iteration t covers
+        // 128 steps: step bits 0-1 are the element k, bits 2-6 the lane, bits 7..Z-1 t, bit Z
+        // the block's parity.  Gray bits g_0..g_5 follow from (k, lane), g_6 from the lane's top
+        // bit and bit 7 of the step, g_7..g_{Z-1} from (parity, t) through a per-warp table.
+        const int zt = Z - 7;
+        int32_t *gs = mel;
+        if (lane == 0)
+            gs[0] = 0;
+        __syncwarp();
+        for (int b = 0; b < zt; ++b) {
+            const int32_t wb = wsm[7 + b];
+            for (int m = lane; m < (1 << b); m += 32)
+                gs[m + (1 << b)] = gs[m] + wb;
+            __syncwarp();
+        }
+        for (int e = lane; e < (2 << zt); e += 32)
+            wt[e] = gs[(e ^ (e >> 1)) & ((1 << zt) - 1)];
+        int32_t a = 0;  // g_2..g_5 from the lane bits
+        for (int r = 0; r < 4; ++r)
+            if (((lane >> r) ^ (lane >> (r + 1))) & 1)
+                a += wsm[2 + r];
+        const bool l0 = lane & 1, l4 = (lane >> 4) & 1;
+        int32_t ae[4], ao[4];  // per element k, for bit 7 of the step = 0 (ae) and 1 (ao)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool g0 = (k ^ (k >> 1)) & 1, g1 = ((k >> 1) & 1) ^ l0;
+            const int32_t base = a + (g0 ? wsm[0] : 0) + (g1 ? wsm[1] : 0);
+            ae[k] = base + (l4 ? wsm[6] : 0);
+            ao[k] = base + (l4 ? 0 : wsm[6]);
+        }
+        __syncwarp();
+        const int nt = 1 << zt;
+        for (int kb = 0; kb < nblk; ++kb) {
+            const int32_t *e = EL + (kb << Z) + 4 * lane;
+            const int32_t *w = wt + ((kb & 1) << zt);
+            int32_t acc;
+            if (nt == 1) {  // Z == 7: bit 7 of the step index is the block's parity
+                int32_t v[4], ak[4];
+                vload<int32_t>(e, v);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    ak[k] = (kb & 1) ? ao[k] : ae[k];
+                acc = min(__vimin3_s32(v[0] + ak[0], v[1] + ak[1], v[2] + ak[2]), v[3] + ak[3]);
+            } else {
+                int32_t me = INT32_MAX, mo = INT32_MAX;
+#pragma unroll 2
+                for (int t = 0; t < nt; t += 2) {
+                    int32_t v[4], u[4];
+                    vload<int32_t>(e + (t << 7), v);
+                    vload<int32_t>(e + ((t + 1) << 7), u);
+                    const int32_t mv = min(__vimin3_s32(v[0] + ae[0], v[1] + ae[1], v[2] + ae[2]), v[3] + ae[3]);
+                    const int32_t mu2 = min(__vimin3_s32(u[0] + ao[0], u[1] + ao[1], u[2] + ao[2]), u[3] + ao[3]);
+                    me = min(me, mv + w[t]);
+                    mo = min(mo, mu2 + w[t + 1]);
+                }
+                acc = min(me, mo);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+                acc = min(acc, __shfl_xor_sync(kFull, acc, o));
+            if (lane == (kb & 31))
+                mel[kb] = acc;
+        }
+    } else if (Z >= 5) {
         const int zt = Z - 5;
         // subset sums of w_5..w_{Z-1} by doubling (mel is free until the block minima), then
         // wt[e] for e = (parity << zt) | t, the bits 5..Z of the step index: the Gray bits
@@ -240,8 +304,64 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
             __syncwarp();
         }
     }
-    if (lane == 0)
-        atomicAdd(&st->scanned, 1ull << BL);
+}
+
+// Persistent work loop of the factored kernels.  Work units are small here (2^24..2^27 states,
+// microseconds each), so a warp claims them in chunks and counts the states it scanned locally,
+// flushing the count when the instance changes and at exit: one atomic per chunk on the queue
+// and one per instance on the counter, instead of two per unit on single addresses.
+template <class UnitFn>
+__device__ __forceinline__ void persistent_units(const ScanArgs &a, int lane, int32_t &Treg, UnitFn &&unit_fn)
+{
+    constexpr unsigned long long kChunk = 8;
+    int cur = -1;
+    unsigned long long done = 0;
+    unsigned long long next = lane == 0 ? atomicAdd(a.queue, kChunk) : 0ull;
+    for (;;) {
+        unsigned long long base = 0;
+        int stop = 0;
+        if (lane == 0) {
+            stop = *a.abort_flag != 0;
+            base = next;
+            if (!stop && base < a.total_items)
+                next = atomicAdd(a.queue, kChunk);
+        }
+        stop = __shfl_sync(kFull, stop, 0);
+        base = __shfl_sync(kFull, base, 0);
+        if (stop || base >= a.total_items)
+            break;
+        const unsigned long long end = base + kChunk < a.total_items ? base + kChunk : (unsigned long long)a.total_items;
+        for (unsigned long long item = base; item < end; ++item) {
+            int inst = 0;
+            if (a.n_inst > 1) {
+                int lo = 0, hi = a.n_inst;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (a.item_base[mid] <= item)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                inst = lo;
+            }
+            if (inst != cur) {
+                if (lane == 0 && done)
+                    atomicAdd(&a.state[cur].scanned, done);
+                done = 0;
+                cur = inst;
+                Treg = Tr<int32_t>::thr_load(a.state + inst);
+            }
+            const Inst d = a.inst[inst];
+            if (d.small) {
+                small_unit<int32_t>(a, d, inst, lane);  // counts its own states
+            } else {
+                unit_fn(d, inst, d.unit_begin + (item - a.item_base[inst]));
+                done += 1ull << (d.B + d.L);
+            }
+        }
+    }
+    if (lane == 0 && done)
+        atomicAdd(&a.state[cur].scanned, done);
 }
 
 template <int S, bool K1>
@@ -251,54 +371,197 @@ __global__ void __launch_bounds__(kScanThreads, 3) zscan_kernel(const ScanArgs a
     __shared__ int32_t wsm_all[kScanThreads / 32][kMaxWalkBits];
     __shared__ int32_t scratch_all[kScanThreads / 32][kZWarpScratch];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int cur = -1;
     int32_t Treg = 0;
-    // The next work item is claimed before the current one is scanned, hiding the atomic.
-    unsigned long long next = lane == 0 ? atomicAdd(a.queue, 1ull) : 0ull;
-    for (;;) {
-        unsigned long long item = 0;
-        int stop = 0;
-        if (lane == 0) {
-            stop = *a.abort_flag != 0;
-            item = next;
-            if (!stop && item < a.total_items)
-                next = atomicAdd(a.queue, 1ull);
-        }
-        stop = __shfl_sync(kFull, stop, 0);
-        item = __shfl_sync(kFull, item, 0);
-        if (stop || item >= a.total_items)
-            break;
-        int inst = 0;
-        if (a.n_inst > 1) {
-            int lo = 0, hi = a.n_inst;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (a.item_base[mid] <= item)
-                    lo = mid;
-                else
-                    hi = mid;
-            }
-            inst = lo;
-        }
-        if (inst != cur) {
-            cur = inst;
-            Treg = Tr<int32_t>::thr_load(a.state + inst);
-        }
-        const Inst d = a.inst[inst];
-        const uint64_t off = item - a.item_base[inst];
-        if (d.small)
-            small_unit<int32_t>(a, d, inst, lane);
-        else
-            zscan_unit<S, K1>(a, d, inst, d.unit_begin + off, Treg, lane, wsm_all[warp], scratch_all[warp],
-                              stage_all[warp]);
+    persistent_units(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
+        zscan_unit<S, K1>(a, d, inst, unit, Treg, lane, wsm_all[warp], scratch_all[warp], stage_all[warp]);
+    });
+}
+
+// ---- one block per unit: every walked row factored out (Z = L >= 7) --------------------------
+// The columns are used once (their minimum, and in a hit unit each column again), so they are
+// not kept in registers: the kernel runs at more warps per SM to hide the E_L reads' latency.
+
+// Minimum over the 2^Z walk steps of a unit of e(i) = E_L(g(i)) + sum of the zero-row couplings
+// of the set bits of g(i) (Z >= 7; the same decomposition as zscan_unit's block minima, parity 0).
+__device__ __forceinline__ int32_t walk_min_one(const int32_t *EL, int Z, int lane, const int32_t *wsm, int32_t *wt,
+                                                int32_t *gs)
+{
+    const int zt = Z - 7;
+    if (lane == 0)
+        gs[0] = 0;
+    __syncwarp();
+    for (int b = 0; b < zt; ++b) {
+        const int32_t wb = wsm[7 + b];
+        for (int m = lane; m < (1 << b); m += 32)
+            gs[m + (1 << b)] = gs[m] + wb;
+        __syncwarp();
     }
+    for (int e = lane; e < (1 << zt); e += 32)  // parity 0: only the lower half of the table
+        wt[e] = gs[(e ^ (e >> 1)) & ((1 << zt) - 1)];
+    int32_t a = 0;
+    for (int r = 0; r < 4; ++r)
+        if (((lane >> r) ^ (lane >> (r + 1))) & 1)
+            a += wsm[2 + r];
+    const bool l0 = lane & 1, l4 = (lane >> 4) & 1;
+    int32_t ae[4], ao[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const bool g0 = (k ^ (k >> 1)) & 1, g1 = ((k >> 1) & 1) ^ l0;
+        const int32_t base = a + (g0 ? wsm[0] : 0) + (g1 ? wsm[1] : 0);
+        ae[k] = base + (l4 ? wsm[6] : 0);
+        ao[k] = base + (l4 ? 0 : wsm[6]);
+    }
+    __syncwarp();
+    const int32_t *e = EL + 4 * lane;
+    int32_t acc;
+    if (zt == 0) {
+        int32_t v[4];
+        vload<int32_t>(e, v);
+        acc = min(__vimin3_s32(v[0] + ae[0], v[1] + ae[1], v[2] + ae[2]), v[3] + ae[3]);
+    } else {
+        int32_t me = INT32_MAX, mo = INT32_MAX;
+        const int nt = 1 << zt;
+#pragma unroll 4
+        for (int t = 0; t < nt; t += 2) {
+            int32_t v[4], u[4];
+            vload<int32_t>(e + (t << 7), v);
+            vload<int32_t>(e + ((t + 1) << 7), u);
+            const int32_t mv = min(__vimin3_s32(v[0] + ae[0], v[1] + ae[1], v[2] + ae[2]), v[3] + ae[3]);
+            const int32_t mw = min(__vimin3_s32(u[0] + ao[0], u[1] + ao[1], u[2] + ao[2]), u[3] + ao[3]);
+            me = min(me, mv + wt[t]);
+            mo = min(mo, mw + wt[t + 1]);
+        }
+        acc = min(me, mo);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        acc = min(acc, __shfl_xor_sync(kFull, acc, o));
+    return acc;
+}
+
+template <int S, bool K1>
+__device__ void zscan_unit_one(const ScanArgs &a, const Inst &d, int inst, uint64_t unit, int32_t &Treg, int lane,
+                               int32_t *wsm, int32_t *wt, int32_t *gs, int32_t *lin_sm)
+{
+    using T = int32_t;
+    constexpr int V = 4, G = S / V, LOGG = ilog2c(G);
+    constexpr int B = 2 + 5 + LOGG;
+    const int n = d.n, Z = d.L, k = d.k, BL = B + Z, nz = 1 << Z;
+    InstState *st = a.state + inst;
+    const int32_t *W = (const int32_t *)d.W;
+
+    int32_t f0, cx;
+    unit_fields<T>(W, n, k, BL, unit, lane, f0, cx);
+    __syncwarp();
+    if (lane >= B && lane < BL)
+        wsm[lane - B] = f0;
+    __syncwarp();
+    int32_t lin_t, lin_e[V], lin_g[G];
+    column_fields<int32_t, V, G>(f0, lane, lin_t, lin_e, lin_g);
+    const int32_t *Es = (const int32_t *)d.Es;
+    // column j = E_s(j) + lin(j), j = (g * 32 + lane) * 4 + e; only its minimum is kept
+    auto column = [&](int g, int e, const int32_t (&ev)[V]) { return ev[e] + lin_e[e] + lin_t + lin_g[g]; };
+    int32_t cm = INT32_MAX;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        int32_t ev[V];
+        vload<int32_t>(Es + (g * 32 + lane) * V, ev);
+        cm = min(cm, __vimin3_s32(column(g, 0, ev), column(g, 1, ev), min(column(g, 2, ev), column(g, 3, ev))));
+    }
+    const int32_t *EL = (const int32_t *)d.EL;
+    const int32_t mel = walk_min_one(EL, Z, lane, wsm, wt, gs);
+    {
+        const int32_t tg = Tr<T>::thr_load(st);
+        Treg = K1 ? min(Treg, tg) : tg;
+    }
+    const int32_t mu = (int32_t)a.margin;
+    const int32_t P = cx;
+    const uint64_t cbase = unit << BL;
+    if (__any_sync(kFull, cm + mel <= Treg + mu - P)) {
+        // rare: as in zscan_unit, the warp enumerates the unit's steps together; each lane
+        // recomputes its columns at a broadcast step
+        int32_t cmin = cm, tmax = Treg;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cmin = min(cmin, __shfl_xor_sync(kFull, cmin, o));
+            tmax = max(tmax, __shfl_xor_sync(kFull, tmax, o));
+        }
+        const int32_t umax = tmax + mu - P;
+#pragma unroll
+        for (int g = 0; g < G; ++g)  // the slow path indexes the column groups at run time
+            lin_sm[g * 32 + lane] = lin_g[g];
+        int ii = lane;
+        int gi = ii ^ (ii >> 1);
+        int32_t zs = zero_row_sum(gi & (nz - 1), wsm, Z);
+        for (int off = 0; off < nz; off += 32) {
+            if (off > 0) {
+                ii += 32;
+                const int gn = ii ^ (ii >> 1);
+                int diff = (gi ^ gn) & (nz - 1);
+                while (diff) {
+                    const int r = __ffs(diff) - 1;
+                    diff &= diff - 1;
+                    zs = ((gn >> r) & 1) ? zs + wsm[r] : zs - wsm[r];
+                }
+                gi = gn;
+            }
+            const int32_t el = __ldg(EL + ii) + zs;
+            unsigned m = __ballot_sync(kFull, cmin + el <= umax);
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                const int32_t els = __shfl_sync(kFull, el, src);
+                const int is = off + src;
+                int32_t tp = Treg + mu - P - els;
+                if (cm > tp)
+                    continue;
+                const uint64_t cb = cbase | ((uint64_t)(is ^ (is >> 1)) << B);
+                for (int g = 0; g < G; ++g) {
+                    int32_t ev[V];
+                    vload<int32_t>(Es + (g * 32 + lane) * V, ev);
+                    const int32_t lg = lin_sm[g * 32 + lane];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const int32_t c = ev[e] + lin_e[e] + lin_t + lg;
+                        if (c <= tp) {
+                            const int32_t Et = c + els + P;
+                            const uint32_t j = (uint32_t)((g * 32 + lane) * V + e);
+                            record<T>(a, inst, Et, unpermute(cb | j, d.perm));
+                            if (K1 && Et < Treg) {
+                                Treg = Et;
+                                tp = Treg + mu - P - els;
+                                Tr<T>::thr_min(st, Et);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int S, bool K1>
+__global__ void __launch_bounds__(kScanThreads, 6) zscan_one_kernel(const ScanArgs a)
+{
+    __shared__ int32_t wsm_all[kScanThreads / 32][kMaxWalkBits];
+    __shared__ int32_t wt_all[kScanThreads / 32][1 << (kZMaxRows - 7)];
+    __shared__ int32_t gs_all[kScanThreads / 32][1 << (kZMaxRows - 7)];
+    __shared__ int32_t lin_all[kScanThreads / 32][S / 4 * 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t Treg = 0;
+    persistent_units(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
+        zscan_unit_one<S, K1>(a, d, inst, unit, Treg, lane, wsm_all[warp], wt_all[warp], gs_all[warp],
+                              lin_all[warp]);
+    });
 }
 
 template <bool K1>
 auto zpick(int variant)
 {
-    return variant == 2 ? zscan_kernel<kZCols[2], K1>
-           : variant == 1 ? zscan_kernel<kZCols[1], K1> : zscan_kernel<kZCols[0], K1>;
+    return variant == 3   ? zscan_one_kernel<kZCols[3], K1>
+           : variant == 2 ? zscan_kernel<kZCols[2], K1>
+           : variant == 1 ? zscan_kernel<kZCols[1], K1>
+                          : zscan_kernel<kZCols[0], K1>;
 }
 
 }  // namespace
