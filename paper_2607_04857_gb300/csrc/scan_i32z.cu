@@ -306,64 +306,6 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
     }
 }
 
-// Persistent work loop of the factored kernels.  Work units are small here (2^24..2^27 states,
-// microseconds each), so a warp claims them in chunks and counts the states it scanned locally,
-// flushing the count when the instance changes and at exit: one atomic per chunk on the queue
-// and one per instance on the counter, instead of two per unit on single addresses.
-template <class UnitFn>
-__device__ __forceinline__ void persistent_units(const ScanArgs &a, int lane, int32_t &Treg, UnitFn &&unit_fn)
-{
-    constexpr unsigned long long kChunk = 8;
-    int cur = -1;
-    unsigned long long done = 0;
-    unsigned long long next = lane == 0 ? atomicAdd(a.queue, kChunk) : 0ull;
-    for (;;) {
-        unsigned long long base = 0;
-        int stop = 0;
-        if (lane == 0) {
-            stop = *a.abort_flag != 0;
-            base = next;
-            if (!stop && base < a.total_items)
-                next = atomicAdd(a.queue, kChunk);
-        }
-        stop = __shfl_sync(kFull, stop, 0);
-        base = __shfl_sync(kFull, base, 0);
-        if (stop || base >= a.total_items)
-            break;
-        const unsigned long long end = base + kChunk < a.total_items ? base + kChunk : (unsigned long long)a.total_items;
-        for (unsigned long long item = base; item < end; ++item) {
-            int inst = 0;
-            if (a.n_inst > 1) {
-                int lo = 0, hi = a.n_inst;
-                while (hi - lo > 1) {
-                    const int mid = (lo + hi) >> 1;
-                    if (a.item_base[mid] <= item)
-                        lo = mid;
-                    else
-                        hi = mid;
-                }
-                inst = lo;
-            }
-            if (inst != cur) {
-                if (lane == 0 && done)
-                    atomicAdd(&a.state[cur].scanned, done);
-                done = 0;
-                cur = inst;
-                Treg = Tr<int32_t>::thr_load(a.state + inst);
-            }
-            const Inst d = a.inst[inst];
-            if (d.small) {
-                small_unit<int32_t>(a, d, inst, lane);  // counts its own states
-            } else {
-                unit_fn(d, inst, d.unit_begin + (item - a.item_base[inst]));
-                done += 1ull << (d.B + d.L);
-            }
-        }
-    }
-    if (lane == 0 && done)
-        atomicAdd(&a.state[cur].scanned, done);
-}
-
 template <int S, bool K1>
 __global__ void __launch_bounds__(kScanThreads, 3) zscan_kernel(const ScanArgs a)
 {
@@ -372,7 +314,7 @@ __global__ void __launch_bounds__(kScanThreads, 3) zscan_kernel(const ScanArgs a
     __shared__ int32_t scratch_all[kScanThreads / 32][kZWarpScratch];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t Treg = 0;
-    persistent_units(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
+    persistent_units<int32_t, 8>(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
         zscan_unit<S, K1>(a, d, inst, unit, Treg, lane, wsm_all[warp], scratch_all[warp], stage_all[warp]);
     });
 }
@@ -549,7 +491,7 @@ __global__ void __launch_bounds__(kScanThreads, 6) zscan_one_kernel(const ScanAr
     __shared__ int32_t lin_all[kScanThreads / 32][S / 4 * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int32_t Treg = 0;
-    persistent_units(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
+    persistent_units<int32_t, 8>(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
         zscan_unit_one<S, K1>(a, d, inst, unit, Treg, lane, wsm_all[warp], wt_all[warp], gs_all[warp],
                               lin_all[warp]);
     });

@@ -714,8 +714,7 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
         }
     }
 
-    if (lane == 0)
-        atomicAdd(&st->scanned, 1ull << BL);
+
 
     if constexpr (Tr<T>::kFloat) {
         // Re-anchoring check: the walk ends at g = 2^(L-1); recompute those energies from the
@@ -944,8 +943,66 @@ __device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &
         }
     }
 
-    if (lane == 0)
-        atomicAdd(&st->scanned, 1ull << BL);
+
+}
+
+// Persistent work loop: a warp claims work units from the queue, kChunk at a time (the next claim
+// is made before the current units are scanned, hiding the atomic), and counts the states it
+// scanned locally, flushing the count when the instance changes and at exit.  Same-address
+// atomics on the queue and on a state counter cap the unit rate near 1.5e8 units/s on GB300,
+// which matters for kernels whose units take microseconds.
+template <class T, unsigned long long kChunk, class UnitFn>
+__device__ __forceinline__ void persistent_units(const ScanArgs &a, int lane, typename Tr<T>::TP &Treg,
+                                                 UnitFn &&unit_fn)
+{
+    int cur = -1;
+    unsigned long long done = 0;
+    unsigned long long next = lane == 0 ? atomicAdd(a.queue, kChunk) : 0ull;
+    for (;;) {
+        unsigned long long base = 0;
+        int stop = 0;
+        if (lane == 0) {
+            stop = *a.abort_flag != 0;
+            base = next;
+            if (!stop && base < a.total_items)
+                next = atomicAdd(a.queue, kChunk);
+        }
+        stop = __shfl_sync(kFull, stop, 0);
+        base = __shfl_sync(kFull, base, 0);
+        if (stop || base >= a.total_items)
+            break;
+        const unsigned long long end = base + kChunk < a.total_items ? base + kChunk : (unsigned long long)a.total_items;
+        for (unsigned long long item = base; item < end; ++item) {
+            int inst = 0;
+            if (a.n_inst > 1) {
+                int lo = 0, hi = a.n_inst;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (a.item_base[mid] <= item)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                inst = lo;
+            }
+            if (inst != cur) {
+                if (lane == 0 && done)
+                    atomicAdd(&a.state[cur].scanned, done);
+                done = 0;
+                cur = inst;
+                Treg = Tr<T>::thr_load(a.state + inst);
+            }
+            const Inst d = a.inst[inst];
+            if (d.small) {
+                small_unit<T>(a, d, inst, lane);  // counts its own states
+            } else {
+                unit_fn(d, inst, d.unit_begin + (item - a.item_base[inst]));
+                done += 1ull << (d.B + d.L);
+            }
+        }
+    }
+    if (lane == 0 && done)
+        atomicAdd(&a.state[cur].scanned, done);
 }
 
 template <class T, int S, int RC, bool K1, int MINB, int ADDM, int MINM>
@@ -958,48 +1015,14 @@ __global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     TC *stage = stage_all[warp];
     TP *wsm = wsm_all[warp];
-    int cur = -1;
     TP Treg = (TP)0;
-    // The next work item is claimed before the current one is scanned, hiding the atomic.
-    unsigned long long next = lane == 0 ? atomicAdd(a.queue, 1ull) : 0ull;
-    for (;;) {
-        unsigned long long item = 0;
-        int stop = 0;
-        if (lane == 0) {
-            stop = *a.abort_flag != 0;
-            item = next;
-            if (!stop && item < a.total_items)
-                next = atomicAdd(a.queue, 1ull);
-        }
-        stop = __shfl_sync(kFull, stop, 0);
-        item = __shfl_sync(kFull, item, 0);
-        if (stop || item >= a.total_items)
-            break;
-        int inst = 0;
-        if (a.n_inst > 1) {
-            int lo = 0, hi = a.n_inst;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (a.item_base[mid] <= item)
-                    lo = mid;
-                else
-                    hi = mid;
-            }
-            inst = lo;
-        }
-        if (inst != cur) {
-            cur = inst;
-            Treg = Tr<T>::thr_load(a.state + inst);
-        }
-        const Inst d = a.inst[inst];
-        const uint64_t off = item - a.item_base[inst];
-        if (d.small)
-            small_unit<T>(a, d, inst, lane);
-        else if constexpr (Tr<T>::kPack == 2)
-            scan_unit_packed<S, RC, K1, ADDM, MINM>(a, d, inst, d.unit_begin + off, Treg, lane, stage, wsm);
+    // units take 0.1-30 ms here: one per claim keeps the end of a launch balanced
+    persistent_units<T, 1>(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
+        if constexpr (Tr<T>::kPack == 2)
+            scan_unit_packed<S, RC, K1, ADDM, MINM>(a, d, inst, unit, Treg, lane, stage, wsm);
         else
-            scan_unit<T, S, RC, K1, ADDM, MINM>(a, d, inst, d.unit_begin + off, Treg, lane, stage, wsm);
-    }
+            scan_unit<T, S, RC, K1, ADDM, MINM>(a, d, inst, unit, Treg, lane, stage, wsm);
+    });
 }
 
 }  // namespace qubo
