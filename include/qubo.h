@@ -58,7 +58,8 @@ typedef enum {
     QUBO_TRUNCATED = 1,      /* warning: the tie set had more members than states_cap; the
                                 results are valid, n_ties is exact, out_states holds the
                                 states_cap smallest codes */
-    QUBO_ERR_ARG = -1,       /* bad argument: n<1, n>64, null pointer, bad dtype, topk, ... */
+    QUBO_ERR_ARG = -1,       /* bad argument: n<1, n>64, more than 2^63 states in one call (at
+                                n = 64 fix at least one bit), null pointer, bad dtype, topk, ... */
     QUBO_ERR_OVERFLOW = -2,  /* integer energies cannot be bounded by any supported accumulator */
     QUBO_ERR_CUDA = -3,      /* CUDA runtime error (no device, launch failure, ...) */
     QUBO_ERR_NOMEM = -4,     /* device or host allocation failed */
