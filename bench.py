@@ -39,7 +39,8 @@ PAPER_CONTEXT = "7.47e12 states/s, int16 energies, 1x H100 (paper Tab. 1); other
 PROFILE_JSON = os.path.join(ROOT, "profiles", "scan_kernel_counters.json")
 # arithmetic type of each accumulator the library reports (integer results are exact in all)
 ACC_DTYPE = {"i32": "int32", "i64": "int64", "f32": "f32", "f64": "f64", "i32f": "f32 (integer-valued)",
-             "i16p": "u16x2 (integer-valued, packed)", "i32z": "int32 (factored sparse scan)"}
+             "i16p": "u16x2 (integer-valued, packed)", "i32z": "int32 (factored sparse scan)",
+             "f32z": "f32 (factored sparse scan)"}
 
 
 def log(*a):
@@ -155,7 +156,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------------------------
 
 ACC_SOURCE = {"i32": ["scan_i32.cu"], "i64": ["scan_i64.cu"], "f32": ["scan_f32.cu"], "f64": ["scan_f64.cu"],
-              "i32f": ["scan_i32f.cu"], "i16p": ["scan_i16p.cu"], "i32z": ["scan_i32z.cu", "zscan.h"]}
+              "i32f": ["scan_i32f.cu"], "i16p": ["scan_i16p.cu"], "i32z": ["scan_sparse.cu", "zscan.h"], "f32z": ["scan_sparse.cu", "zscan.h"]}
 
 
 def kernel_source_hash(acc: str) -> str:
@@ -448,7 +449,7 @@ def main():
     # the packed scan holds two 16-bit columns in each 32-bit lane: twice the lane-ops per cycle
     halves = 2 if acc == "i16p" else 1
     ops_per_state = ALG_OPS_PER_STATE
-    if acc == "i32z":
+    if acc in ("i32z", "f32z"):
         # factored scan: one add and one min per column per block of 2^Z walk steps, and one
         # add and one min per walk step per 2^B columns (the block minima of E_L)
         Zr, Bs = infos[0]["zero_rows"], infos[0]["suffix_bits"]
@@ -460,7 +461,7 @@ def main():
             "traffic": None, "kernel": "scan_kernel",
             "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes" + (" x 2 packed 16-bit halves" if halves == 2 else "")
                           + f" x {clk_max:.0f} MHz; {ops_per_state:.4g} ops/state"
-                          + (" (add + min)" if acc != "i32z" else
+                          + (" (add + min)" if acc not in ("i32z", "f32z") else
                              f" (factored scan: 2/2^Z + 2/2^B, Z = {infos[0]['zero_rows']}, B = {infos[0]['suffix_bits']})")}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (halves * sms * LANES_PER_SM * clocks["sm_mhz"] * 1e-3)

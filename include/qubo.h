@@ -42,7 +42,9 @@ typedef enum { QUBO_I16 = 1, QUBO_I32 = 2, QUBO_F32 = 3, QUBO_F64 = 4 } qubo_dty
  * variables can be ordered so that at least 3 walked prefix variables have no coupling to any
  * suffix variable: the scan then factors those variables out of the column walk (the minimum
  * over their patterns separates from the minimum over the columns) and updates the columns
- * 2^Z times less often.  All give exact integer results, as QUBO_ACC_I32 does. */
+ * 2^Z times less often.  All give exact integer results, as QUBO_ACC_I32 does.
+ * QUBO_ACC_F32Z: the factored scan of a sparse float instance, in FP32 with the same FP64
+ * rescoring of every candidate as QUBO_ACC_F32. */
 typedef enum {
     QUBO_ACC_I32 = 1,
     QUBO_ACC_I64 = 2,
@@ -50,7 +52,8 @@ typedef enum {
     QUBO_ACC_F64 = 4,
     QUBO_ACC_I32F = 5,
     QUBO_ACC_I16P = 6,
-    QUBO_ACC_I32Z = 7
+    QUBO_ACC_I32Z = 7,
+    QUBO_ACC_F32Z = 8
 } qubo_acc;
 
 typedef enum {

@@ -19,7 +19,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libqubo.so")
 
 QUBO_I16, QUBO_I32, QUBO_F32, QUBO_F64 = 1, 2, 3, 4
-ACC_NAMES = {1: "i32", 2: "i64", 3: "f32", 4: "f64", 5: "i32f", 6: "i16p", 7: "i32z"}
+ACC_NAMES = {1: "i32", 2: "i64", 3: "f32", 4: "f64", 5: "i32f", 6: "i16p", 7: "i32z", 8: "f32z"}
 QUBO_OK, QUBO_TRUNCATED = 0, 1
 QUBO_ERR_ARG, QUBO_ERR_OVERFLOW, QUBO_ERR_CUDA = -1, -2, -3
 QUBO_ERR_NOMEM, QUBO_ERR_TIMEOUT, QUBO_ERR_INTERNAL = -4, -5, -6

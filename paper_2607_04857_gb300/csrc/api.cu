@@ -63,8 +63,9 @@ struct HostInst {
     double thr0 = 0.0;  // initial threshold (a bound on the K-th lowest energy of the range)
     int32_t clampC = 0; // ACC_I32F: threshold clamp
     int32_t col_lo = 0, col_hi = 0;  // ACC_I16P: proven range of every column value
-    int Z = 0;                  // ACC_I32Z: walked rows without suffix couplings
-    std::vector<uint8_t> perm;  // ACC_I32Z: caller's variable at each scan position
+    int Z = 0;                  // ACC_I32Z / ACC_F32Z: walked rows without suffix couplings
+    std::vector<uint8_t> perm;  // ACC_I32Z / ACC_F32Z: caller's variable at each scan position
+    bool no_factored = false;   // the factored FP32 scan used up its margin: plan the dense one
 };
 
 bool dtype_ok(qubo_dtype dt) { return dt == QUBO_I16 || dt == QUBO_I32 || dt == QUBO_F32 || dt == QUBO_F64; }
@@ -117,11 +118,13 @@ int prepare(const void *Q, int n, qubo_dtype dt, uint32_t flags, HostInst &h)
 }
 
 int acc_bytes(Acc a) { return (a == ACC_I64 || a == ACC_F64) ? 8 : 4; }
+bool acc_float(Acc a) { return a == ACC_F32 || a == ACC_F64 || a == ACC_F32Z; }
+bool acc_factored(Acc a) { return a == ACC_I32Z || a == ACC_F32Z; }
 
 // Suffix bits (log2 of the columns of one work unit) of an accumulator and kernel variant.
 int acc_suffix_bits(Acc a, int variant)
 {
-    if (a == ACC_I32Z)
+    if (acc_factored(a))
         return zscan_suffix_bits(variant);
     return a == ACC_I16P ? packed_suffix_bits(variant) : suffix_bits(acc_bytes(a), variant);
 }
@@ -129,7 +132,7 @@ int acc_suffix_bits(Acc a, int variant)
 // Columns held by one thread (two per word in the packed scan).
 int acc_cols_per_thread(Acc a, int variant)
 {
-    if (a == ACC_I32Z)
+    if (acc_factored(a))
         return kZCols[(variant >= 0 && variant < kZVariants) ? variant : 0];
     return a == ACC_I16P ? 2 * packed_words(variant) : cols_per_thread(acc_bytes(a), variant);
 }
@@ -138,7 +141,7 @@ int acc_cols_per_thread(Acc a, int variant)
 int reg_rows_of(Acc a, int variant)
 {
     const int v = variant >= 0 && variant < kScanVariants ? variant : 0;
-    if (a == ACC_I32Z)
+    if (acc_factored(a))
         return 2;  // the factored scan needs at least 3 walked rows
     return a == ACC_I16P ? kPackedRegRows[v] : kVariantRegRows[acc_bytes(a) == 4 ? v : 0];
 }
@@ -180,9 +183,9 @@ int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bi
     else if (walk_bits > 0)
         L = walk_bits;
     else
-        L = std::max(rc + 1, std::min(h.acc == ACC_F32   ? kFloatMaxWalkBits
-                                      : h.acc == ACC_I32Z ? kZMaxWalkBits
-                                                          : kDefaultMaxWalkBits,
+        L = std::max(rc + 1, std::min(h.acc == ACC_F32          ? kFloatMaxWalkBits
+                                      : acc_factored(h.acc) ? kZMaxWalkBits
+                                                            : kDefaultMaxWalkBits,
                                       free_bits - h.B - kTargetUnitsLog2));
     const int k = n - h.B - L;
     if (L < rc + 1 || L > kMaxWalkBits || k < fix_bits || k > 63)
@@ -316,7 +319,10 @@ int zero_rows_search(HostInst &h)
     const int n = h.n, nf = n - h.fix_bits, B = h.B, L = h.L;
     if (h.small || nf < B + L)
         return 0;
-    auto adj = [&](int a, int b) { return a != b && h.Ui[(size_t)std::min(a, b) * n + std::max(a, b)] != 0; };
+    auto adj = [&](int a, int b) {
+        const size_t o = (size_t)std::min(a, b) * n + std::max(a, b);
+        return a != b && (h.is_float ? h.Uf[o] != 0.0 : h.Ui[o] != 0);
+    };
     std::vector<int> deg(n, 0);
     for (int a = 0; a < n; ++a)
         for (int b = 0; b < n; ++b)
@@ -388,42 +394,49 @@ bool i16p_allowed()
 // Accumulator, kernel variant and plan of one run.  Integer instances scan in packed 16-bit lanes
 // or else in FP32 lanes when the plan keeps every value exact (and the plain form was not asked
 // for), else in int32.
+// Plan the factored scan (accumulator acc, ACC_I32Z or ACC_F32Z) when at least 3 walked rows can be
+// factored out; true when planned.
+bool plan_factored(HostInst &h, Acc acc, int fix_bits, uint64_t fix_value, int split_k, int walk_bits)
+{
+    // QUBO_ZSCAN_VARIANT pins the factored scan's column count (variant index)
+    const char *zenv = std::getenv("QUBO_ZSCAN_VARIANT");
+    const int z0 = zenv ? std::max(0, std::min(kZVariants - 1, std::atoi(zenv))) : 0;
+    const int z1 = zenv ? z0 + 1 : kZVariants - 1;  // variant 3 is chosen below, not searched
+    for (int zv = z0; zv < z1; ++zv) {
+        h.acc = acc;
+        h.variant = zv;
+        if (plan(h, fix_bits, fix_value, split_k, walk_bits) != QUBO_OK || (h.Z = zero_rows_search(h)) < 3)
+            continue;
+        if (h.L - h.Z > kZMaxBlocksLog2) {
+            // too many blocks for the per-warp table: a shorter walk, if the plan is ours
+            if (split_k > 0 || walk_bits > 0 || plan(h, fix_bits, fix_value, 0, h.Z + kZMaxBlocksLog2) != QUBO_OK ||
+                (h.Z = zero_rows_search(h)) < 3 || h.L - h.Z > kZMaxBlocksLog2)
+                continue;
+        }
+        // every walked row factored: one block per unit, the kernel without column registers
+        if (!zenv && h.variant == 0 && h.Z == h.L && h.Z >= 7)
+            h.variant = 3;
+        return true;
+    }
+    h.Z = 0;
+    h.perm.clear();
+    return false;
+}
+
 int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bits, int variant_req,
              uint32_t flags)
 {
+    if ((h.acc == ACC_F32 || h.acc == ACC_F32Z) && !(flags & QUBO_FLAG_PLAIN)) {
+        if (i32z_allowed() && !h.no_factored && plan_factored(h, ACC_F32Z, fix_bits, fix_value, split_k, walk_bits))
+            return QUBO_OK;
+        h.acc = ACC_F32;
+    }
     if ((h.acc == ACC_I32 || h.acc == ACC_I32F || h.acc == ACC_I16P || h.acc == ACC_I32Z) &&
         !(flags & QUBO_FLAG_PLAIN)) {
         Acc chosen = ACC_I32;
         // sparse instances: at least 3 walked rows factored out (8x fewer column updates)
-        if (i32z_allowed()) {
-            // QUBO_ZSCAN_VARIANT pins the factored scan's column count (variant index)
-            const char *zenv = std::getenv("QUBO_ZSCAN_VARIANT");
-            const int z0 = zenv ? std::max(0, std::min(kZVariants - 1, std::atoi(zenv))) : 0;
-            const int z1 = zenv ? z0 + 1 : kZVariants;
-            for (int zv = z0; zv < z1 && chosen == ACC_I32; ++zv) {
-                h.acc = ACC_I32Z;
-                h.variant = zv;
-                if (plan(h, fix_bits, fix_value, split_k, walk_bits) != QUBO_OK || (h.Z = zero_rows_search(h)) < 3)
-                    continue;
-                if (h.L - h.Z > kZMaxBlocksLog2) {
-                    // too many blocks for the per-warp table: a shorter walk, if the plan is ours
-                    if (split_k > 0 || walk_bits > 0 ||
-                        plan(h, fix_bits, fix_value, 0, h.Z + kZMaxBlocksLog2) != QUBO_OK ||
-                        (h.Z = zero_rows_search(h)) < 3 || h.L - h.Z > kZMaxBlocksLog2)
-                        continue;
-                }
-                chosen = ACC_I32Z;
-            }
-            if (chosen == ACC_I32Z) {
-                h.acc = ACC_I32Z;
-                // every walked row factored: one block per unit, the kernel without column registers
-                if (!zenv && h.variant == 0 && h.Z == h.L && h.Z >= 7)
-                    h.variant = 3;
-                return QUBO_OK;
-            }
-            h.Z = 0;
-            h.perm.clear();
-        }
+        if (i32z_allowed() && plan_factored(h, ACC_I32Z, fix_bits, fix_value, split_k, walk_bits))
+            return QUBO_OK;
         if (i16p_allowed()) {
             h.acc = ACC_I16P;
             h.variant = pick_variant(h.acc, variant_req);
@@ -560,7 +573,8 @@ unsigned long long encode_thr(Acc acc, double t)
     case ACC_I16P:
     case ACC_I32Z: return (unsigned long long)(uint32_t)(int32_t)t;
     case ACC_I64: return (unsigned long long)(int64_t)t;
-    case ACC_F32: {
+    case ACC_F32:
+    case ACC_F32Z: {
         float f = (float)t;
         if ((double)f < t)
             f = std::nextafter(f, INFINITY);
@@ -579,7 +593,8 @@ unsigned long long encode_max(Acc acc)
     case ACC_I16P:
     case ACC_I32Z: return (unsigned long long)(uint32_t)INT32_MAX;
     case ACC_I64: return (unsigned long long)INT64_MAX;
-    case ACC_F32: return ord32h(INFINITY);
+    case ACC_F32:
+    case ACC_F32Z: return ord32h(INFINITY);
     case ACC_F64: return ord64h(INFINITY);
     }
     return 0;
@@ -961,7 +976,7 @@ int job_layout(Job &j)
             j.off_W[i] = o;
             o = align_up(o + (size_t)eb * nn, 256);
         }
-        if (j.acc == ACC_I32Z && !h.small) {  // scan order of the variables
+        if (acc_factored(j.acc) && !h.small) {  // scan order of the variables
             j.off_perm[i] = o;
             o = align_up(o + 64, 256);
         }
@@ -1039,13 +1054,17 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
         if (h.is_float) {
             double *W64 = (double *)(up + j.off_W64[i]);
             double *U64 = (double *)(up + j.off_U64[i]);
+            // the factored scan's tables and fields follow its scan order; the rescore reads the
+            // caller's order (records carry the caller's codes)
+            const bool permuted = j.acc == ACC_F32Z && !h.small;
             for (int a = 0; a < h.n; ++a)
                 for (int b = 0; b < h.n; ++b) {
-                    const int lo = std::min(a, b), hi2 = std::max(a, b);
+                    const int va = permuted ? h.perm[a] : a, vb = permuted ? h.perm[b] : b;
+                    const int lo = std::min(va, vb), hi2 = std::max(va, vb);
                     const double w = h.Uf[(size_t)lo * h.n + hi2];
                     W64[(size_t)a * h.n + b] = w;
                     U64[(size_t)a * h.n + b] = h.Uf[(size_t)a * h.n + b];
-                    if (j.acc == ACC_F32)
+                    if (j.acc == ACC_F32 || j.acc == ACC_F32Z)
                         ((float *)(up + j.off_W[i]))[(size_t)a * h.n + b] = (float)w;
                     else
                         ((double *)(up + j.off_W[i]))[(size_t)a * h.n + b] = w;
@@ -1053,6 +1072,8 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
             d.W = dev + j.off_W[i];
             d.W64 = (const double *)(dev + j.off_W64[i]);
             d.U64 = (const double *)(dev + j.off_U64[i]);
+            if (permuted)
+                std::memcpy(up + j.off_perm[i], h.perm.data(), h.n);
         } else {
             if (j.acc == ACC_I32Z && !h.small) {
                 // the couplings in scan order: W[a][b] couples the variables perm[a] and perm[b]
@@ -1083,7 +1104,7 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
         d.EL = h.small ? nullptr : dev + j.off_EL[i];
         d.thr0 = 0;
         d.Z = h.Z;
-        d.perm = (j.acc == ACC_I32Z && !h.small) ? (const uint8_t *)(dev + j.off_perm[i]) : nullptr;
+        d.perm = (acc_factored(j.acc) && !h.small) ? (const uint8_t *)(dev + j.off_perm[i]) : nullptr;
         hi[i] = d;
         InstState s{};
         s.thr = encode_thr(j.acc, h.thr0);
@@ -1147,9 +1168,9 @@ int job_enqueue_scan(Workspace &ws, Job &j, const void *state_init = nullptr)
     a.rec_cap = j.rec_cap;
     a.nrec = (unsigned long long *)(dev + j.off_ctr) + 1;
     a.abort_flag = ws.d_abort;
-    a.margin = (j.acc == ACC_F32 || j.acc == ACC_F64) ? j.margin : 0.0;
+    a.margin = acc_float(j.acc) ? j.margin : 0.0;
     if (j.window >= 0.0)  // record everything within the window of the running minimum
-        a.margin += (j.acc == ACC_F32 || j.acc == ACC_F64) ? j.window : std::floor(j.window);
+        a.margin += acc_float(j.acc) ? j.window : std::floor(j.window);
     a.zero = 0;
     CK(launch_scan(j.acc, a, j.blocks, j.variant, s));
     CK(record_event(ws.ev[1], s));
@@ -1228,7 +1249,7 @@ int job_enqueue_finalize(Workspace &ws, Job &j, unsigned long long max_count, un
     char *dev = (char *)ws.d_arena;
     cudaStream_t s = j.stream;
     const bool batched = ni > 1;
-    const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
+    const bool is_float = acc_float(j.acc);
     const unsigned long long *d_nrec = (const unsigned long long *)(dev + j.off_ctr) + 1;
     if (is_float) {
         CK(launch_rescore((const Inst *)(dev + j.off_inst), (InstState *)(dev + j.off_state), ws.d_rec, d_nrec,
@@ -1261,7 +1282,7 @@ Part part_from(const Down &d, const Job &j, int i);
 void job_unpack(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seconds)
 {
     const int ni = (int)j.insts.size();
-    const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
+    const bool is_float = acc_float(j.acc);
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ws.ev[0], ws.ev[2]) == cudaSuccess && gpu_seconds)
         *gpu_seconds = ms * 1e-3;
@@ -1276,7 +1297,7 @@ void job_unpack(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_sec
 // Per-instance result of a finished job, read from the download staging buffer.
 Part part_from(const Down &d, const Job &j, int i)
 {
-    const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
+    const bool is_float = acc_float(j.acc);
     Part p;
     {
         const ResOut &r = d.res[i];
@@ -1330,7 +1351,7 @@ int job_finish(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seco
     job_unpack(ws, j, parts, gpu_seconds);
     if (j.window >= 0.0 && !parts.empty() && parts[0].has) {
         Part &p = parts[0];
-        const bool fl = j.acc == ACC_F32 || j.acc == ACC_F64;
+        const bool fl = acc_float(j.acc);
         const double lim = p.min_f + j.window;
         for (const Rec &r : sorted) {
             const double e = fl ? bits_to_double(r.e) : (double)r.e;
@@ -1418,13 +1439,15 @@ int solve_range(Workspace &ws, HostInst &h, int fix_bits, uint64_t fix_value, co
     return QUBO_OK;
 }
 
-// Float scans: the FP32 candidate margin must exceed twice the drift measured at re-anchoring
-// (plus rounding of the threshold arithmetic); otherwise the instance is rescanned in FP64.
+// FP32 scans: the candidate margin must cover twice the measured drift plus the rounding of the
+// per-step threshold arithmetic (a few FP32 operations on values bounded by beta; the factored
+// scan's E_L plus up to 14 zero-row couplings, more).  Otherwise the caller rescans with a
+// shorter walk, the dense FP32 scan, or FP64.
 bool float_margin_ok(const HostInst &h, const Part &p, double margin)
 {
-    if (h.acc != ACC_F32)
+    if (h.acc != ACC_F32 && h.acc != ACC_F32Z)
         return true;
-    const double slack = 8.0 * std::ldexp(1.0, -24) * (1.0 + h.beta);
+    const double slack = (h.acc == ACC_F32Z ? 32.0 : 8.0) * std::ldexp(1.0, -24) * (1.0 + h.beta);
     return 2.0 * p.drift + slack < margin;
 }
 
@@ -1524,7 +1547,11 @@ int solve_one(Workspace &ws, HostInst &h, const qubo_options &o, size_t states_c
     // FP32 drift above the margin's budget: shorten the anchoring period (the walk), and as a
     // last resort rescan in FP64.
     while (!float_margin_ok(h, p, c.margin)) {
-        if (h.acc == ACC_F32 && !h.small && h.L > variant_reg_rows(h) + 1 && c.split_k <= 0) {
+        if (h.acc == ACC_F32Z) {  // the dense FP32 scan next
+            h.no_factored = true;
+            h.acc = ACC_F32;
+            c.walk_bits = o.walk_bits;
+        } else if (h.acc == ACC_F32 && !h.small && h.L > variant_reg_rows(h) + 1 && c.split_k <= 0) {
             c.walk_bits = std::max(variant_reg_rows(h) + 1, h.L - 2);
         } else {
             h.acc = ACC_F64;
@@ -1559,7 +1586,7 @@ void fill_plan_info(const HostInst &h, const SolveStats &stats, double t0, qubo_
     info->walk_bits = h.L;
     info->suffix_bits = h.small ? 0 : h.B;
     info->cols_per_thread = h.small ? 0 : acc_cols_per_thread(h.acc, h.variant);
-    info->zero_rows = h.acc == ACC_I32Z ? h.Z : 0;
+    info->zero_rows = acc_factored(h.acc) ? h.Z : 0;
     info->threads = kScanThreads;
     info->blocks = stats.blocks;
     info->passes = stats.passes;
@@ -2469,7 +2496,7 @@ int qubo_batch_fetch(qubo_batch *b, void *out_min, uint64_t *out_states, uint64_
     }
     // the graph's launches: the same kernels a direct run makes, with every sort stage present
     {
-        const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
+        const bool is_float = acc_float(j.acc);
         unsigned long long P = 1;
         while (P < j.rec_cap)
             P <<= 1;
@@ -2485,7 +2512,7 @@ int qubo_batch_fetch(qubo_batch *b, void *out_min, uint64_t *out_states, uint64_
     if (j.aborted)
         return QUBO_ERR_TIMEOUT;
     const Down d = down_view(b->ws, j);
-    const bool is_float = j.acc == ACC_F32 || j.acc == ACC_F64;
+    const bool is_float = acc_float(j.acc);
     SolveStats stats;
     stats.add(j, gs);
     int worst = QUBO_OK;

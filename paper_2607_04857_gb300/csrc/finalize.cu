@@ -17,6 +17,7 @@ cudaError_t launch_tables(Acc acc, const Inst *d_inst, int n_inst, int max_entri
     case ACC_I32F: return launch_tables_t<i32f>(d_inst, n_inst, max_entries, s);
     case ACC_I16P: return launch_tables_t<i16p>(d_inst, n_inst, max_entries, s);
     case ACC_I32Z: return launch_tables_t<int32_t>(d_inst, n_inst, max_entries, s);
+    case ACC_F32Z: return launch_tables_t<float>(d_inst, n_inst, max_entries, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -30,7 +31,8 @@ cudaError_t launch_scan(Acc acc, const ScanArgs &a, int blocks, int variant, cud
     case ACC_F64: return launch_scan_t<double>(a, blocks, variant, s);
     case ACC_I32F: return launch_scan_t<i32f>(a, blocks, variant, s);
     case ACC_I16P: return launch_scan_t<i16p>(a, blocks, variant, s);
-    case ACC_I32Z: return launch_zscan(a, blocks, variant, s);
+    case ACC_I32Z: return launch_zscan(a, blocks, variant, false, s);
+    case ACC_F32Z: return launch_zscan(a, blocks, variant, true, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -44,7 +46,8 @@ int scan_blocks_per_sm(Acc acc, bool k1, int variant)
     case ACC_F64: return scan_blocks_per_sm_t<double>(k1, variant);
     case ACC_I32F: return scan_blocks_per_sm_t<i32f>(k1, variant);
     case ACC_I16P: return scan_blocks_per_sm_t<i16p>(k1, variant);
-    case ACC_I32Z: return zscan_blocks_per_sm(k1, variant);
+    case ACC_I32Z: return zscan_blocks_per_sm(k1, variant, false);
+    case ACC_F32Z: return zscan_blocks_per_sm(k1, variant, true);
     }
     return -1;
 }

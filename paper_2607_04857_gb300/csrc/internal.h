@@ -10,9 +10,18 @@ namespace qubo {
 
 // ACC_I32F: integer energies scanned exactly in FP32 lanes (partial sums below 2^24).
 // ACC_I16P: integer energies whose column values fit 16 bits, two columns per 32-bit word.
-// ACC_I32Z: int32 energies, sparse instances: walked rows without couplings to the suffix
-// variables are factored out of the column walk (zscan_kernel).
-enum Acc : int32_t { ACC_I32 = 1, ACC_I64 = 2, ACC_F32 = 3, ACC_F64 = 4, ACC_I32F = 5, ACC_I16P = 6, ACC_I32Z = 7 };
+// ACC_I32Z / ACC_F32Z: int32 / FP32 energies of sparse instances: walked rows without couplings
+// to the suffix variables are factored out of the column walk (scan_sparse.cu).
+enum Acc : int32_t {
+    ACC_I32 = 1,
+    ACC_I64 = 2,
+    ACC_F32 = 3,
+    ACC_F64 = 4,
+    ACC_I32F = 5,
+    ACC_I16P = 6,
+    ACC_I32Z = 7,
+    ACC_F32Z = 8
+};
 
 // Walked prefix rows kept in registers by the scan kernel (the largest of the compiled
 // variants); the inner loop is unrolled over 2^(RC+1) Gray steps so that every register-row
@@ -150,8 +159,8 @@ cudaError_t launch_scan_t(const ScanArgs &a, int blocks, int variant, cudaStream
 template <class T>
 int scan_blocks_per_sm_t(bool k1, int variant);
 
-cudaError_t launch_zscan(const ScanArgs &a, int blocks, int variant, cudaStream_t s);
-int zscan_blocks_per_sm(bool k1, int variant);
+cudaError_t launch_zscan(const ScanArgs &a, int blocks, int variant, bool is_float, cudaStream_t s);
+int zscan_blocks_per_sm(bool k1, int variant, bool is_float);
 
 // ---- dispatch and finalize (finalize.cu) -----------------------------------------------------
 cudaError_t launch_tables(Acc acc, const Inst *d_inst, int n_inst, int max_entries, cudaStream_t s);

@@ -1,4 +1,4 @@
-// Factored scan of sparse integer instances (int32 energies).
+// Factored scan of sparse instances (int32 energies, or FP32 energies with FP64 rescoring).
 //
 // The host reorders the variables (Sec. 2.4 permutation invariance) so that the first Z walked
 // rows have no coupling to any suffix variable.  Their table rows M_r are then zero: flipping
@@ -30,48 +30,58 @@ __device__ __forceinline__ uint64_t unpermute(uint64_t c, const uint8_t *perm)
     return o;
 }
 
+template <class X>
+__device__ __forceinline__ X zbig();
+template <>
+__device__ __forceinline__ int32_t zbig<int32_t>() { return INT32_MAX; }
+template <>
+__device__ __forceinline__ float zbig<float>() { return __int_as_float(0x7f800000); }
+__device__ __forceinline__ int32_t emax(int32_t a, int32_t b) { return max(a, b); }
+__device__ __forceinline__ float emax(float a, float b) { return fmaxf(a, b); }
+
 // Per-warp scratch: the (parity, t) table of zero-row sums (at most 2^(16-4) entries would be
 // needed for 16 zero rows; the host keeps Z <= kZMaxRows) and the block minima.
 constexpr int kZTableEntries = 1 << (kZMaxRows - 4);
 constexpr int kZWarpScratch = 1 << kZMaxBlocksLog2;
 
 // Sum of the couplings w_r of the zero rows r set in the pattern m (slow path only).
-__device__ __forceinline__ int32_t zero_row_sum(int m, const int32_t *wsm, int Z)
+template <class X>
+__device__ __forceinline__ X zero_row_sum(int m, const X *wsm, int Z)
 {
-    int32_t s = 0;
+    X s = 0;
     for (int r = 0; r < Z; ++r)
         if ((m >> r) & 1)
             s += wsm[r];
     return s;
 }
 
-template <int S, bool K1>
-__device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t unit, int32_t &Treg, int lane,
-                           int32_t *wsm, int32_t *scratch, int32_t *stage)
+template <class T, int S, bool K1>
+__device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t unit, typename Tr<T>::TP &Treg,
+                           int lane, typename Tr<T>::TC *wsm, typename Tr<T>::TC *scratch, typename Tr<T>::TC *stage)
 {
-    using T = int32_t;
+    using X = typename Tr<T>::TC;
     constexpr int V = 4, G = S / V, LOGG = ilog2c(G);
     constexpr int B = 2 + 5 + LOGG;
     constexpr int NB = 1 << B;
     const int n = d.n, L = d.L, k = d.k, BL = B + L, Z = d.Z;
     const int nz = 1 << Z, nblk = 1 << (L - Z);
     InstState *st = a.state + inst;
-    const int32_t *W = (const int32_t *)d.W;
+    const X *W = unit_matrix<T>(d);
 
-    int32_t f0, cx;
+    X f0, cx;
     unit_fields<T>(W, n, k, BL, unit, lane, f0, cx);
     __syncwarp();
     if (lane >= B && lane < BL)
         wsm[lane - B] = f0;
     __syncwarp();
-    int32_t lin_t, lin_e[V], lin_g[G];
-    column_fields<int32_t, V, G>(f0, lane, lin_t, lin_e, lin_g);
-    const int32_t *Es = (const int32_t *)d.Es;
-    int32_t E[S];
+    X lin_t, lin_e[V], lin_g[G];
+    column_fields<X, V, G>(f0, lane, lin_t, lin_e, lin_g);
+    const X *Es = (const X *)d.Es;
+    X E[S];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        int32_t ev[V];
-        vload<int32_t>(Es + (g * 32 + lane) * V, ev);
+        X ev[V];
+        vload<X>(Es + (g * 32 + lane) * V, ev);
 #pragma unroll
         for (int e = 0; e < V; ++e)
             E[g * V + e] = ev[e] + lin_e[e] + lin_t + lin_g[g];
@@ -83,71 +93,71 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
     // 5..Z-1 from t and, at the top, the block's parity.  So a lane adds its own part after its
     // running minimum, and the t part comes from a small per-warp table (a broadcast read).
     // A block's minimum is then reduced over the lanes that hold it.
-    const int32_t *EL = (const int32_t *)d.EL;
-    int32_t *wt = stage;                         // Z >= 5: 2^(Z-4) entries (parity, t); the slow
+    const X *EL = (const X *)d.EL;
+    X *wt = stage;                         // Z >= 5: 2^(Z-4) entries (parity, t); the slow
                                                  // path's staging reuses it after the table
-    int32_t *mel = scratch;                      // per block: min_i e(i)
+    X *mel = scratch;                      // per block: min_i e(i)
     if (Z >= 7) {
         // Lanes take 4 consecutive steps each (one 16-byte E_L read), a warp iteration t covers
         // 128 steps: step bits 0-1 are the element k, bits 2-6 the lane, bits 7..Z-1 t, bit Z
         // the block's parity.  Gray bits g_0..g_5 follow from (k, lane), g_6 from the lane's top
         // bit and bit 7 of the step, g_7..g_{Z-1} from (parity, t) through a per-warp table.
         const int zt = Z - 7;
-        int32_t *gs = mel;
+        X *gs = mel;
         if (lane == 0)
             gs[0] = 0;
         __syncwarp();
         for (int b = 0; b < zt; ++b) {
-            const int32_t wb = wsm[7 + b];
+            const X wb = wsm[7 + b];
             for (int m = lane; m < (1 << b); m += 32)
                 gs[m + (1 << b)] = gs[m] + wb;
             __syncwarp();
         }
         for (int e = lane; e < (2 << zt); e += 32)
             wt[e] = gs[(e ^ (e >> 1)) & ((1 << zt) - 1)];
-        int32_t a = 0;  // g_2..g_5 from the lane bits
+        X a = 0;  // g_2..g_5 from the lane bits
         for (int r = 0; r < 4; ++r)
             if (((lane >> r) ^ (lane >> (r + 1))) & 1)
                 a += wsm[2 + r];
         const bool l0 = lane & 1, l4 = (lane >> 4) & 1;
-        int32_t ae[4], ao[4];  // per element k, for bit 7 of the step = 0 (ae) and 1 (ao)
+        X ae[4], ao[4];  // per element k, for bit 7 of the step = 0 (ae) and 1 (ao)
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             const bool g0 = (k ^ (k >> 1)) & 1, g1 = ((k >> 1) & 1) ^ l0;
-            const int32_t base = a + (g0 ? wsm[0] : 0) + (g1 ? wsm[1] : 0);
+            const X base = a + (g0 ? wsm[0] : 0) + (g1 ? wsm[1] : 0);
             ae[k] = base + (l4 ? wsm[6] : 0);
             ao[k] = base + (l4 ? 0 : wsm[6]);
         }
         __syncwarp();
         const int nt = 1 << zt;
         for (int kb = 0; kb < nblk; ++kb) {
-            const int32_t *e = EL + (kb << Z) + 4 * lane;
-            const int32_t *w = wt + ((kb & 1) << zt);
-            int32_t acc;
+            const X *e = EL + (kb << Z) + 4 * lane;
+            const X *w = wt + ((kb & 1) << zt);
+            X acc;
             if (nt == 1) {  // Z == 7: bit 7 of the step index is the block's parity
-                int32_t v[4], ak[4];
-                vload<int32_t>(e, v);
+                X v[4], ak[4];
+                vload<X>(e, v);
 #pragma unroll
                 for (int k = 0; k < 4; ++k)
                     ak[k] = (kb & 1) ? ao[k] : ae[k];
-                acc = min(__vimin3_s32(v[0] + ak[0], v[1] + ak[1], v[2] + ak[2]), v[3] + ak[3]);
+                acc = emin(emin3(v[0] + ak[0], v[1] + ak[1], v[2] + ak[2]), v[3] + ak[3]);
             } else {
-                int32_t me = INT32_MAX, mo = INT32_MAX;
+                X me = zbig<X>(), mo = zbig<X>();
 #pragma unroll 2
                 for (int t = 0; t < nt; t += 2) {
-                    int32_t v[4], u[4];
-                    vload<int32_t>(e + (t << 7), v);
-                    vload<int32_t>(e + ((t + 1) << 7), u);
-                    const int32_t mv = min(__vimin3_s32(v[0] + ae[0], v[1] + ae[1], v[2] + ae[2]), v[3] + ae[3]);
-                    const int32_t mu2 = min(__vimin3_s32(u[0] + ao[0], u[1] + ao[1], u[2] + ao[2]), u[3] + ao[3]);
-                    me = min(me, mv + w[t]);
-                    mo = min(mo, mu2 + w[t + 1]);
+                    X v[4], u[4];
+                    vload<X>(e + (t << 7), v);
+                    vload<X>(e + ((t + 1) << 7), u);
+                    const X mv = emin(emin3(v[0] + ae[0], v[1] + ae[1], v[2] + ae[2]), v[3] + ae[3]);
+                    const X mu2 = emin(emin3(u[0] + ao[0], u[1] + ao[1], u[2] + ao[2]), u[3] + ao[3]);
+                    me = emin(me, mv + w[t]);
+                    mo = emin(mo, mu2 + w[t + 1]);
                 }
-                acc = min(me, mo);
+                acc = emin(me, mo);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
-                acc = min(acc, __shfl_xor_sync(kFull, acc, o));
+                acc = emin(acc, __shfl_xor_sync(kFull, acc, o));
             if (lane == (kb & 31))
                 mel[kb] = acc;
         }
@@ -156,61 +166,61 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
         // subset sums of w_5..w_{Z-1} by doubling (mel is free until the block minima), then
         // wt[e] for e = (parity << zt) | t, the bits 5..Z of the step index: the Gray bits
         // g_5..g_{Z-1} of the step are the Gray code of e cut to zt bits.
-        int32_t *gs = mel;
+        X *gs = mel;
         if (lane == 0)
             gs[0] = 0;
         __syncwarp();
         for (int b = 0; b < zt; ++b) {
-            const int32_t wb = wsm[5 + b];
+            const X wb = wsm[5 + b];
             for (int m = lane; m < (1 << b); m += 32)
                 gs[m + (1 << b)] = gs[m] + wb;
             __syncwarp();
         }
         for (int e = lane; e < (2 << zt); e += 32)
             wt[e] = gs[(e ^ (e >> 1)) & ((1 << zt) - 1)];
-        int32_t a = 0;
+        X a = 0;
         for (int r = 0; r < 4; ++r)
             if (((lane >> r) ^ (lane >> (r + 1))) & 1)
                 a += wsm[r];
         const bool l4 = (lane >> 4) & 1;
-        const int32_t a0 = a + (l4 ? wsm[4] : 0);  // even t: bit 5 of the step index is 0
-        const int32_t a1 = a + (l4 ? 0 : wsm[4]);  // odd t
+        const X a0 = a + (l4 ? wsm[4] : 0);  // even t: bit 5 of the step index is 0
+        const X a1 = a + (l4 ? 0 : wsm[4]);  // odd t
         __syncwarp();
         const int nt = 1 << zt;
 #pragma unroll 2
         for (int kb = 0; kb < nblk; ++kb) {
-            const int32_t *e = EL + (kb << Z) + lane;
-            const int32_t *w = wt + ((kb & 1) << zt);
-            int32_t acc;
+            const X *e = EL + (kb << Z) + lane;
+            const X *w = wt + ((kb & 1) << zt);
+            X acc;
             if (nt == 1) {  // Z == 5: bit 5 of the step index is the block's parity
                 acc = __ldg(e) + ((kb & 1) ? a1 : a0);
             } else {
-                int32_t ae = INT32_MAX, ao = INT32_MAX;
+                X ae = zbig<X>(), ao = zbig<X>();
 #pragma unroll 4
                 for (int t = 0; t < nt; t += 2) {
-                    ae = min(ae, __ldg(e + (t << 5)) + w[t]);
-                    ao = min(ao, __ldg(e + ((t + 1) << 5)) + w[t + 1]);
+                    ae = emin(ae, __ldg(e + (t << 5)) + w[t]);
+                    ao = emin(ao, __ldg(e + ((t + 1) << 5)) + w[t + 1]);
                 }
-                acc = min(ae + a0, ao + a1);
+                acc = emin(ae + a0, ao + a1);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
-                acc = min(acc, __shfl_xor_sync(kFull, acc, o));
+                acc = emin(acc, __shfl_xor_sync(kFull, acc, o));
             if (lane == (kb & 31))
                 mel[kb] = acc;
         }
     } else {
         // blocks shorter than a warp: the whole zero-row sum of a step follows from its lane
-        int32_t wl = 0;
+        X wl = 0;
         for (int r = 0; r < Z; ++r)
             if (((lane >> r) ^ (lane >> (r + 1))) & 1)
                 wl += wsm[r];
         const int total = 1 << L, iters = (total + 31) >> 5;
         for (int t = 0; t < iters; ++t) {
             const int i = (t << 5) + lane;
-            int32_t acc = i < total ? __ldg(EL + i) + wl : INT32_MAX;
+            X acc = i < total ? __ldg(EL + i) + wl : zbig<X>();
             for (int o = 1; o < nz; o <<= 1)
-                acc = min(acc, __shfl_xor_sync(kFull, acc, o));
+                acc = emin(acc, __shfl_xor_sync(kFull, acc, o));
             if (i < total && (lane & (nz - 1)) == 0)
                 mel[i >> Z] = acc;
         }
@@ -218,12 +228,12 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
     __syncwarp();
 
     {
-        const int32_t tg = Tr<T>::thr_load(st);
-        Treg = K1 ? min(Treg, tg) : tg;
+        const X tg = Tr<T>::thr_load(st);
+        Treg = K1 ? emin(Treg, tg) : tg;
     }
-    const int32_t mu = (int32_t)a.margin;
-    int32_t P = cx;  // c(x_f) + couplings of the set walked rows >= Z to the fixed variables
-    const int32_t *Mt = (const int32_t *)d.M;
+    const X mu = (X)a.margin;
+    X P = cx;  // c(x_f) + couplings of the set walked rows >= Z to the fixed variables
+    const X *Mt = (const X *)d.M;
     const uint64_t cbase = unit << BL;
 
     for (int kb = 0; kb < nblk; ++kb) {
@@ -231,18 +241,18 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
             const int kk = __ffs(kb) - 1;
             const int r = Z + kk;
             const bool neg = (kb >> (kk + 1)) & 1;
-            const int32_t *row = Mt + (size_t)r * NB;
+            const X *row = Mt + (size_t)r * NB;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-                int32_t mv[V];
-                vload<int32_t>(row + (g * 32 + lane) * V, mv);
+                X mv[V];
+                vload<X>(row + (g * 32 + lane) * V, mv);
 #pragma unroll
                 for (int e = 0; e < V; ++e)
                     E[g * V + e] = neg ? E[g * V + e] - mv[e] : E[g * V + e] + mv[e];
             }
             P = neg ? P - wsm[r] : P + wsm[r];
         }
-        const int32_t cm = tree_min<int32_t, 3, S>(E);
+        const X cm = tree_min<X, 3, S>(E);
         if (__any_sync(kFull, cm + mel[kb] <= Treg + mu - P)) {
             // rare: the warp enumerates the block together.  Lanes take consecutive walk steps
             // (coalesced E_L reads); a step whose e(i) plus the smallest column of any lane
@@ -251,17 +261,17 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
 #pragma unroll
             for (int q = 0; q < S; ++q)
                 stage[q * 32 + lane] = E[q];
-            int32_t cmin = cm, tmax = Treg;
+            X cmin = cm, tmax = Treg;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                cmin = min(cmin, __shfl_xor_sync(kFull, cmin, o));
-                tmax = max(tmax, __shfl_xor_sync(kFull, tmax, o));
+                cmin = emin(cmin, __shfl_xor_sync(kFull, cmin, o));
+                tmax = emax(tmax, __shfl_xor_sync(kFull, tmax, o));
             }
-            const int32_t umax = tmax + mu - P;
+            const X umax = tmax + mu - P;
             const int i0 = kb << Z;
             int ii = i0 + lane;
             int gi = ii ^ (ii >> 1);
-            int32_t zs = zero_row_sum(gi & (nz - 1), wsm, Z);
+            X zs = zero_row_sum(gi & (nz - 1), wsm, Z);
             for (int off = 0; off < nz; off += 32) {
                 if (off > 0) {  // ii advances by 32: refresh the zero-row bits that changed
                     ii += 32;
@@ -275,21 +285,21 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
                     gi = gn;
                 }
                 const bool valid = off + lane < nz;
-                const int32_t el = valid ? __ldg(EL + ii) + zs : 0;
+                const X el = valid ? __ldg(EL + ii) + zs : 0;
                 unsigned m = __ballot_sync(kFull, valid && cmin + el <= umax);
                 while (m) {
                     const int src = __ffs(m) - 1;
                     m &= m - 1;
-                    const int32_t els = __shfl_sync(kFull, el, src);
+                    const X els = __shfl_sync(kFull, el, src);
                     const int is = i0 + off + src;
-                    int32_t tp = Treg + mu - P - els;
+                    X tp = Treg + mu - P - els;
                     if (cm > tp)
                         continue;
                     const uint64_t cb = cbase | ((uint64_t)(is ^ (is >> 1)) << B);
                     for (int q = 0; q < S; ++q) {
-                        const int32_t ev = stage[q * 32 + lane];
+                        const X ev = stage[q * 32 + lane];
                         if (ev <= tp) {
-                            const int32_t Et = ev + els + P;
+                            const X Et = ev + els + P;
                             const uint32_t j = (uint32_t)(((q / V) * 32 + lane) * V + (q % V));
                             record<T>(a, inst, Et, unpermute(cb | j, d.perm));
                             if (K1 && Et < Treg) {
@@ -304,18 +314,45 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
             __syncwarp();
         }
     }
+
+    if constexpr (Tr<T>::kFloat) {
+        // FP32 drift: the columns and P after 2^(L-Z) - 1 block updates against fresh values at
+        // the walk's end, where only walked row L - 1 (the top one) is set
+        X f0r, cxr, lt, le[V], lg[G];
+        unit_fields<T>(W, n, k, BL, unit, lane, f0r, cxr);
+        column_fields<X, V, G>(f0r, lane, lt, le, lg);
+        const X *rowT = Mt + (size_t)(L - 1) * NB;
+        double dmax = 0.0;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            X ev[V], mv[V];
+            vload<X>(Es + (g * 32 + lane) * V, ev);
+            vload<X>(rowT + (g * 32 + lane) * V, mv);
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                dmax = fmax(dmax, fabs((double)E[g * V + e] - (double)(ev[e] + le[e] + lt + lg[g] + mv[e])));
+        }
+        const X wtop = __shfl_sync(kFull, f0r, B + L - 1);
+        dmax = fmax(dmax, fabs((double)P - (double)(cxr + wtop)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
+        if (lane == 0)
+            atomicMax(&st->drift, (unsigned long long)__double_as_longlong(dmax));
+    }
 }
 
-template <int S, bool K1>
+template <class T, int S, bool K1>
 __global__ void __launch_bounds__(kScanThreads, 3) zscan_kernel(const ScanArgs a)
 {
-    __shared__ int32_t stage_all[kScanThreads / 32][S * 32 > kZTableEntries ? S * 32 : kZTableEntries];
-    __shared__ int32_t wsm_all[kScanThreads / 32][kMaxWalkBits];
-    __shared__ int32_t scratch_all[kScanThreads / 32][kZWarpScratch];
+    using X = typename Tr<T>::TC;
+    __shared__ X stage_all[kScanThreads / 32][S * 32 > kZTableEntries ? S * 32 : kZTableEntries];
+    __shared__ X wsm_all[kScanThreads / 32][kMaxWalkBits];
+    __shared__ X scratch_all[kScanThreads / 32][kZWarpScratch];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t Treg = 0;
-    persistent_units<int32_t, 8>(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
-        zscan_unit<S, K1>(a, d, inst, unit, Treg, lane, wsm_all[warp], scratch_all[warp], stage_all[warp]);
+    typename Tr<T>::TP Treg = 0;
+    persistent_units<T, 8>(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
+        zscan_unit<T, S, K1>(a, d, inst, unit, Treg, lane, wsm_all[warp], scratch_all[warp], stage_all[warp]);
     });
 }
 
@@ -325,116 +362,117 @@ __global__ void __launch_bounds__(kScanThreads, 3) zscan_kernel(const ScanArgs a
 
 // Minimum over the 2^Z walk steps of a unit of e(i) = E_L(g(i)) + sum of the zero-row couplings
 // of the set bits of g(i) (Z >= 7; the same decomposition as zscan_unit's block minima, parity 0).
-__device__ __forceinline__ int32_t walk_min_one(const int32_t *EL, int Z, int lane, const int32_t *wsm, int32_t *wt,
-                                                int32_t *gs)
+template <class X>
+__device__ __forceinline__ X walk_min_one(const X *EL, int Z, int lane, const X *wsm, X *wt, X *gs)
 {
     const int zt = Z - 7;
     if (lane == 0)
         gs[0] = 0;
     __syncwarp();
     for (int b = 0; b < zt; ++b) {
-        const int32_t wb = wsm[7 + b];
+        const X wb = wsm[7 + b];
         for (int m = lane; m < (1 << b); m += 32)
             gs[m + (1 << b)] = gs[m] + wb;
         __syncwarp();
     }
     for (int e = lane; e < (1 << zt); e += 32)  // parity 0: only the lower half of the table
         wt[e] = gs[(e ^ (e >> 1)) & ((1 << zt) - 1)];
-    int32_t a = 0;
+    X a = 0;
     for (int r = 0; r < 4; ++r)
         if (((lane >> r) ^ (lane >> (r + 1))) & 1)
             a += wsm[2 + r];
     const bool l0 = lane & 1, l4 = (lane >> 4) & 1;
-    int32_t ae[4], ao[4];
+    X ae[4], ao[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const bool g0 = (k ^ (k >> 1)) & 1, g1 = ((k >> 1) & 1) ^ l0;
-        const int32_t base = a + (g0 ? wsm[0] : 0) + (g1 ? wsm[1] : 0);
+        const X base = a + (g0 ? wsm[0] : 0) + (g1 ? wsm[1] : 0);
         ae[k] = base + (l4 ? wsm[6] : 0);
         ao[k] = base + (l4 ? 0 : wsm[6]);
     }
     __syncwarp();
-    const int32_t *e = EL + 4 * lane;
-    int32_t acc;
+    const X *e = EL + 4 * lane;
+    X acc;
     if (zt == 0) {
-        int32_t v[4];
-        vload<int32_t>(e, v);
-        acc = min(__vimin3_s32(v[0] + ae[0], v[1] + ae[1], v[2] + ae[2]), v[3] + ae[3]);
+        X v[4];
+        vload<X>(e, v);
+        acc = emin(emin3(v[0] + ae[0], v[1] + ae[1], v[2] + ae[2]), v[3] + ae[3]);
     } else {
-        int32_t me = INT32_MAX, mo = INT32_MAX;
+        X me = zbig<X>(), mo = zbig<X>();
         const int nt = 1 << zt;
 #pragma unroll 4
         for (int t = 0; t < nt; t += 2) {
-            int32_t v[4], u[4];
-            vload<int32_t>(e + (t << 7), v);
-            vload<int32_t>(e + ((t + 1) << 7), u);
-            const int32_t mv = min(__vimin3_s32(v[0] + ae[0], v[1] + ae[1], v[2] + ae[2]), v[3] + ae[3]);
-            const int32_t mw = min(__vimin3_s32(u[0] + ao[0], u[1] + ao[1], u[2] + ao[2]), u[3] + ao[3]);
-            me = min(me, mv + wt[t]);
-            mo = min(mo, mw + wt[t + 1]);
+            X v[4], u[4];
+            vload<X>(e + (t << 7), v);
+            vload<X>(e + ((t + 1) << 7), u);
+            const X mv = emin(emin3(v[0] + ae[0], v[1] + ae[1], v[2] + ae[2]), v[3] + ae[3]);
+            const X mw = emin(emin3(u[0] + ao[0], u[1] + ao[1], u[2] + ao[2]), u[3] + ao[3]);
+            me = emin(me, mv + wt[t]);
+            mo = emin(mo, mw + wt[t + 1]);
         }
-        acc = min(me, mo);
+        acc = emin(me, mo);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
-        acc = min(acc, __shfl_xor_sync(kFull, acc, o));
+        acc = emin(acc, __shfl_xor_sync(kFull, acc, o));
     return acc;
 }
 
-template <int S, bool K1>
-__device__ void zscan_unit_one(const ScanArgs &a, const Inst &d, int inst, uint64_t unit, int32_t &Treg, int lane,
-                               int32_t *wsm, int32_t *wt, int32_t *gs, int32_t *lin_sm)
+template <class T, int S, bool K1>
+__device__ void zscan_unit_one(const ScanArgs &a, const Inst &d, int inst, uint64_t unit, typename Tr<T>::TP &Treg,
+                               int lane, typename Tr<T>::TC *wsm, typename Tr<T>::TC *wt, typename Tr<T>::TC *gs,
+                               typename Tr<T>::TC *lin_sm)
 {
-    using T = int32_t;
+    using X = typename Tr<T>::TC;
     constexpr int V = 4, G = S / V, LOGG = ilog2c(G);
     constexpr int B = 2 + 5 + LOGG;
     const int n = d.n, Z = d.L, k = d.k, BL = B + Z, nz = 1 << Z;
     InstState *st = a.state + inst;
-    const int32_t *W = (const int32_t *)d.W;
+    const X *W = unit_matrix<T>(d);
 
-    int32_t f0, cx;
+    X f0, cx;
     unit_fields<T>(W, n, k, BL, unit, lane, f0, cx);
     __syncwarp();
     if (lane >= B && lane < BL)
         wsm[lane - B] = f0;
     __syncwarp();
-    int32_t lin_t, lin_e[V], lin_g[G];
-    column_fields<int32_t, V, G>(f0, lane, lin_t, lin_e, lin_g);
-    const int32_t *Es = (const int32_t *)d.Es;
+    X lin_t, lin_e[V], lin_g[G];
+    column_fields<X, V, G>(f0, lane, lin_t, lin_e, lin_g);
+    const X *Es = (const X *)d.Es;
     // column j = E_s(j) + lin(j), j = (g * 32 + lane) * 4 + e; only its minimum is kept
-    auto column = [&](int g, int e, const int32_t (&ev)[V]) { return ev[e] + lin_e[e] + lin_t + lin_g[g]; };
-    int32_t cm = INT32_MAX;
+    auto column = [&](int g, int e, const X (&ev)[V]) { return ev[e] + lin_e[e] + lin_t + lin_g[g]; };
+    X cm = zbig<X>();
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        int32_t ev[V];
-        vload<int32_t>(Es + (g * 32 + lane) * V, ev);
-        cm = min(cm, __vimin3_s32(column(g, 0, ev), column(g, 1, ev), min(column(g, 2, ev), column(g, 3, ev))));
+        X ev[V];
+        vload<X>(Es + (g * 32 + lane) * V, ev);
+        cm = emin(cm, emin3(column(g, 0, ev), column(g, 1, ev), emin(column(g, 2, ev), column(g, 3, ev))));
     }
-    const int32_t *EL = (const int32_t *)d.EL;
-    const int32_t mel = walk_min_one(EL, Z, lane, wsm, wt, gs);
+    const X *EL = (const X *)d.EL;
+    const X mel = walk_min_one(EL, Z, lane, wsm, wt, gs);
     {
-        const int32_t tg = Tr<T>::thr_load(st);
-        Treg = K1 ? min(Treg, tg) : tg;
+        const X tg = Tr<T>::thr_load(st);
+        Treg = K1 ? emin(Treg, tg) : tg;
     }
-    const int32_t mu = (int32_t)a.margin;
-    const int32_t P = cx;
+    const X mu = (X)a.margin;
+    const X P = cx;
     const uint64_t cbase = unit << BL;
     if (__any_sync(kFull, cm + mel <= Treg + mu - P)) {
         // rare: as in zscan_unit, the warp enumerates the unit's steps together; each lane
         // recomputes its columns at a broadcast step
-        int32_t cmin = cm, tmax = Treg;
+        X cmin = cm, tmax = Treg;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            cmin = min(cmin, __shfl_xor_sync(kFull, cmin, o));
-            tmax = max(tmax, __shfl_xor_sync(kFull, tmax, o));
+            cmin = emin(cmin, __shfl_xor_sync(kFull, cmin, o));
+            tmax = emax(tmax, __shfl_xor_sync(kFull, tmax, o));
         }
-        const int32_t umax = tmax + mu - P;
+        const X umax = tmax + mu - P;
 #pragma unroll
         for (int g = 0; g < G; ++g)  // the slow path indexes the column groups at run time
             lin_sm[g * 32 + lane] = lin_g[g];
         int ii = lane;
         int gi = ii ^ (ii >> 1);
-        int32_t zs = zero_row_sum(gi & (nz - 1), wsm, Z);
+        X zs = zero_row_sum(gi & (nz - 1), wsm, Z);
         for (int off = 0; off < nz; off += 32) {
             if (off > 0) {
                 ii += 32;
@@ -447,26 +485,26 @@ __device__ void zscan_unit_one(const ScanArgs &a, const Inst &d, int inst, uint6
                 }
                 gi = gn;
             }
-            const int32_t el = __ldg(EL + ii) + zs;
+            const X el = __ldg(EL + ii) + zs;
             unsigned m = __ballot_sync(kFull, cmin + el <= umax);
             while (m) {
                 const int src = __ffs(m) - 1;
                 m &= m - 1;
-                const int32_t els = __shfl_sync(kFull, el, src);
+                const X els = __shfl_sync(kFull, el, src);
                 const int is = off + src;
-                int32_t tp = Treg + mu - P - els;
+                X tp = Treg + mu - P - els;
                 if (cm > tp)
                     continue;
                 const uint64_t cb = cbase | ((uint64_t)(is ^ (is >> 1)) << B);
                 for (int g = 0; g < G; ++g) {
-                    int32_t ev[V];
-                    vload<int32_t>(Es + (g * 32 + lane) * V, ev);
-                    const int32_t lg = lin_sm[g * 32 + lane];
+                    X ev[V];
+                    vload<X>(Es + (g * 32 + lane) * V, ev);
+                    const X lg = lin_sm[g * 32 + lane];
 #pragma unroll
                     for (int e = 0; e < V; ++e) {
-                        const int32_t c = ev[e] + lin_e[e] + lin_t + lg;
+                        const X c = ev[e] + lin_e[e] + lin_t + lg;
                         if (c <= tp) {
-                            const int32_t Et = c + els + P;
+                            const X Et = c + els + P;
                             const uint32_t j = (uint32_t)((g * 32 + lane) * V + e);
                             record<T>(a, inst, Et, unpermute(cb | j, d.perm));
                             if (K1 && Et < Treg) {
@@ -482,45 +520,58 @@ __device__ void zscan_unit_one(const ScanArgs &a, const Inst &d, int inst, uint6
     }
 }
 
-template <int S, bool K1>
+template <class T, int S, bool K1>
 __global__ void __launch_bounds__(kScanThreads, 6) zscan_one_kernel(const ScanArgs a)
 {
-    __shared__ int32_t wsm_all[kScanThreads / 32][kMaxWalkBits];
-    __shared__ int32_t wt_all[kScanThreads / 32][1 << (kZMaxRows - 7)];
-    __shared__ int32_t gs_all[kScanThreads / 32][1 << (kZMaxRows - 7)];
-    __shared__ int32_t lin_all[kScanThreads / 32][S / 4 * 32];
+    using X = typename Tr<T>::TC;
+    __shared__ X wsm_all[kScanThreads / 32][kMaxWalkBits];
+    __shared__ X wt_all[kScanThreads / 32][1 << (kZMaxRows - 7)];
+    __shared__ X gs_all[kScanThreads / 32][1 << (kZMaxRows - 7)];
+    __shared__ X lin_all[kScanThreads / 32][S / 4 * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int32_t Treg = 0;
-    persistent_units<int32_t, 8>(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
-        zscan_unit_one<S, K1>(a, d, inst, unit, Treg, lane, wsm_all[warp], wt_all[warp], gs_all[warp],
+    typename Tr<T>::TP Treg = 0;
+    persistent_units<T, 8>(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
+        zscan_unit_one<T, S, K1>(a, d, inst, unit, Treg, lane, wsm_all[warp], wt_all[warp], gs_all[warp],
                               lin_all[warp]);
     });
 }
 
-template <bool K1>
+template <class T, bool K1>
 auto zpick(int variant)
 {
-    return variant == 3   ? zscan_one_kernel<kZCols[3], K1>
-           : variant == 2 ? zscan_kernel<kZCols[2], K1>
-           : variant == 1 ? zscan_kernel<kZCols[1], K1>
-                          : zscan_kernel<kZCols[0], K1>;
+    return variant == 3   ? zscan_one_kernel<T, kZCols[3], K1>
+           : variant == 2 ? zscan_kernel<T, kZCols[2], K1>
+           : variant == 1 ? zscan_kernel<T, kZCols[1], K1>
+                          : zscan_kernel<T, kZCols[0], K1>;
 }
 
-}  // namespace
-
-cudaError_t launch_zscan(const ScanArgs &a, int blocks, int variant, cudaStream_t s)
+template <class T>
+cudaError_t launch_z(const ScanArgs &a, int blocks, int variant, cudaStream_t s)
 {
-    auto k = a.k1 ? zpick<true>(variant) : zpick<false>(variant);
+    auto k = a.k1 ? zpick<T, true>(variant) : zpick<T, false>(variant);
     k<<<blocks, kScanThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-int zscan_blocks_per_sm(bool k1, int variant)
+template <class T>
+int z_blocks_per_sm(bool k1, int variant)
 {
     int nb = 0;
-    auto k = k1 ? zpick<true>(variant) : zpick<false>(variant);
+    auto k = k1 ? zpick<T, true>(variant) : zpick<T, false>(variant);
     const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kScanThreads, 0);
     return e == cudaSuccess ? nb : -1;
+}
+
+}  // namespace
+
+cudaError_t launch_zscan(const ScanArgs &a, int blocks, int variant, bool is_float, cudaStream_t s)
+{
+    return is_float ? launch_z<float>(a, blocks, variant, s) : launch_z<int32_t>(a, blocks, variant, s);
+}
+
+int zscan_blocks_per_sm(bool k1, int variant, bool is_float)
+{
+    return is_float ? z_blocks_per_sm<float>(k1, variant) : z_blocks_per_sm<int32_t>(k1, variant);
 }
 
 }  // namespace qubo

@@ -1,9 +1,9 @@
-// Constants of the factored scan of sparse instances (scan_i32z.cu), shared with the host driver.
+// Constants of the factored scan of sparse instances (scan_sparse.cu), shared with the host driver.
 #pragma once
 
 namespace qubo {
 
-// Factored scan of sparse instances (scan_i32z.cu): columns per thread of each variant, the
+// Factored scan of sparse instances: columns per thread of each variant, the
 // most zero rows (walked rows without suffix couplings) and the most column-walk blocks.
 // Variant 3 is the one-block-per-unit kernel (every walked row factored, Z = L >= 7).
 constexpr int kZVariants = 4;

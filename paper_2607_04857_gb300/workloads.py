@@ -76,6 +76,20 @@ def sparse_int(n: int, density: float, lo: int, hi: int, seed: int, dtype=np.int
     return Q.astype(dtype)
 
 
+def sparse_float32(n: int, density: float, seed: int) -> np.ndarray:
+    """Symmetric FP32 Q: diagonal N(0,1), each off-diagonal pair present with probability
+    `density` with value N(0,1)/sqrt(n * density) (a sparse SK-like spin glass); stored FP32."""
+    rng = _rng(seed)
+    iu = np.triu_indices(n, k=1)
+    present = rng.random(len(iu[0])) < density
+    off = (rng.standard_normal(len(iu[0])) / np.sqrt(max(1.0, n * density))).astype(np.float32) * present
+    Q = np.zeros((n, n), dtype=np.float32)
+    Q[iu] = off
+    Q[(iu[1], iu[0])] = off
+    Q[np.arange(n), np.arange(n)] = rng.standard_normal(n).astype(np.float32)
+    return Q
+
+
 def planted(n: int, seed: int, x_star: int | None = None, dtype=np.int32):
     """Diagonal Q = diag(w * (1 - 2 x*)) with w > 0, whose unique minimiser is x*.
     Returns (Q, x*)."""

@@ -167,3 +167,56 @@ def test_sparse_wide_subproblem(q):
     assert r.ties == [int(t) | (v << 28) for t in o.ties]
     assert r.topk == [int(t) | (v << 28) for t in o.topk]
     assert r.topk_E.tolist() == [int(e) + c for e in o.topk_E]
+
+
+# --- sparse float instances: the factored scan in FP32 with FP64 rescoring ---------------------
+
+FLOAT_RTOL = 1e-9
+
+
+def check_float(r, o):
+    assert abs(r.min - o.min) <= FLOAT_RTOL * max(1.0, abs(o.min)), (r.min, o.min)
+    assert r.n_ties == o.n_ties
+    assert np.array_equal(r.ties, o.ties)
+    assert np.array_equal(r.topk, o.topk), (r.topk, o.topk)
+    assert np.allclose(r.topk_E, o.topk_E, rtol=FLOAT_RTOL, atol=FLOAT_RTOL)
+
+
+@pytest.mark.parametrize("n", [18, 24, 29])
+@pytest.mark.parametrize("topk", [0, 8])
+def test_sparse_float_parity(q, n, topk):
+    Q = wl.sparse_float32(n, 0.1, seed=500 + n)
+    r = q.solve(Q, topk=topk)
+    assert r.info["acc"] == "f32z", r.info
+    check_float(r, oracle.solve(Q, topk=topk))
+
+
+def test_sparse_float_several_blocks_drift(q):
+    """A walk longer than the factored rows: the columns change between blocks and the FP32
+    drift is measured at the end of every unit."""
+    Q = wl.sparse_float32(30, 0.25, seed=31)
+    r = q.solve(Q, topk=6, walk_bits=10)
+    assert r.info["acc"] == "f32z" and r.info["walk_bits"] == 10
+    assert 0 < r.info["zero_rows"] < 10
+    assert 2 * r.info["fp32_max_drift"] < 1e-3
+    check_float(r, oracle.solve(Q, topk=6))
+
+
+def test_sparse_float_window_and_subcube(q):
+    Q = wl.sparse_float32(26, 0.1, seed=7)
+    cnt, codes, E, info = q.solve_window(Q, 0.5)  # splits its cube (the window holds many states)
+    o = oracle.solve(Q, topk=4096, cap=1)
+    sel = o.topk_E <= o.min + 0.5
+    assert cnt == int(sel.sum()) and np.array_equal(codes, o.topk[sel])
+    assert np.allclose(E, o.topk_E[sel], rtol=FLOAT_RTOL, atol=FLOAT_RTOL)
+    r = q.solve(Q, topk=4, fix_bits=2, fix_value=1)  # planned in whichever FP32 scan fits
+    check_float(r, oracle.solve(Q, topk=4, fix_bits=2, fix_value=1))
+
+
+def test_sparse_float_disabled_falls_back(q, monkeypatch):
+    Q = wl.sparse_float32(24, 0.1, seed=8)
+    o = oracle.solve(Q, topk=4)
+    monkeypatch.setenv("QUBO_NO_I32Z", "1")
+    r = q.solve(Q, topk=4)
+    assert r.info["acc"] == "f32"
+    check_float(r, o)
