@@ -9,7 +9,7 @@ take consecutive sub-cubes, so 2^fix_bits steps cover the whole instance.  The r
 per second (2^n / total time, the paper's convention, Sec. 5.3).
 
   python bench.py [--gpus N] [--steps K] [--warmup W]
-                  [--workload n50_int32|n44_fp32|maxcut_n48|sparse_n56|batched]
+                  [--workload n50_int32|n44_fp32|maxcut_n48|sparse_n56|sparse_f32_n56|batched]
   python bench.py --impl reference ...   (the CPU oracle on the host cores, same workload)
 
 Under torchrun every rank takes disjoint sub-cubes (no data-path collective; weak scaling).
@@ -81,6 +81,14 @@ def make_workload(name: str, fix_bits: int | None):
                     config={"workload": "sparse_n56_top16", "n": 56, "topk": 16, "seed": 56,
                             "entries": "upper-triangular int32: diagonal uniform [-1000, 1000], off-diagonal "
                                        "present with probability 0.05, uniform [-1000, 1000]",
+                            "step": f"one sub-cube of 2^{56 - fb} states (top {fb} code bits fixed)"})
+    if name == "sparse_f32_n56":
+        fb = 10 if fix_bits is None else fix_bits
+        return dict(name=name, Q=wl.sparse_float32(56, 0.05, seed=56), n=56, topk=16, fix_bits=fb,
+                    metric="states/s (n=56 sparse FP32 QUBO)", unit="states/s", dtype="f32",
+                    config={"workload": "sparse_f32_n56_top16", "n": 56, "topk": 16, "seed": 56, "margin": 1e-3,
+                            "entries": "symmetric FP32: diagonal N(0,1), off-diagonal pairs present with "
+                                       "probability 0.05, N(0,1)/sqrt(2.8)",
                             "step": f"one sub-cube of 2^{56 - fb} states (top {fb} code bits fixed)"})
     if name == "batched":
         return dict(name=name, Qs=wl.config4(), topk=0, metric="instances/s (4096 QUBOs, n uniform in 16..32)",
@@ -282,7 +290,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n50_int32",
-                    choices=["n50_int32", "n44_fp32", "maxcut_n48", "sparse_n56", "batched"])
+                    choices=["n50_int32", "n44_fp32", "maxcut_n48", "sparse_n56", "sparse_f32_n56", "batched"])
     ap.add_argument("--fix-bits", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-loop", action="store_true",
