@@ -215,6 +215,22 @@ def cpu_oracle_rate(Q, n: int, target_s: float, fix_hint: int):
     return (1 << free) / dt, dt, fb2, oracle.max_threads()
 
 
+def cpu_oracle_rate_one_core(Q, n: int, target_s: float):
+    """The same oracle on one thread (a sub-cube of about target_s seconds)."""
+    import oracle
+
+    free = min(n, 22)
+    t = time.perf_counter()
+    oracle.solve(Q, method=oracle.GRAY, topk=16, fix_bits=n - free, fix_value=1, nthreads=1)
+    rate = (1 << free) / (time.perf_counter() - t)
+    while free < n and (1 << (free + 1)) / rate < target_s:
+        free += 1
+    t = time.perf_counter()
+    oracle.solve(Q, method=oracle.GRAY, topk=16, fix_bits=n - free, fix_value=0, nthreads=1)
+    dt = time.perf_counter() - t
+    return (1 << free) / dt, dt, n - free
+
+
 # ---------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------------------------
@@ -336,9 +352,12 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline and W["name"] != "batched":
         # the oracle runs on the host cores before the GPU timing (it uses threads, no fork)
         rate, dt, fb, cores = cpu_oracle_rate(W["Q"], W["n"], 12.0, W["fix_bits"])
+        rate1, dt1, fb1 = cpu_oracle_rate_one_core(W["Q"], W["n"], 3.0)
         cpu = {"value": rate, "unit": "states/s", "cores": cores, "kind": "oracle",
                "sample": f"Gray-walk oracle on one sub-cube of 2^{W['n'] - fb} states of the same instance "
-                         f"({dt:.1f} s)"}
+                         f"({dt:.1f} s)",
+               "one_core": {"value": rate1, "unit": "states/s",
+                            "sample": f"one thread, one sub-cube of 2^{W['n'] - fb1} states ({dt1:.1f} s)"}}
         log(f"cpu oracle: {rate:.3e} states/s on {cores} threads")
 
     launches = 0
