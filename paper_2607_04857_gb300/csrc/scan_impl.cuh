@@ -723,7 +723,8 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
         unit_fields<T>(W, n, k, BL, unit, lane, f0r, cxr);
         column_fields<F, V, G>(f0r, lane, lt, le, lg);
         const TC *rowL = Mt + (size_t)(L - 1) * NB;
-        double dmax = 0.0;
+        // differences in the column type (exact for close values; FP64 is slow on this part)
+        TC cmax = 0;
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             TC ev[V], mv[V];
@@ -732,11 +733,13 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
 #pragma unroll
             for (int e = 0; e < V; ++e) {
                 const TC fresh = (TC)((F)ev[e] + (le[e] + lt + lg[g])) + mv[e];
-                dmax = fmax(dmax, fabs((double)E[g * V + e] - (double)fresh));
+                const TC dd = E[g * V + e] - fresh;
+                const TC ad = dd < 0 ? -dd : dd;
+                cmax = cmax > ad ? cmax : ad;
             }
         }
         const F wl = __shfl_sync(kFull, f0r, B + L - 1);
-        dmax = fmax(dmax, fabs((double)P - (double)(TP)(cxr + wl)));
+        double dmax = fmax((double)cmax, fabs((double)P - (double)(TP)(cxr + wl)));
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
