@@ -281,6 +281,25 @@ typedef struct {
  * input.  Host only. */
 int qubo_merge(const qubo_partial *a, const qubo_partial *b, size_t cap, int topk, qubo_partial *out);
 
+/* The same merge for results of qubo_solve_wide (128-bit codes, two words each: bits 0..63
+ * then bits 64..127), e.g. the ranges of outer values scanned by different processes or GPUs
+ * (Sec. 4.3).  ties and topk hold 2 * cap and 2 * topk words. */
+typedef struct {
+    int32_t is_float;
+    int32_t n_topk;
+    int64_t min_i;
+    double min_f;
+    uint64_t n_ties;
+    uint64_t n_written;
+    uint64_t states_scanned;
+    uint64_t *ties;
+    uint64_t *topk;
+    void *topk_E;
+} qubo_partial_wide;
+
+int qubo_merge_wide(const qubo_partial_wide *a, const qubo_partial_wide *b, size_t cap, int topk,
+                    qubo_partial_wide *out);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Solving without allocating.                                                               */
 /* ---------------------------------------------------------------------------------------- */

@@ -33,6 +33,7 @@ EXPORTS = (
     "qubo_abort_clear", "qubo_device_sm_count", "qubo_version", "qubo_solve_noalloc",
     "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_batch_destroy",
     "qubo_autotune", "qubo_autotune_batched", "qubo_autotune_clear", "qubo_solve_window", "qubo_solve_wide",
+    "qubo_merge_wide",
 )
 WIDE_MAX_N = 128
 QUBO_MAX_TOPK = 1024
@@ -89,6 +90,10 @@ class Partial(ctypes.Structure):
     ]
 
 
+class PartialWide(Partial):
+    """qubo_partial_wide: the same fields, with two words per code in ties and topk."""
+
+
 _lib = None
 
 
@@ -120,6 +125,7 @@ def load_library(path: str = LIB_PATH):
     lib.qubo_solve_window.argtypes = [P, I, I, ctypes.c_double, P, P, P, SZ, P, P, P]
     lib.qubo_autotune_batched.argtypes = [P, P, P, I, I, P]
     lib.qubo_solve_wide.argtypes = [P, I, I, I, U64, U64, P, P, P, SZ, P, P, P, P, P]
+    lib.qubo_merge_wide.argtypes = [P, P, SZ, I, P]
     lib.qubo_autotune_clear.restype = None
     lib.qubo_strerror.argtypes = [I]
     lib.qubo_strerror.restype = ctypes.c_char_p
@@ -129,7 +135,7 @@ def load_library(path: str = LIB_PATH):
     for name in ("qubo_solve", "qubo_solve_ex", "qubo_solve_batched", "qubo_problem_create", "qubo_problem_run",
                  "qubo_problem_fetch", "qubo_merge", "qubo_device_sm_count", "qubo_solve_noalloc",
                  "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_autotune",
-                 "qubo_autotune_batched", "qubo_solve_window", "qubo_solve_wide"):
+                 "qubo_autotune_batched", "qubo_solve_window", "qubo_solve_wide", "qubo_merge_wide"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -511,3 +517,47 @@ def merge(a: Result, b: Result, states_cap: int, topk: int) -> Result:
     return Result(float(mval) if isf else int(mval), int(po.n_ties), ot[: po.n_written].copy(),
                   ok[: po.n_topk].copy(), okE[: po.n_topk].copy(), 0,
                   {"states_scanned": int(po.states_scanned)})
+def merge_wide(a: Result, b: Result, states_cap: int, topk: int) -> Result:
+    """Merge two results of qubo_solve_wide over disjoint state sets (qubo_merge_wide); codes are
+    Python ints of up to 128 bits."""
+    lib = load_library()
+    isf = isinstance(a.min, float)
+    edt = np.float64 if isf else np.int64
+
+    def words(codes):
+        w = np.zeros(2 * max(len(codes), 1), dtype=np.uint64)
+        for t, c in enumerate(codes):
+            w[2 * t], w[2 * t + 1] = int(c) & (2**64 - 1), int(c) >> 64
+        return w
+
+    def part(r: Result, keep):
+        ties, tk = words(r.ties), words(r.topk)
+        tkE = np.ascontiguousarray(r.topk_E, dtype=edt)
+        keep.extend([ties, tk, tkE])
+        return PartialWide(is_float=int(isf), n_topk=len(r.topk), min_i=0 if isf else int(r.min),
+                           min_f=float(r.min), n_ties=r.n_ties, n_written=len(r.ties),
+                           states_scanned=int(r.info.get("states_scanned", 1)), ties=ties.ctypes.data,
+                           topk=tk.ctypes.data, topk_E=tkE.ctypes.data if tkE.size else None)
+
+    keep = []
+    pa, pb = part(a, keep), part(b, keep)
+    ot = np.zeros(2 * max(states_cap, 1), dtype=np.uint64)
+    ok = np.zeros(2 * max(topk, 1), dtype=np.uint64)
+    okE = np.zeros(max(topk, 1), dtype=edt)
+    po = PartialWide(ties=ot.ctypes.data, topk=ok.ctypes.data, topk_E=okE.ctypes.data)
+    _check(lib.qubo_merge_wide(ctypes.byref(pa), ctypes.byref(pb), states_cap, topk, ctypes.byref(po)),
+           "qubo_merge_wide")
+    mval = po.min_f if isf else po.min_i
+    wide = lambda w, k: [int(w[2 * t]) | (int(w[2 * t + 1]) << 64) for t in range(k)]  # noqa: E731
+    return Result(float(mval) if isf else int(mval), int(po.n_ties), wide(ot, int(po.n_written)),
+                  wide(ok, int(po.n_topk)), okE[: po.n_topk].copy(), 0, {"states_scanned": int(po.states_scanned)})
+
+
+def merge_all_wide(results, states_cap: int, topk: int) -> Result:
+    """Fold qubo_merge_wide over results of disjoint state sets."""
+    acc = None
+    for r in results:
+        acc = r if acc is None else merge_wide(acc, r, states_cap, topk)
+    return acc
+
+

@@ -2748,6 +2748,69 @@ void qubo_autotune_clear(void)
     g_tuned.clear();
 }
 
+int qubo_merge_wide(const qubo_partial_wide *a, const qubo_partial_wide *b, size_t cap, int topk,
+                    qubo_partial_wide *out)
+{
+    if (!a || !b || !out || topk < 0 || topk > QUBO_MAX_TOPK || a->is_float != b->is_float)
+        return QUBO_ERR_ARG;
+    if ((cap > 0 && !out->ties) || (topk > 0 && (!out->topk || !out->topk_E)))
+        return QUBO_ERR_ARG;
+    const bool fl = a->is_float != 0;
+    using Code = std::pair<uint64_t, uint64_t>;  // (bits 64..127, bits 0..63): ordered as the code
+    auto code = [](const uint64_t *w, size_t t) { return Code(w[2 * t + 1], w[2 * t]); };
+    auto energy = [&](const qubo_partial_wide *x, int t) {
+        return fl ? ((const double *)x->topk_E)[t] : (double)((const int64_t *)x->topk_E)[t];
+    };
+    const bool ha = a->states_scanned > 0, hb = b->states_scanned > 0;
+    const bool a_lower = fl ? a->min_f < b->min_f : a->min_i < b->min_i;
+    const bool equal = fl ? a->min_f == b->min_f : a->min_i == b->min_i;
+    std::vector<Code> ties;
+    const qubo_partial_wide *lo = (!hb || (ha && a_lower)) ? a : b;
+    if (ha && hb && equal) {
+        std::vector<Code> ta, tb;
+        for (size_t t = 0; t < a->n_written; ++t)
+            ta.push_back(code(a->ties, t));
+        for (size_t t = 0; t < b->n_written; ++t)
+            tb.push_back(code(b->ties, t));
+        std::merge(ta.begin(), ta.end(), tb.begin(), tb.end(), std::back_inserter(ties));
+        out->n_ties = a->n_ties + b->n_ties;
+    } else {
+        for (size_t t = 0; t < lo->n_written; ++t)
+            ties.push_back(code(lo->ties, t));
+        out->n_ties = lo->n_ties;
+    }
+    out->is_float = a->is_float;
+    out->min_i = lo->min_i;
+    out->min_f = lo->min_f;
+    out->states_scanned = a->states_scanned + b->states_scanned;
+    out->n_written = std::min(cap, ties.size());
+    for (size_t t = 0; t < out->n_written; ++t) {
+        out->ties[2 * t] = ties[t].second;
+        out->ties[2 * t + 1] = ties[t].first;
+    }
+    // K lowest by (E, code); integer energies stay exact as int64 in the comparison key
+    std::vector<std::tuple<double, int64_t, Code>> top;
+    for (const qubo_partial_wide *x : {a, b})
+        for (int t = 0; t < x->n_topk; ++t)
+            top.emplace_back(energy(x, t), fl ? 0 : ((const int64_t *)x->topk_E)[t], code(x->topk, t));
+    std::sort(top.begin(), top.end(), [&](const auto &p, const auto &q) {
+        if (fl ? std::get<0>(p) != std::get<0>(q) : std::get<1>(p) != std::get<1>(q))
+            return fl ? std::get<0>(p) < std::get<0>(q) : std::get<1>(p) < std::get<1>(q);
+        return std::get<2>(p) < std::get<2>(q);
+    });
+    const int nk = std::min<int>(topk, (int)top.size());
+    out->n_topk = nk;
+    for (int t = 0; t < nk; ++t) {
+        out->topk[2 * t] = std::get<2>(top[t]).second;
+        out->topk[2 * t + 1] = std::get<2>(top[t]).first;
+        if (fl)
+            ((double *)out->topk_E)[t] = std::get<0>(top[t]);
+        else
+            ((int64_t *)out->topk_E)[t] = std::get<1>(top[t]);
+    }
+    return QUBO_OK;
+}
+
 int qubo_merge(const qubo_partial *a, const qubo_partial *b, size_t cap, int topk, qubo_partial *out)
 {
     if (!a || !b || !out || topk < 0 || topk > QUBO_MAX_TOPK || a->is_float != b->is_float)
