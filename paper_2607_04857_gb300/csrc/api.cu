@@ -793,6 +793,11 @@ struct Workspace {
     }
     int ensure(size_t arena, unsigned long long recs, size_t up, size_t down)
     {
+        // fault injection for tests: QUBO_FAIL_ALLOC=1 makes every workspace request fail the
+        // way an exhausted device or pinned-host pool does (nothing is freed or touched)
+        const char *fail = std::getenv("QUBO_FAIL_ALLOC");
+        if (fail && fail[0] == '1')
+            return QUBO_ERR_NOMEM;
         int st;
         if ((st = grow_dev(&d_arena, &arena_cap, arena)))
             return st;

@@ -88,3 +88,27 @@ def test_merge_of_subcube_results_equals_full_solve(q, kind):
     assert np.array_equal(acc.ties, full.ties)
     assert np.array_equal(acc.topk, full.topk) and np.array_equal(acc.topk_E, full.topk_E)
     assert acc.info["states_scanned"] == 1 << n
+
+
+def test_ncu_summary_arithmetic(tmp_path):
+    """The counters summary: instructions per state = warp instructions x 32 / states, and the
+    issue roofline = SMs x 128 lanes x clock / instructions per state."""
+    from paper_2607_04857_gb300 import ncu_summary
+
+    rows = [
+        '"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
+        '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"',
+        '"0","1","python","h","scan_kernel","1","7","(128, 1, 1)","(456, 1, 1)","0","10.3","",'
+        '"sm__inst_executed.sum","inst","2,147,483,648"',
+        '"0","1","python","h","scan_kernel","1","7","(128, 1, 1)","(456, 1, 1)","0","10.3","",'
+        '"dram__bytes_read.sum","byte","1,024"',
+        '"0","1","python","h","scan_kernel","1","7","(128, 1, 1)","(456, 1, 1)","0","10.3","",'
+        '"gpu__time_duration.sum","ns","1,000,000"',
+    ]
+    p = tmp_path / "x.csv"
+    p.write_text("==PROF== noise\n" + "\n".join(rows) + "\n")
+    s = ncu_summary.summarise(ncu_summary.read_metrics(str(p)), 1 << 36)
+    assert s["inst_per_state"] == 2**31 * 32 / 2**36 == 1.0
+    assert s["issue_roofline_states_per_s"] == 152 * 128 * 2070e6
+    assert s["dram_bytes_per_state"] == 1024 / 2**36
+    assert s["states_per_s_under_ncu"] == 2**36 / 1e-3

@@ -83,3 +83,17 @@ def test_wide_time_limit(q):
     assert e.value.status == q.QUBO_ERR_TIMEOUT
     Q2 = wl.upper_int(20, -10, 10, seed=4)
     check_int(q.solve(Q2), oracle.solve(Q2))
+
+
+def test_allocation_failure_is_reported_and_recovers(q, monkeypatch):
+    """An injected allocation failure (QUBO_FAIL_ALLOC=1) returns QUBO_ERR_NOMEM from every entry
+    point that needs its workspace; once lifted, the next call succeeds."""
+    Q = wl.upper_int(22, -20, 20, seed=6)
+    monkeypatch.setenv("QUBO_FAIL_ALLOC", "1")
+    for call in (lambda: q.solve(Q, topk=4), lambda: q.solve_batched([Q[:18, :18], Q[:20, :20]]),
+                 lambda: q.solve_window(Q, 5)):
+        with pytest.raises(q.QuboError) as e:
+            call()
+        assert e.value.status == q.QUBO_ERR_NOMEM
+    monkeypatch.delenv("QUBO_FAIL_ALLOC")
+    check_int(q.solve(Q, topk=4), oracle.solve(Q, topk=4))
