@@ -366,6 +366,14 @@ int qubo_autotune_batched(const void *Q_packed, const int *n, const size_t *offs
 /* Forget every installed plan. */
 void qubo_autotune_clear(void);
 
+/* Keep tuned plans across processes: qubo_autotune_save writes the plans installed for the
+ * current device to a text file (one line per plan: device name, SM count, accumulator, n,
+ * variant, walk bits); qubo_autotune_load installs, for the current device, every plan of the
+ * file whose device name and SM count match it.  Both return the number of plans written or
+ * installed, or a negative qubo_status (QUBO_ERR_ARG for an unreadable file or a bad line). */
+int qubo_autotune_save(const char *path);
+int qubo_autotune_load(const char *path);
+
 /* ---------------------------------------------------------------------------------------- */
 /* Utilities.                                                                                 */
 /* ---------------------------------------------------------------------------------------- */

@@ -33,7 +33,7 @@ EXPORTS = (
     "qubo_abort_clear", "qubo_device_sm_count", "qubo_version", "qubo_solve_noalloc",
     "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_batch_destroy",
     "qubo_autotune", "qubo_autotune_batched", "qubo_autotune_clear", "qubo_solve_window", "qubo_solve_wide",
-    "qubo_merge_wide",
+    "qubo_merge_wide", "qubo_autotune_save", "qubo_autotune_load",
 )
 WIDE_MAX_N = 128
 QUBO_MAX_TOPK = 1024
@@ -126,6 +126,8 @@ def load_library(path: str = LIB_PATH):
     lib.qubo_autotune_batched.argtypes = [P, P, P, I, I, P]
     lib.qubo_solve_wide.argtypes = [P, I, I, I, U64, U64, P, P, P, SZ, P, P, P, P, P]
     lib.qubo_merge_wide.argtypes = [P, P, SZ, I, P]
+    lib.qubo_autotune_save.argtypes = [ctypes.c_char_p]
+    lib.qubo_autotune_load.argtypes = [ctypes.c_char_p]
     lib.qubo_autotune_clear.restype = None
     lib.qubo_strerror.argtypes = [I]
     lib.qubo_strerror.restype = ctypes.c_char_p
@@ -135,7 +137,8 @@ def load_library(path: str = LIB_PATH):
     for name in ("qubo_solve", "qubo_solve_ex", "qubo_solve_batched", "qubo_problem_create", "qubo_problem_run",
                  "qubo_problem_fetch", "qubo_merge", "qubo_device_sm_count", "qubo_solve_noalloc",
                  "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_autotune",
-                 "qubo_autotune_batched", "qubo_solve_window", "qubo_solve_wide", "qubo_merge_wide"):
+                 "qubo_autotune_batched", "qubo_solve_window", "qubo_solve_wide", "qubo_merge_wide",
+                 "qubo_autotune_save", "qubo_autotune_load"):
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -295,6 +298,16 @@ def autotune_batched(Qs) -> dict:
 
 def autotune_clear() -> None:
     load_library().qubo_autotune_clear()
+
+
+def autotune_save(path: str) -> int:
+    """Write the plans tuned on the current device to `path` (qubo_autotune_save)."""
+    return _check(load_library().qubo_autotune_save(os.fsencode(path)), "qubo_autotune_save")
+
+
+def autotune_load(path: str) -> int:
+    """Install the plans of `path` saved on a device like the current one (qubo_autotune_load)."""
+    return _check(load_library().qubo_autotune_load(os.fsencode(path)), "qubo_autotune_load")
 
 
 class BatchResults:

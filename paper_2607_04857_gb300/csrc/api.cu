@@ -4,6 +4,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
@@ -12,6 +13,7 @@
 #include <tuple>
 #include <new>
 #include <random>
+#include <string>
 #include <thread>
 #include <unordered_set>
 #include <utility>
@@ -2751,6 +2753,85 @@ void qubo_autotune_clear(void)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tuned.clear();
+}
+
+namespace {
+// Name and SM count of the current device: the key a saved plan is valid for.
+bool device_key(int *dev, std::string *name, int *sms)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDevice(dev) != cudaSuccess || cudaGetDeviceProperties(&prop, *dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    *name = prop.name;
+    std::replace(name->begin(), name->end(), '\t', ' ');
+    *sms = prop.multiProcessorCount;
+    return true;
+}
+}  // namespace
+
+int qubo_autotune_save(const char *path)
+{
+    int dev = -1, sms = 0;
+    std::string name;
+    if (!path || !device_key(&dev, &name, &sms))
+        return path ? QUBO_ERR_CUDA : QUBO_ERR_ARG;
+    FILE *f = std::fopen(path, "w");
+    if (!f)
+        return QUBO_ERR_ARG;
+    std::fprintf(f, "qubo-autotune 1\n");
+    int count = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (const auto &kv : g_tuned) {
+            if (std::get<0>(kv.first) != dev)
+                continue;
+            std::fprintf(f, "%s\t%d\t%d\t%d\t%d\t%d\n", name.c_str(), sms, std::get<1>(kv.first),
+                         std::get<2>(kv.first), kv.second.first, kv.second.second);
+            ++count;
+        }
+    }
+    const bool ok = std::fclose(f) == 0;
+    return ok ? count : QUBO_ERR_ARG;
+}
+
+int qubo_autotune_load(const char *path)
+{
+    int dev = -1, sms = 0;
+    std::string name;
+    if (!path || !device_key(&dev, &name, &sms))
+        return path ? QUBO_ERR_CUDA : QUBO_ERR_ARG;
+    FILE *f = std::fopen(path, "r");
+    if (!f)
+        return QUBO_ERR_ARG;
+    char line[512];
+    int count = 0, st = QUBO_OK;
+    if (!std::fgets(line, sizeof line, f) || std::strncmp(line, "qubo-autotune 1", 15) != 0)
+        st = QUBO_ERR_ARG;
+    std::vector<std::pair<std::tuple<int, int, int>, std::pair<int, int>>> plans;
+    while (st == QUBO_OK && std::fgets(line, sizeof line, f)) {
+        char *tab = std::strchr(line, '\t');
+        int fs = 0, acc = 0, n = 0, variant = 0, walk = 0;
+        if (!tab || std::sscanf(tab + 1, "%d\t%d\t%d\t%d\t%d", &fs, &acc, &n, &variant, &walk) != 5 ||
+            acc < ACC_I32 || acc > ACC_F32Z || n < 0 || n > 64 || variant < 0 || variant >= kScanVariants ||
+            walk < 0 || walk > kMaxWalkBits) {
+            st = QUBO_ERR_ARG;
+            break;
+        }
+        *tab = 0;
+        if (name == line && fs == sms)
+            plans.push_back({{dev, acc, n}, {variant, walk}});
+    }
+    std::fclose(f);
+    if (st)
+        return st;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto &p : plans) {
+        g_tuned[p.first] = p.second;
+        ++count;
+    }
+    return count;
 }
 
 int qubo_merge_wide(const qubo_partial_wide *a, const qubo_partial_wide *b, size_t cap, int topk,

@@ -377,6 +377,32 @@ def test_autotune_installs_a_working_plan(q):
         q.autotune_clear()
 
 
+def test_autotune_plans_persist(q, tmp_path):
+    """Tuned plans saved to a file and loaded into a cleared process state are used again; a file
+    from another device model installs nothing, and a malformed file is an argument error."""
+    Q = wl.upper_int(34, -500, 500, seed=56)
+    p = q.autotune(Q, fix_bits=8)
+    path = str(tmp_path / "plans.txt")
+    try:
+        assert q.autotune_save(path) >= 1
+        q.autotune_clear()
+        assert q.autotune_load(path) >= 1
+        r = q.solve(Q, topk=4, fix_bits=6, fix_value=1)
+        assert r.info["walk_bits"] == p["walk_bits"]
+        check_int(r, oracle.solve(Q, topk=4, fix_bits=6, fix_value=1))
+        other = tmp_path / "other.txt"
+        other.write_text("qubo-autotune 1\nSome Other GPU\t80\t1\t34\t0\t9\n")
+        q.autotune_clear()
+        assert q.autotune_load(str(other)) == 0
+        bad = tmp_path / "bad.txt"
+        bad.write_text("not a plan file\n")
+        with pytest.raises(q.QuboError) as e:
+            q.autotune_load(str(bad))
+        assert e.value.status == q.QUBO_ERR_ARG
+    finally:
+        q.autotune_clear()
+
+
 def test_autotune_batched(q):
     insts = [wl.upper_int(n, -100, 100, seed=n, dtype=np.int16) for n in (14, 17, 20, 22, 23)]
     p = q.autotune_batched(insts)
