@@ -65,7 +65,7 @@ def make_workload(name: str, fix_bits: int | None):
                     unit="states/s", dtype="f32",
                     config={"workload": "n44_fp32_sk", "n": 44, "seed": 3, "margin": 1e-3,
                             "entries": "symmetric FP32, off-diagonal N(0,1)/sqrt(44), diagonal N(0,1)",
-                            "anchor": "re-anchored at every unit start: 2^10 Gray steps per walk",
+                            "anchor": "re-anchored every 2^10 Gray steps inside 2^14-step walks",
                             "step": f"one sub-cube of 2^{44 - fb} states (top {fb} code bits fixed)"})
     if name == "maxcut_n48":
         fb = 6 if fix_bits is None else fix_bits

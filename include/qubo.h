@@ -108,7 +108,8 @@ typedef struct {
     int32_t truncated;        /* 1 if n_ties > states_cap */
     int32_t acc;              /* qubo_acc the scan ran in */
     int32_t n_topk;           /* entries written to out_topk (min(topk, states in the scan)) */
-    int32_t reserved0;
+    int32_t anchor_bits;      /* QUBO_ACC_F32: the scan re-anchored every 2^anchor_bits walk steps
+                                 (and at every unit start); 0 otherwise */
     double fp32_max_abs_err;  /* float Q: max |E_scan - E_fp64| over the rescored candidates */
     double fp32_max_drift;    /* float Q: max |incremental - recomputed| energy at re-anchoring */
     uint64_t n_near_ties;     /* float Q: states within 1e-9*max(1,|min|) of min (among the

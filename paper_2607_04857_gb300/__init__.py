@@ -59,7 +59,7 @@ class ResultInfo(ctypes.Structure):
     _fields_ = [
         ("min_i", ctypes.c_int64), ("min_f", ctypes.c_double), ("n_ties", ctypes.c_uint64),
         ("n_written", ctypes.c_uint64), ("truncated", ctypes.c_int32), ("acc", ctypes.c_int32),
-        ("n_topk", ctypes.c_int32), ("reserved0", ctypes.c_int32), ("fp32_max_abs_err", ctypes.c_double),
+        ("n_topk", ctypes.c_int32), ("anchor_bits", ctypes.c_int32), ("fp32_max_abs_err", ctypes.c_double),
         ("fp32_max_drift", ctypes.c_double), ("n_near_ties", ctypes.c_uint64),
         ("states_scanned", ctypes.c_uint64), ("candidates", ctypes.c_uint64), ("seconds", ctypes.c_double),
         ("seconds_gpu", ctypes.c_double), ("seconds_scan", ctypes.c_double), ("states_per_s", ctypes.c_double),

@@ -87,7 +87,7 @@ struct Inst {
     void *EL;             // 2^L walked-prefix energies in Gray-walk order
     int64_t thr0;         // initial threshold (int64 value or double bits)
     int32_t Z;            // ACC_I32Z: walked rows 0..Z-1 have no coupling to a suffix variable
-    int32_t pad;
+    int32_t anchor;       // float scans: re-anchor every 2^anchor walk steps (0 or >= L: at the end only)
     const uint8_t *perm;  // ACC_I32Z: variable of the caller's order at each scan position
 };
 

@@ -230,6 +230,8 @@ __device__ __forceinline__ void vload(const E *p, E (&o)[VecOf<E>::V])
 {
     vsplit(__ldg((const typename VecOf<E>::type *)p), o);
 }
+__device__ __forceinline__ float4 vjoin(const float *v) { return make_float4(v[0], v[1], v[2], v[3]); }
+__device__ __forceinline__ double2 vjoin(const double *v) { return make_double2(v[0], v[1]); }
 
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 __host__ __device__ constexpr int ctzc(int v) { return (v & 1) ? 0 : 1 + ctzc(v >> 1); }
@@ -499,7 +501,7 @@ __device__ __forceinline__ void column_fields(F f0, int lane, F &lin_t, F (&lin_
 template <class T, int S, int RC, bool K1, int ADDM, int MINM>
 __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t unit,
                                           typename Tr<T>::TP &Treg, int lane, typename Tr<T>::TC *stage,
-                                          typename Tr<T>::TP *wsm)
+                                          typename Tr<T>::TP *wsm, typename Tr<T>::TC *anc)
 {
     using F = typename Tr<T>::FU;
     using TC = typename Tr<T>::TC;
@@ -539,6 +541,12 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
 #pragma unroll
         for (int e = 0; e < V; ++e)
             E[g * V + e] = (TC)((F)ev[e] + (lin_e[e] + lin_t + lin_g[g]));
+    }
+    if constexpr (Tr<T>::kFloat) {
+        // float scans: these columns (walked bits all zero) are the base of every re-anchoring
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+            *(typename VecOf<TC>::type *)(anc + (g * 32 + lane) * V) = vjoin(E + g * V);
     }
 
     // Register rows r < RC: M_r[j] + w_r, the walked-fixed coupling of row r folded in.
@@ -591,12 +599,63 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
         uc = to_col<T>(u, clampC);
     };
 
+    // Float scans re-anchor (Sec. 6.2, periodic correction): at walk step i (a multiple of 2^(RC+1),
+    // so the register rows are clear) the columns are rebuilt as the base columns plus the rows of
+    // the set walked bits, and P as c(x_f) plus their couplings; the largest difference to the
+    // incrementally updated values is the drift the host checks against the candidate margin.
+    // Mid-walk anchors every 2^anchor steps; one at the walk's end in any case.
+    TC dl = 0;
+    auto reanchor = [&](int i) {
+        const int gi = i ^ (i >> 1);
+        TP Pf = (TP)cx;
+        TC fr[S];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            TC bv[V];
+            vsplit(*(const typename VecOf<TC>::type *)(anc + (g * 32 + lane) * V), bv);
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                fr[g * V + e] = bv[e];
+        }
+        for (unsigned bits = (unsigned)gi >> RC; bits; bits &= bits - 1) {
+            const int r = RC + __ffs(bits) - 1;
+            Pf = Pf + wsm[r];
+            const TC *row = Mt + (size_t)r * NB;
+#pragma unroll
+            for (int g = 0; g < G; ++g) {
+                TC mv[V];
+                vload<TC>(row + (g * 32 + lane) * V, mv);
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    fr[g * V + e] = fr[g * V + e] + mv[e];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+            const TC dd = E[q] - fr[q];  // exact for close values
+            const TC ad = dd < 0 ? -dd : dd;
+            dl = dl > ad ? dl : ad;
+            E[q] = fr[q];
+        }
+        const TC dp = (TC)(P < Pf ? Pf - P : P - Pf);
+        dl = dl > dp ? dl : dp;
+        P = Pf;
+        u = Treg + mu - P;
+        uc = to_col<T>(u, clampC);
+    };
+    // anchor period in bodies minus one; -1 (never) without mid-walk anchors
+    const int amask = (Tr<T>::kFloat && d.anchor > RC && d.anchor < L) ? (1 << (d.anchor - RC - 1)) - 1 : -1;
+
     const TC *ELp = (const TC *)d.EL;
     const int nblk = 1 << (L - RC - 1);
     const uint64_t cbase = unit << BL;
 
     for (int blk = 0; blk < nblk; ++blk) {
         const int i0 = blk * BODY;
+        if constexpr (Tr<T>::kFloat) {
+            if (blk != 0 && (blk & amask) == 0)
+                reanchor(i0);
+        }
         TC elv[V];
         bool hit = false;
         TP Pmid = P;
@@ -714,32 +773,10 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
         }
     }
 
-
-
     if constexpr (Tr<T>::kFloat) {
-        // Re-anchoring check: the walk ends at g = 2^(L-1); recompute those energies from the
-        // tables and compare with the incrementally updated ones.
-        F f0r, cxr, lt, le[V], lg[G];
-        unit_fields<T>(W, n, k, BL, unit, lane, f0r, cxr);
-        column_fields<F, V, G>(f0r, lane, lt, le, lg);
-        const TC *rowL = Mt + (size_t)(L - 1) * NB;
-        // differences in the column type (exact for close values; FP64 is slow on this part)
-        TC cmax = 0;
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            TC ev[V], mv[V];
-            vload<TC>(Es + (g * 32 + lane) * V, ev);
-            vload<TC>(rowL + (g * 32 + lane) * V, mv);
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                const TC fresh = (TC)((F)ev[e] + (le[e] + lt + lg[g])) + mv[e];
-                const TC dd = E[g * V + e] - fresh;
-                const TC ad = dd < 0 ? -dd : dd;
-                cmax = cmax > ad ? cmax : ad;
-            }
-        }
-        const F wl = __shfl_sync(kFull, f0r, B + L - 1);
-        double dmax = fmax((double)cmax, fabs((double)P - (double)(TP)(cxr + wl)));
+        // the walk ends at step 2^L - 1 (g = 2^(L-1)): the last segment's drift
+        reanchor((1 << L) - 1);
+        double dmax = (double)dl;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
             dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, o));
@@ -1013,10 +1050,13 @@ __global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs
 {
     using TC = typename Tr<T>::TC;
     using TP = typename Tr<T>::TP;
+    constexpr int kAncWarps = Tr<T>::kFloat ? kScanThreads / 32 : 1;  // float scans: re-anchoring base
     __shared__ TC stage_all[kScanThreads / 32][S * 32];
+    __shared__ __align__(16) TC anc_all[kAncWarps][Tr<T>::kFloat ? S * 32 : 1];
     __shared__ TP wsm_all[kScanThreads / 32][kMaxWalkBits];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     TC *stage = stage_all[warp];
+    TC *anc = anc_all[Tr<T>::kFloat ? warp : 0];
     TP *wsm = wsm_all[warp];
     TP Treg = (TP)0;
     // units take 0.1-30 ms here: one per claim keeps the end of a launch balanced
@@ -1024,7 +1064,7 @@ __global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs
         if constexpr (Tr<T>::kPack == 2)
             scan_unit_packed<S, RC, K1, ADDM, MINM>(a, d, inst, unit, Treg, lane, stage, wsm);
         else
-            scan_unit<T, S, RC, K1, ADDM, MINM>(a, d, inst, unit, Treg, lane, stage, wsm);
+            scan_unit<T, S, RC, K1, ADDM, MINM>(a, d, inst, unit, Treg, lane, stage, wsm, anc);
     });
 }
 

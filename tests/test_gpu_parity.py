@@ -231,6 +231,42 @@ def test_float_drift_within_margin(q):
     check_float(r, oracle.solve(Q, topk=4))
 
 
+def test_fp32_reanchoring_inside_long_walks(q):
+    """Walks of 2^14 Gray steps re-anchored every 2^10.  On an instance whose FP32 sums are all
+    exact (multiples of 2^-10 below 2^6) the rebuilt columns must equal the incrementally updated
+    ones, so the measured drift is exactly 0 (a wrong row set or a missing coupling in the rebuild
+    shows up here) and the results equal the oracle's; on an SK instance the drift is positive and
+    within the margin."""
+    Qd = (wl.upper_int(34, -60, 60, seed=7) / 1024.0).astype(np.float32)
+    r = q.solve(Qd, topk=8, fix_bits=4, fix_value=5, walk_bits=14)
+    i = r.info
+    assert (i["acc"], i["walk_bits"], i["anchor_bits"]) == ("f32", 14, 10), i
+    assert i["fp32_max_drift"] == 0.0
+    check_float(r, oracle.solve(Qd, topk=8, fix_bits=4, fix_value=5))
+    Q = wl.sk_float32(34, seed=34)
+    r = q.solve(Q, topk=8, fix_bits=4, fix_value=9, walk_bits=14)
+    i = r.info
+    assert (i["acc"], i["walk_bits"], i["anchor_bits"]) == ("f32", 14, 10), i
+    assert 0.0 < 2 * i["fp32_max_drift"] < 1e-3
+    check_float(r, oracle.solve(Q, topk=8, fix_bits=4, fix_value=9))
+
+
+def test_fp32_drift_guard_shortens_the_anchor_period(q):
+    """A candidate margin just below what the measured drift needs at 2^10-step anchoring makes the
+    host rescan with a shorter period (or, at the shortest, in FP64); the results stay exact."""
+    Q = wl.sk_float32(34, seed=35)
+    r0 = q.solve(Q, topk=4, fix_bits=4, walk_bits=14)
+    d10 = r0.info["fp32_max_drift"]
+    U = np.triu(Q.astype(np.float64)) + np.triu(Q.astype(np.float64).T, 1)
+    slack = 8.0 * 2.0 ** -24 * (1.0 + np.abs(U).sum())
+    margin = 0.999 * (2 * d10 + slack)
+    r = q.solve(Q, topk=4, fix_bits=4, walk_bits=14, margin=margin)
+    i = r.info
+    assert i["acc"] == "f64" or (i["acc"] == "f32" and i["anchor_bits"] < 10), i
+    assert i["passes"] >= 2
+    check_float(r, oracle.solve(Q, topk=4, fix_bits=4))
+
+
 # --- batched ----------------------------------------------------------------------------------
 
 def test_batched_matches_per_instance(q):
