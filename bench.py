@@ -9,7 +9,8 @@ take consecutive sub-cubes, so 2^fix_bits steps cover the whole instance.  The r
 per second (2^n / total time, the paper's convention, Sec. 5.3).
 
   python bench.py [--gpus N] [--steps K] [--warmup W]
-                  [--workload n50_int32|n44_fp32|maxcut_n48|sparse_n56|sparse_f32_n56|batched]
+                  [--workload n50_int32|n44_fp32|maxcut_n48|sparse_n56|sparse_f32_n56|window_n50|wide_n80|
+                              batched]
   python bench.py --impl reference ...   (the CPU oracle on the host cores, same workload)
 
 Under torchrun every rank takes disjoint sub-cubes (no data-path collective; weak scaling).
@@ -90,6 +91,22 @@ def make_workload(name: str, fix_bits: int | None):
                             "entries": "symmetric FP32: diagonal N(0,1), off-diagonal pairs present with "
                                        "probability 0.05, N(0,1)/sqrt(2.8)",
                             "step": f"one sub-cube of 2^{56 - fb} states (top {fb} code bits fixed)"})
+    if name == "window_n50":
+        fb = 7 if fix_bits is None else fix_bits
+        return dict(name=name, Q=wl.config5(), n=50, topk=0, fix_bits=fb, window=20000,
+                    metric="states/s (n=50 int32 dense QUBO, low-energy window)", unit="states/s", dtype="int32",
+                    config={"workload": "window_n50_delta20000", "n": 50, "seed": 5, "window": 20000,
+                            "entries": "upper-triangular int32 uniform [-32768, 32767]",
+                            "outputs": "every state with E <= E_min + 20000 of the sub-cube, (E, code) order",
+                            "step": f"one sub-cube of 2^{50 - fb} states (top {fb} code bits fixed)"})
+    if name == "wide_n80":
+        outer = 64 if fix_bits is None else (1 << fix_bits)
+        return dict(name=name, Q=wl.upper_int(80, -1000, 1000, seed=80), n=80, n_inner=40, outer=outer, topk=16,
+                    metric="states/s (n=80 int32 dense QUBO, sub-problems of 40 variables)", unit="states/s",
+                    dtype="int32",
+                    config={"workload": "wide_n80_inner40_top16", "n": 80, "n_inner": 40, "topk": 16, "seed": 80,
+                            "entries": "upper-triangular int32 uniform [-1000, 1000]",
+                            "step": f"{outer} consecutive outer values (2^40 states each, one batched launch)"})
     if name == "batched":
         return dict(name=name, Qs=wl.config4(), topk=0, metric="instances/s (4096 QUBOs, n uniform in 16..32)",
                     unit="instances/s", dtype="int32",
@@ -266,6 +283,9 @@ def run_reference(args, W):
         del per, t0
     else:
         Q, n = W["Q"], W["n"]
+        if W["name"] == "wide_n80":  # the sub-problem of outer value 0 (40 variables)
+            Q, _ = oracle.reduce(W["Q"], W["n_inner"], 0)
+            n = W["n_inner"]
         # each step: one sub-cube of about 1 s of oracle work
         fb = max(0, n - 28)
         t = time.perf_counter()
@@ -306,7 +326,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n50_int32",
-                    choices=["n50_int32", "n44_fp32", "maxcut_n48", "sparse_n56", "sparse_f32_n56", "batched"])
+                    choices=["n50_int32", "n44_fp32", "maxcut_n48", "sparse_n56", "sparse_f32_n56", "window_n50",
+                             "wide_n80", "batched"])
     ap.add_argument("--fix-bits", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-loop", action="store_true",
@@ -351,13 +372,19 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and W["name"] != "batched":
         # the oracle runs on the host cores before the GPU timing (it uses threads, no fork)
-        rate, dt, fb, cores = cpu_oracle_rate(W["Q"], W["n"], 12.0, W["fix_bits"])
-        rate1, dt1, fb1 = cpu_oracle_rate_one_core(W["Q"], W["n"], 3.0)
+        Qc, nc = W["Q"], W["n"]
+        if W["name"] == "wide_n80":
+            import oracle
+
+            Qc, _ = oracle.reduce(W["Q"], W["n_inner"], 0)  # the sub-problem of outer value 0
+            nc = W["n_inner"]
+        rate, dt, fb, cores = cpu_oracle_rate(Qc, nc, 12.0, 0)
+        rate1, dt1, fb1 = cpu_oracle_rate_one_core(Qc, nc, 3.0)
         cpu = {"value": rate, "unit": "states/s", "cores": cores, "kind": "oracle",
-               "sample": f"Gray-walk oracle on one sub-cube of 2^{W['n'] - fb} states of the same instance "
-                         f"({dt:.1f} s)",
+               "sample": f"Gray-walk oracle on one sub-cube of 2^{nc - fb} states of the same instance "
+                         + ("(outer value 0's sub-problem) " if nc != W["n"] else "") + f"({dt:.1f} s)",
                "one_core": {"value": rate1, "unit": "states/s",
-                            "sample": f"one thread, one sub-cube of 2^{W['n'] - fb1} states ({dt1:.1f} s)"}}
+                            "sample": f"one thread, one sub-cube of 2^{nc - fb1} states ({dt1:.1f} s)"}}
         log(f"cpu oracle: {rate:.3e} states/s on {cores} threads")
 
     launches = 0
@@ -410,6 +437,60 @@ def main():
                 q.solve(Q, states_cap=64, stream=stream)
             torch.cuda.synchronize(dev)
             loop_rate = len(mats) / (time.perf_counter() - t)
+    elif W["name"] in ("window_n50", "wide_n80"):
+        # host-buffer entry points (no device-resident form): value = states / the device time the
+        # library measures with CUDA events on the launching stream (tables, scan, reduction);
+        # e2e = states / wall time of the calls
+        loop_rate = None
+        Q = W["Q"]
+        if W["name"] == "window_n50":
+            my = q.shard_subcubes(W["fix_bits"], world, rank)
+
+            def call(s):
+                cnt, codes, E, info = q.solve_window(Q, W["window"], cap=1 << 16, fix_bits=W["fix_bits"],
+                                                     fix_value=my[s % len(my)], stream=stream)
+                info["window_count"] = cnt
+                return info
+        else:
+            n_outer_vals = 1 << (W["n"] - W["n_inner"])
+
+            def call(s):
+                begin = ((s * world + rank) * W["outer"]) % n_outer_vals
+                r = q.solve_wide(Q, W["n_inner"], outer_begin=begin, outer_count=W["outer"], topk=W["topk"],
+                                 stream=stream)
+                return r.info
+        for s in range(args.warmup):
+            call(s)
+        barrier()
+        sampler.start()
+        infos = []
+        for s in range(args.steps):
+            flush_l2(l2buf)
+            infos.append(call(args.warmup + s))
+        barrier()
+        clocks = sampler.stop()
+        t_dev = sum(i["seconds_gpu"] for i in infos)
+        states_per_step = infos[0]["states_scanned"]
+        units = sum(i["states_scanned"] for i in infos)
+        launches = sum(i["kernel_launches"] for i in infos)
+        scan_s = [i["seconds_scan"] for i in infos]
+        # e2e: the same calls timed by the host clock (after the clock sampler has stopped, as for
+        # the other workloads)
+        t = time.perf_counter()
+        walls = []
+        for s in range(args.steps):
+            tc = time.perf_counter()
+            call(args.warmup + s)
+            walls.append(time.perf_counter() - tc)
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter() - t
+        log("e2e call walls (s): " + " ".join(f"{w:.4f}" for w in walls))
+        e2e_val = units / t_wall
+        h2d, d2h = infos[-1]["h2d_bytes"], infos[-1]["d2h_bytes"]
+        e2e_note = ("qubo_solve_window" if W["name"] == "window_n50" else "qubo_solve_wide") + \
+            " from host buffers (host preparation and copies inside every step)"
+        if W["name"] == "window_n50":
+            W["config"]["window_states_per_step"] = [i["window_count"] for i in infos]
     else:
         loop_rate = None
         Q, n, topk, fb = W["Q"], W["n"], W["topk"], W["fix_bits"]
@@ -464,6 +545,8 @@ def main():
         dist.all_reduce(ee, op=dist.ReduceOp.SUM)
         e2e_val = float(ee.item())
     value = units * world / t_max
+    if W["name"] in ("window_n50", "wide_n80"):
+        W["config"]["value_timing"] = "device time of each call's kernels (CUDA events on the launching stream)"
 
     # roofline of the enumeration kernel: algorithmic ALU ops per launch / its event-timed duration
     mean_scan = sum(scan_s) / len(scan_s)

@@ -1693,8 +1693,10 @@ int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
     // One accumulator for the batch: packed 16-bit lanes, else FP32 lanes, when every
     // instance's plan is exact in it (instances evaluated directly need nothing).
     for (const Acc alt_acc : {ACC_I16P, ACC_I32F}) {
-        if (acc != ACC_I32 || !(alt_acc == ACC_I16P ? i16p_allowed() : i32f_allowed()))
+        if (acc != ACC_I32)
             break;
+        if (!(alt_acc == ACC_I16P ? i16p_allowed() : i32f_allowed()))
+            continue;
         std::vector<HostInst> alt = hs;
         int v2 = pick_variant(alt_acc, -1);
         int tv = 0, tw = 0;

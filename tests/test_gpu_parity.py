@@ -467,6 +467,19 @@ def test_window_matches_oracle(q, n, window):
     assert cnt == ocnt and np.array_equal(codes, ocodes) and np.array_equal(E, oE)
 
 
+@pytest.mark.parametrize("fix_value", [0, 12345, (1 << 22) - 1])
+def test_window_n50_subcubes(q, fix_value):
+    """The benchmark's window (20000 above the minimum) on the n = 50 instance, on 2^28-state
+    sub-cubes: the states in the window are the oracle's, in (E, code) order."""
+    Q = wl.config5()
+    cnt, codes, E, info = q.solve_window(Q, 20000, fix_bits=22, fix_value=fix_value)
+    o = oracle.solve(Q, topk=4096, cap=1, fix_bits=22, fix_value=fix_value)
+    sel = o.topk_E <= o.min + 20000
+    assert not sel.all()
+    assert cnt == int(sel.sum()) and np.array_equal(codes, o.topk[sel]) and np.array_equal(E, o.topk_E[sel])
+    assert info["states_scanned"] == 1 << 28
+
+
 def test_window_float(q):
     Q = wl.sk_float32(20, seed=41)
     cnt, codes, E, info = q.solve_window(Q, 0.5)

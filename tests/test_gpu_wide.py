@@ -122,3 +122,45 @@ def test_wide_rejects_bad_ranges(q):
         with pytest.raises(q.QuboError) as e:
             q.solve_wide(Q, **kw)
         assert e.value.status == q.QUBO_ERR_ARG
+
+
+def test_wide_benchmark_shape_closed_form(q, monkeypatch):
+    """The benchmark's launch shape (n = 80, 40 inner variables, 64 outer values in one batched
+    launch, top 16) on an instance whose inner variables couple only to outer ones: each
+    sub-problem's minimum is c + sum_i min(0, R_ii) (R, c from oracle.reduce) and its tie count
+    2^(number of zero R_ii).  The FP32-lane kernel is forced (the factored and packed scans would
+    take such sub-problems)."""
+    monkeypatch.setenv("QUBO_NO_I32Z", "1")
+    monkeypatch.setenv("QUBO_NO_I16P", "1")
+    rng = np.random.default_rng(81)
+    n, m, base = 80, 40, 1000
+    Q = np.triu(rng.integers(-1000, 1000, size=(n, n))).astype(np.int32)
+    Q[:m, :m] = np.diag(np.diag(Q)[:m])
+    r = q.solve_wide(Q, m, outer_begin=base, outer_count=64, topk=16, states_cap=64)
+    best, ties = None, 0
+    for v in range(base, base + 64):
+        R, c = oracle.reduce(Q, m, v)
+        d = np.diag(R).astype(np.int64)
+        e = c + int(np.minimum(d, 0).sum())
+        if best is None or e < best:
+            best, ties = e, 0
+        if e == best:
+            ties += 1 << int((d == 0).sum())
+    assert r.min == best and r.n_ties == ties
+    assert r.info["acc"] == "i32f" and r.info["states_scanned"] == 64 << 40
+
+
+def test_wide_benchmark_instance_codes(q):
+    """The benchmark instance and launch shape: each of the 16 returned states has the reported
+    energy (its outer value's sub-problem from oracle.reduce, direct energy), they come in (E, code)
+    order, and the sub-problem holding the minimum, solved alone (the unbatched path), agrees."""
+    Q = wl.upper_int(80, -1000, 1000, seed=80)
+    r = q.solve_wide(Q, 40, outer_begin=0, outer_count=64, topk=16)
+    E = r.topk_E.tolist()
+    for code, e in zip(r.topk, E):
+        R, c = oracle.reduce(Q, 40, code >> 40)
+        assert oracle.energy(R, code & ((1 << 40) - 1)) + c == e
+    assert list(zip(E, r.topk)) == sorted(zip(E, r.topk)) and E[0] == r.min
+    v = r.topk[0] >> 40
+    r1 = q.solve_wide(Q, 40, outer_begin=v, outer_count=1, topk=1)
+    assert r1.min == r.min and r1.topk[0] == r.topk[0]
