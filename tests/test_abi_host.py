@@ -112,3 +112,25 @@ def test_ncu_summary_arithmetic(tmp_path):
     assert s["issue_roofline_states_per_s"] == 152 * 128 * 2070e6
     assert s["dram_bytes_per_state"] == 1024 / 2**36
     assert s["states_per_s_under_ncu"] == 2**36 / 1e-3
+
+
+def build_c_client(q, out_dir):
+    """Compile tests/c_abi_client.c with the system C compiler against include/qubo.h and link it
+    to the in-tree libqubo.so (no Python between the client and the library)."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("cc") or shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(q.LIB_PATH)
+    exe = os.path.join(str(out_dir), "c_abi_client")
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-O2", "-I", os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "c_abi_client.c"), "-L", libdir, "-lqubo",
+                        f"-Wl,-rpath,{libdir}", "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+def test_c_client_compiles_and_links_against_the_header(q, tmp_path):
+    assert os.path.exists(build_c_client(q, tmp_path))

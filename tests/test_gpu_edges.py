@@ -97,3 +97,17 @@ def test_allocation_failure_is_reported_and_recovers(q, monkeypatch):
         assert e.value.status == q.QUBO_ERR_NOMEM
     monkeypatch.delenv("QUBO_FAIL_ALLOC")
     check_int(q.solve(Q, topk=4), oracle.solve(Q, topk=4))
+
+
+def test_plain_c_client(q, tmp_path):
+    """tests/c_abi_client.c, a C program linked to libqubo.so: a dense planted n = 34 instance
+    (unique minimiser, closed-form minimum) and the all-zero n = 20 instance (truncated tie set,
+    exact count) through qubo_solve."""
+    import subprocess
+
+    from test_abi_host import build_c_client
+
+    exe = build_c_client(q, tmp_path)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "c_abi_client ok" in r.stdout
