@@ -263,8 +263,6 @@ def run_reference(args, W):
         Qs = W["Qs"]
         order = np.random.default_rng(0).permutation(len(Qs))
         # bounded sample: instances solved one by one until each step takes ~2 s
-        per = []
-        t0 = time.perf_counter()
         i = 0
         times = []
         for s in range(args.warmup + args.steps):
@@ -280,7 +278,6 @@ def run_reference(args, W):
         value = sum(c for c, _ in times) / sum(t for _, t in times)
         sample = "instances of the 4096-instance batch, solved one by one on the host cores"
         ms = 1000 * sum(t for _, t in times) / len(times)
-        del per, t0
     else:
         Q, n = W["Q"], W["n"]
         if W["name"] == "wide_n80":  # the sub-problem of outer value 0 (40 variables)
@@ -550,10 +547,7 @@ def main():
 
     # roofline of the enumeration kernel: algorithmic ALU ops per launch / its event-timed duration
     mean_scan = sum(scan_s) / len(scan_s)
-    if W["name"] == "batched":
-        per_launch_states = states_per_step
-    else:
-        per_launch_states = states_per_step
+    per_launch_states = states_per_step  # one enumeration launch per step
     acc = infos[0].get("acc", "i32")
     W["dtype"] = ACC_DTYPE.get(acc, acc)
     # the packed scan holds two 16-bit columns in each 32-bit lane: twice the lane-ops per cycle

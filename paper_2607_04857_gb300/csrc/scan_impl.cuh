@@ -506,7 +506,6 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
     using F = typename Tr<T>::FU;
     using TC = typename Tr<T>::TC;
     using TP = typename Tr<T>::TP;
-    constexpr bool kIntCols = std::is_integral_v<TC>;
     constexpr int V = VecOf<TC>::V;
     constexpr int G = S / V;
     constexpr int LOGV = ilog2c(V);
