@@ -31,6 +31,9 @@ constexpr unsigned long long kBatchGraphRecords = 1ull << 18;  // candidate reco
 constexpr double kDefaultMargin = 1e-3;
 constexpr int kTargetUnitsLog2 = 15;   // aim for >= 2^15 work units per scan
 constexpr int kDefaultMaxWalkBits = 12;
+// Integers in FP32 lanes: 2^14-step walks (n=50: 0.7% faster than 2^12) when the plan stays exact
+// in FP32 lanes, else the default length is tried.
+constexpr int kI32FMaxWalkBits = 14;
 // FP32 scans re-anchor every 2^kFloatAnchorBits walk steps (and at every unit start): 2^10 Gray
 // steps keep the measured drift (2.4e-4 on the n=44 SK instance) well inside the budget of the
 // default 1e-3 candidate margin; the drift guard shortens the period when it does not.  The walk
@@ -189,6 +192,7 @@ int plan(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bi
         L = walk_bits;
     else
         L = std::max(rc + 1, std::min(h.acc == ACC_F32          ? kFloatMaxWalkBits
+                                      : h.acc == ACC_I32F       ? kI32FMaxWalkBits
                                       : acc_factored(h.acc) ? kZMaxWalkBits
                                                             : kDefaultMaxWalkBits,
                                       free_bits - h.B - kTargetUnitsLog2));
@@ -223,17 +227,25 @@ int scan_variant(Acc acc = ACC_I32)
 // The variant a run uses: the caller's (tuned) choice, else the accumulator's default.
 int pick_variant(Acc acc, int requested) { return requested >= 0 ? requested : scan_variant(acc); }
 
-// Integer energies can be scanned exactly in FP32 lanes when every column energy, table row and
-// clamped threshold stays below 2^24 in magnitude.  With nf = B + L non-fixed variables, every
+void col_range_exact(const HostInst &h, int64_t &lo, int64_t &hi);
+int64_t walked_energy_max(const HostInst &h);
+
+// Integer energies can be scanned exactly in FP32 lanes when every value held in an FP32 lane stays
+// below 2^24 in magnitude: the column values, the stored tables (E_s, the walked rows M_r with the
+// register rows' fixed couplings folded in, E_L) and the clamped per-step threshold.  The unit
+// fields, c(x_f) and the prefix part are int32.  The per-step threshold is clamped to +-C with
+// C = max|column| + max|E_L| + 1, which leaves every decision unchanged, so |threshold - E_L| <=
+// C + max|E_L| must stay below 2^24.  Quick accept: with nf = B + L non-fixed variables, every
 // column value is a signed subset sum of the entries touching a non-fixed variable (S_nf bounds
-// it) and every E_L value one of the entries among walked variables (S_ww); the per-step
-// threshold is clamped to +-(S_nf + S_ww + 1), which leaves every decision unchanged, so
-// |threshold - E_L| <= S_nf + 2 S_ww + 1 must stay below 2^24.
+// it) and every E_L value one of the entries among walked variables (S_ww).  Otherwise the
+// column range is computed exactly per suffix pattern, E_L by enumeration, and every table row
+// by the sum of |U| over its entries.
 bool i32f_exact(const HostInst &h, int32_t *clampC)
 {
     if (h.small || h.is_float)
         return false;
-    const int n = h.n, nf = h.B + h.L;
+    const int n = h.n, nf = h.B + h.L, B = h.B, rc = variant_reg_rows(h);
+    constexpr double kLimit = 16777216.0;
     double s_nf = 0.0, s_ww = 0.0;
     for (int i = 0; i < n; ++i)
         for (int j = i; j < n; ++j) {
@@ -243,9 +255,28 @@ bool i32f_exact(const HostInst &h, int32_t *clampC)
             if (i >= h.B && j < nf)
                 s_ww += a;
         }
-    if (s_nf + 2.0 * s_ww + 2.0 >= 16777216.0)
+    if (s_nf + 2.0 * s_ww + 2.0 < kLimit) {
+        *clampC = (int32_t)(s_nf + s_ww + 1.0);
+        return true;
+    }
+    auto U = [&](int i, int j) { return i < j ? h.Ui[(size_t)i * n + j] : h.Ui[(size_t)j * n + i]; };
+    for (int r = B; r < nf; ++r) {  // table row r: M_r[j] (+ w_r for a register row)
+        double row = 0.0;
+        for (int b = 0; b < B; ++b)
+            row += std::fabs((double)U(r, b));
+        if (r < B + rc)
+            for (int f = nf; f < n; ++f)
+                row += std::fabs((double)U(r, f));
+        if (row >= kLimit)
+            return false;
+    }
+    int64_t lo, hi;
+    col_range_exact(h, lo, hi);
+    const double el = (double)walked_energy_max(h);
+    const double C = (double)std::max(-lo, hi) + el + 1.0;
+    if (C + el + 1.0 >= kLimit)
         return false;
-    *clampC = (int32_t)(s_nf + s_ww + 1.0);
+    *clampC = (int32_t)C;
     return true;
 }
 
@@ -255,17 +286,14 @@ bool i32f_allowed()
     return !(v && v[0] == '1');
 }
 
-// Integer energies can be scanned as packed 16-bit lanes when every column value the plan's
-// kernel holds lies in [-32768, 32767].  For suffix pattern j, a column holds
+// Range of every column value the plan's packed or FP32-lane kernel holds.  For suffix pattern j
+// a column holds
 //   E_s(j) + sum_{i outside the suffix} x_i c_i(j) + sum_{r < RC} x_r w_r,
 // with c_i(j) = sum_{b in j} U_bi, w_r = sum_{f fixed} x_f U_rf (the couplings of the register
 // rows folded into their table rows).  Its range over all outside bits is bounded by taking every
-// c_i(j) and every U_rf at its sign's extreme, computed exactly for each j.  The scan's
-// threshold arithmetic (threshold - prefix - E_L + 2^15 in int32) asks beta < 2^29 as well.
-bool i16p_exact(HostInst &h)
+// c_i(j) and every U_rf at its sign's extreme, computed exactly for each j (O(2^B n)).
+void col_range_exact(const HostInst &h, int64_t &lo, int64_t &hi)
 {
-    if (h.small || h.is_float || h.beta >= 536870912.0)
-        return false;
     const int n = h.n, B = h.B, rc = variant_reg_rows(h), nf = h.B + h.L;
     auto U = [&](int i, int j) { return i < j ? h.Ui[(size_t)i * n + j] : h.Ui[(size_t)j * n + i]; };
     int64_t wpos = 0, wneg = 0;
@@ -274,22 +302,11 @@ bool i16p_exact(HostInst &h)
             const int64_t u = U(r, f);
             (u > 0 ? wpos : wneg) += u;
         }
-    // quick accept: the sum of |U| over every entry a column can contain
-    int64_t crude = wpos - wneg;
-    for (int b = 0; b < B; ++b)
-        for (int i = b; i < n; ++i) {
-            const int64_t u = U(b, i);
-            crude += u < 0 ? -u : u;
-        }
-    if (crude <= 32767) {
-        h.col_lo = (int32_t)-crude;
-        h.col_hi = (int32_t)crude;
-        return true;
-    }
-    // exact per-pattern range: c[j][i] for every variable i, built from j without its lowest bit
+    // c[j][i] for every variable i, built from j without its lowest bit
     const size_t NB = 1ull << B;
     std::vector<int64_t> c(NB * n, 0), es(NB, 0);
-    int64_t lo = 0, hi = 0;
+    lo = 0;
+    hi = 0;
     for (size_t j = 1; j < NB; ++j) {
         const int b = __builtin_ctzll(j);
         const size_t jp = j & (j - 1);
@@ -306,6 +323,54 @@ bool i16p_exact(HostInst &h)
     }
     lo += wneg;
     hi += wpos;
+}
+
+// Largest |E_L(g)| over the 2^L walked patterns (the energy of the walked variables alone),
+// enumerated in Gray order with a running field per variable.
+int64_t walked_energy_max(const HostInst &h)
+{
+    const int n = h.n, B = h.B, L = h.L;
+    auto U = [&](int i, int j) { return i < j ? h.Ui[(size_t)i * n + j] : h.Ui[(size_t)j * n + i]; };
+    std::vector<int64_t> field(L, 0);  // sum of U over the set walked variables other than r
+    std::vector<int> x(L, 0);
+    int64_t e = 0, m = 0;
+    for (uint64_t i = 1; i < (1ull << L); ++i) {
+        const int r = __builtin_ctzll(i);
+        const int s = x[r] ? -1 : 1;
+        e += s * (U(B + r, B + r) + field[r]);
+        x[r] ^= 1;
+        for (int t = 0; t < L; ++t)
+            if (t != r)
+                field[t] += s * U(B + r, B + t);
+        m = std::max(m, e < 0 ? -e : e);
+    }
+    return m;
+}
+
+// Integer energies can be scanned as packed 16-bit lanes when every column value the plan's
+// kernel holds lies in [-32768, 32767].  The scan's threshold arithmetic (threshold - prefix -
+// E_L + 2^15 in int32) asks beta < 2^29 as well.
+bool i16p_exact(HostInst &h)
+{
+    if (h.small || h.is_float || h.beta >= 536870912.0)
+        return false;
+    const int n = h.n, B = h.B, rc = variant_reg_rows(h), nf = h.B + h.L;
+    auto U = [&](int i, int j) { return i < j ? h.Ui[(size_t)i * n + j] : h.Ui[(size_t)j * n + i]; };
+    // quick accept: the sum of |U| over every entry a column can contain
+    int64_t crude = 0;
+    for (int r = B; r < B + rc; ++r)
+        for (int f = nf; f < n; ++f)
+            crude += std::llabs(U(r, f));
+    for (int b = 0; b < B; ++b)
+        for (int i = b; i < n; ++i)
+            crude += std::llabs(U(b, i));
+    if (crude <= 32767) {
+        h.col_lo = (int32_t)-crude;
+        h.col_hi = (int32_t)crude;
+        return true;
+    }
+    int64_t lo, hi;
+    col_range_exact(h, lo, hi);
     if (lo < -32768 || hi > 32767)
         return false;
     h.col_lo = (int32_t)lo;
@@ -453,6 +518,11 @@ int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int wal
             h.variant = pick_variant(h.acc, variant_req);
             if (plan(h, fix_bits, fix_value, split_k, walk_bits) == QUBO_OK && i32f_exact(h, &h.clampC))
                 chosen = ACC_I32F;
+            else if (split_k <= 0 && walk_bits <= 0 && h.L > kDefaultMaxWalkBits &&
+                     plan(h, fix_bits, fix_value, 0, kDefaultMaxWalkBits) == QUBO_OK && i32f_exact(h, &h.clampC)) {
+                chosen = ACC_I32F;  // a shorter walk keeps fewer values in the lanes
+                walk_bits = kDefaultMaxWalkBits;
+            }
         }
         h.acc = chosen;
     }

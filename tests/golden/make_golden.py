@@ -2,6 +2,8 @@
 
     python tests/golden/make_golden.py cfg2      # n=36 int32, min + ties + 16 lowest (~2 min, 8 cores)
     python tests/golden/make_golden.py cfg4      # 4096 batched instances (~1 h, 8 cores)
+    python tests/golden/make_golden.py cfg5_sub  # n=50, one 2^40-state sub-cube (~1 h, 8 cores)
+    python tests/golden/make_golden.py cfg3_sub  # n=44 FP32, one 2^40-state sub-cube (~1 h, 8 cores)
 
 The inputs come from the seeded generators in paper_2607_04857_gb300/workloads.py; the paper's
 benchmark matrices are uniformly random (Sec. 5.3), so the instances are synthetic stand-ins of
@@ -53,6 +55,29 @@ def cfg4():
         json.dump(out, fh, separators=(",", ":"))
 
 
+def subcube(name, Q, n, seed, generator, fix_bits, fix_value, is_float):
+    """One sub-cube (top fix_bits code bits = fix_value) of a benchmark instance: min, exact tie
+    count, up to 4096 tie codes, the 16 lowest states."""
+    t = time.time()
+    r = oracle.solve(Q, method=oracle.GRAY, topk=16, cap=4096, fix_bits=fix_bits, fix_value=fix_value)
+    conv = float if is_float else int
+    out = {"generator": generator, "n": n, "seed": seed, "fix_bits": fix_bits, "fix_value": fix_value,
+           "oracle": "gray" + (" (candidates rescored by the direct FP64 evaluator)" if is_float else ""),
+           "seconds": round(time.time() - t, 1), "min": conv(r.min), "n_ties": r.n_ties,
+           "ties": [int(c) for c in r.ties], "topk": [int(c) for c in r.topk],
+           "topk_E": [conv(e) for e in r.topk_E]}
+    with open(os.path.join(HERE, name), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
+def cfg5_sub():
+    subcube("cfg5_n50_sub40.json", wl.config5(), 50, 5, "workloads.config5()", 10, 613, False)
+
+
+def cfg3_sub():
+    subcube("cfg3_n44_sub40.json", wl.config3(), 44, 3, "workloads.config3()", 4, 9, True)
+
+
 if __name__ == "__main__":
     for what in sys.argv[1:]:
-        {"cfg2": cfg2, "cfg4": cfg4}[what]()
+        {"cfg2": cfg2, "cfg4": cfg4, "cfg5_sub": cfg5_sub, "cfg3_sub": cfg3_sub}[what]()

@@ -7,6 +7,9 @@ independent kernels of the library on the same step (the dense scans against the
 FP32 with FP64 rescoring against the plain FP64 scan), and every returned state's energy is
 re-evaluated directly by the oracle.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -122,3 +125,34 @@ def test_sparse_f32_n56_bench_step_factored_vs_dense(q, monkeypatch):
     assert d.info["acc"] == "f32"
     same_float(r, d)
     energies_direct(Q, r)
+
+
+def load_golden(name):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    with open(path) as fh:
+        return json.load(fh)
+
+
+def test_n50_bench_plan_subcube_golden(q):
+    """A 2^40-state sub-cube of the n = 50 instance (the benchmark's plan: FP32 lanes, 14 walked
+    bits, 9 suffix bits) against the oracle's stored result (tests/golden/make_golden.py)."""
+    g = load_golden("cfg5_n50_sub40.json")
+    Q = wl.config5()
+    r = q.solve(Q, topk=16, states_cap=4096, fix_bits=g["fix_bits"], fix_value=g["fix_value"])
+    i = r.info
+    assert (i["acc"], i["walk_bits"], i["suffix_bits"]) == ("i32f", 14, 9), i
+    assert r.min == g["min"] and r.n_ties == g["n_ties"]
+    assert r.ties.tolist() == g["ties"] and r.topk.tolist() == g["topk"] and r.topk_E.tolist() == g["topk_E"]
+
+
+def test_n44_fp32_bench_plan_subcube_golden(q):
+    """A 2^40-state sub-cube of the n = 44 FP32 instance (the benchmark's plan: 2^14-step walks
+    re-anchored every 2^10 steps) against the oracle's stored FP64 result."""
+    g = load_golden("cfg3_n44_sub40.json")
+    Q = wl.config3()
+    r = q.solve(Q, topk=16, states_cap=4096, fix_bits=g["fix_bits"], fix_value=g["fix_value"])
+    i = r.info
+    assert (i["acc"], i["walk_bits"], i["anchor_bits"]) == ("f32", 14, 10), i
+    assert abs(r.min - g["min"]) <= FLOAT_RTOL * max(1.0, abs(g["min"]))
+    assert r.n_ties == g["n_ties"] and r.ties.tolist() == g["ties"] and r.topk.tolist() == g["topk"]
+    assert np.allclose(r.topk_E, g["topk_E"], rtol=FLOAT_RTOL, atol=FLOAT_RTOL)

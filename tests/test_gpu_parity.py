@@ -290,15 +290,15 @@ def test_batched_float(q):
 # --- the n=50 configuration, sampled ---------------------------------------------------------
 
 def test_n50_sampled_subcubes(q):
-    """The n=50 instance with the plan the benchmark uses (the default variant, 12 walked bits):
+    """The n=50 instance with the plan the benchmark uses (the default variant, 14 walked bits):
     sub-cubes of 2^24 states at 64 sampled prefixes, each checked against the oracle."""
     Q = wl.config5()
     rng = np.random.default_rng(50)
     for v in rng.integers(0, 1 << 26, size=64):
-        r = q.solve(Q, topk=16, fix_bits=26, fix_value=int(v), walk_bits=12)
+        r = q.solve(Q, topk=16, fix_bits=26, fix_value=int(v), walk_bits=14)
         i = r.info
-        # the benchmark's 2^43-state steps plan 12 walked bits with the default variant too
-        assert i["acc"] == "i32f" and i["walk_bits"] == 12  # exact in FP32 lanes for this plan
+        # the benchmark's 2^43-state steps plan 14 walked bits with the default variant too
+        assert i["acc"] == "i32f" and i["walk_bits"] == 14  # exact in FP32 lanes for this plan
         assert i["split_k"] + i["walk_bits"] + i["suffix_bits"] == 50
         check_int(r, oracle.solve(Q, topk=16, fix_bits=26, fix_value=int(v)))
 
@@ -518,30 +518,62 @@ def test_int32_kernel_when_fp32_lanes_disabled(q, monkeypatch):
         check_int(r, oracle.solve(Q, topk=16))
 
 
-def test_fp32_lanes_rejected_beyond_2_24(q):
-    """Entries of +-2^20: the partial sums exceed 2^24, so the int32 kernel must run."""
-    Q = wl.upper_int(21, -(1 << 20), 1 << 20, seed=8)
-    r = q.solve(Q, topk=8)
-    assert r.info["acc"] == "i32"
-    check_int(r, oracle.solve(Q, topk=8))
-
-
 def plan_bound(Q, suffix_bits, walk_bits):
-    """S_nf + 2 S_ww of a plan: the largest magnitude the FP32-lane scan would form."""
+    """S_nf + 2 S_ww of a plan: the crude bound on the magnitudes the FP32-lane scan forms."""
     U = np.abs(oracle.fold(Q)).astype(np.float64)
     nf = suffix_bits + walk_bits
     return U[:nf, :].sum() + 2 * U[suffix_bits:nf, suffix_bits:nf].sum()
 
 
-@pytest.mark.parametrize("lim", [60000, 95000, 100000, 105000, 120000])
+def fp32_lanes_fit(Q, B, L, RC):
+    """Whether every value an FP32-lane scan with B suffix bits, L walked bits and RC register
+    rows holds stays below 2^24: the crude bound, else the exact column range (every outside
+    coupling sum at its sign's extreme, per suffix pattern), the walked energies E_L by brute
+    force, and each table row's sum of |U|."""
+    if plan_bound(Q, B, L) + 2 < 2**24:
+        return True
+    U = oracle.fold(np.asarray(Q).astype(np.int64)).astype(np.int64)
+    nf = B + L
+    W = np.triu(U, 1) + np.triu(U, 1).T
+    for r in range(B, nf):
+        row = np.abs(W[r, :B]).sum() + (np.abs(W[r, nf:]).sum() if r < B + RC else 0)
+        if row >= 2**24:
+            return False
+    j = np.arange(1 << B, dtype=np.int64)
+    J = (j[:, None] >> np.arange(B)) & 1
+    Es = J @ np.diag(U)[:B] + ((J @ W[:B, :B]) * J).sum(1) // 2
+    c = J @ W[:B, B:]
+    wr = W[B:B + RC, nf:]
+    hi = int((Es + np.clip(c, 0, None).sum(1)).max() + np.clip(wr, 0, None).sum())
+    lo = int((Es + np.clip(c, None, 0).sum(1)).min() + np.clip(wr, None, 0).sum())
+    g = np.arange(1 << L, dtype=np.int64)
+    G = (g[:, None] >> np.arange(L)) & 1
+    Uw = U[B:nf, B:nf]
+    EL = G @ np.diag(Uw) + ((G @ np.triu(Uw, 1)) * G).sum(1)
+    el = int(np.abs(EL).max())
+    C = max(-lo, hi, 0) + el + 1
+    return C + el + 1 < 2**24
+
+
+def test_fp32_lanes_rejected_when_out_of_range(q):
+    """Entries of +-2^22: column values exceed 2^24, so the int32 kernel must run."""
+    Q = wl.upper_int(21, -(1 << 22), 1 << 22, seed=8)
+    r = q.solve(Q, topk=8)
+    assert not fp32_lanes_fit(Q, r.info["suffix_bits"], r.info["walk_bits"], 4)
+    assert r.info["acc"] == "i32"
+    check_int(r, oracle.solve(Q, topk=8))
+
+
+@pytest.mark.parametrize("lim", [60000, 120000, 350000, 400000, 1000000])
 def test_fp32_lanes_chosen_exactly_when_bounded(q, lim, monkeypatch):
-    """Entries sized around the 2^24 bound: the FP32-lane scan is used exactly when the run's
-    plan keeps S_nf + 2 S_ww + 2 below 2^24, and the results are bit-exact either way."""
+    """Entries sized across the 2^24 bound (the crude S_nf + 2 S_ww bound alone for the
+    smallest, the exact range beyond it): the FP32-lane scan is used exactly when the run's plan
+    keeps every value it forms below 2^24, and the results are bit-exact either way."""
     monkeypatch.setenv("QUBO_NO_I16P", "1")
     Q = wl.upper_int(27, -lim, lim, seed=9)
     r = q.solve(Q, topk=8, walk_bits=5)  # the same plan for either kernel (both 9 suffix bits)
     check_int(r, oracle.solve(Q, topk=8))
     i = r.info
     assert (i["suffix_bits"], i["walk_bits"]) == (9, 5)
-    expect = "i32f" if plan_bound(Q, 9, 5) + 2 < 2**24 else "i32"
+    expect = "i32f" if fp32_lanes_fit(Q, 9, 5, 4) else "i32"  # default variant: 4 register rows
     assert i["acc"] == expect
