@@ -193,16 +193,16 @@ def kernel_source_hash(acc: str) -> str:
     return h.hexdigest()[:16]
 
 
-def profile_counters(acc: str):
+def profile_counters(acc: str, workload: str):
     """ncu counters committed under profiles/ for the scan kernel, if they were taken on the
-    current kernel source; else None."""
+    current kernel source in this workload's plan; else None."""
     try:
         with open(PROFILE_JSON) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return None
     e = d.get(acc)
-    if not e or e.get("kernel_hash") != kernel_source_hash(acc):
+    if not e or e.get("kernel_hash") != kernel_source_hash(acc) or e.get("workload") != workload:
         return None
     return e
 
@@ -569,7 +569,7 @@ def main():
                              f" (factored scan: 2/2^Z + 2/2^B, Z = {infos[0]['zero_rows']}, B = {infos[0]['suffix_bits']})")}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (halves * sms * LANES_PER_SM * clocks["sm_mhz"] * 1e-3)
-    prof = profile_counters(acc)
+    prof = profile_counters(acc, W["name"])
     if prof:
         # DRAM bytes per launch, scaled from the captured launch by the states it processed
         roof["traffic"] = prof["dram_bytes_per_state"] * per_launch_states

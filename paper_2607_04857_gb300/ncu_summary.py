@@ -2,12 +2,14 @@
 uses: instructions per state, the issue roofline, DRAM bytes per state, issue activity.
 
     python -m paper_2607_04857_gb300.ncu_summary CSV --states 2^36 [--sms 152 --clock-mhz 2070]
-        [--acc i32f --variant 1 --command "..." --update profiles/scan_kernel_counters.json]
+        [--acc i32f --variant 1 --workload n50_int32 --command "..."
+         --update profiles/scan_kernel_counters.json]
 
 CSV is the `--csv --log-file` output of `ncu --metrics ...` for one launch (`-c 1`).  With
 --update, the entry of accumulator --acc in the counters file is replaced, tagged with the hash of
-the kernel sources the capture was taken on (bench.kernel_source_hash), so the benchmark only
-uses counters that still match the code.
+the kernel sources the capture was taken on (bench.kernel_source_hash) and the benchmark workload
+whose plan it was taken in, so the benchmark only uses counters that still match the code, on that
+workload.
 """
 from __future__ import annotations
 
@@ -55,6 +57,7 @@ def main(argv=None) -> int:
     ap.add_argument("--clock-mhz", type=float, default=2070.0)
     ap.add_argument("--acc")
     ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--workload", default="")
     ap.add_argument("--command", default="")
     ap.add_argument("--update")
     a = ap.parse_args(argv)
@@ -69,7 +72,8 @@ def main(argv=None) -> int:
         import bench
 
         d = json.load(open(a.update)) if os.path.exists(a.update) else {}
-        d[a.acc] = {"kernel_hash": bench.kernel_source_hash(a.acc), "variant": a.variant, "captured_states": states,
+        d[a.acc] = {"kernel_hash": bench.kernel_source_hash(a.acc), "workload": a.workload, "variant": a.variant,
+                    "captured_states": states,
                     "inst_per_state": round(s["inst_per_state"], 7),
                     "dram_bytes_per_launch": s["dram_bytes_per_launch"],
                     "dram_bytes_per_state": s["dram_bytes_per_state"],
