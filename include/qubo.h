@@ -34,9 +34,11 @@ extern "C" {
 /* Element type of Q. */
 typedef enum { QUBO_I16 = 1, QUBO_I32 = 2, QUBO_F32 = 3, QUBO_F64 = 4 } qubo_dtype;
 
-/* Accumulator the scan ran in (reported in qubo_result.acc).  QUBO_ACC_I32F: integer energies
- * held exactly in FP32 lanes, chosen when every partial sum of the run's plan stays below 2^24
- * in magnitude.  QUBO_ACC_I16P: integer energies held as two 16-bit lanes per 32-bit word,
+/* Accumulator the scan ran in (reported in qubo_result.acc).  QUBO_ACC_F32: float Q scanned in
+ * FP32, the running energies rebuilt from the tables every 2^10 walk steps (shorter when the
+ * measured drift needs it; qubo_result.anchor_bits), every state within the candidate margin
+ * rescored in FP64.  QUBO_ACC_I32F: integer energies held exactly in FP32 lanes, chosen when
+ * every value the run's plan holds in a lane stays below 2^24 in magnitude.  QUBO_ACC_I16P: integer energies held as two 16-bit lanes per 32-bit word,
  * chosen (before QUBO_ACC_I32F) when every column value of the run's plan provably lies in
  * [-32768, 32767].  QUBO_ACC_I32Z: int32 energies of a sparse instance, chosen first when the
  * variables can be ordered so that at least 3 walked prefix variables have no coupling to any
