@@ -253,7 +253,25 @@ def solve(Q, topk: int = 0, states_cap: int = 1 << 16, split_k: int = 0, walk_bi
                   tkE[:k].copy(), st, info.as_dict())
 
 
+class PackedBatch:
+    """Instances in qubo_solve_batched's input layout (one contiguous row-major array of all
+    matrices, their sizes and element offsets), built once by pack_batch and accepted wherever a
+    list of matrices is, so repeated solves of the same batch skip the repacking."""
+
+    def __init__(self, packed, ns, offs, dt):
+        self.packed, self.ns, self.offs, self.dt = packed, ns, offs, dt
+
+    def __len__(self):
+        return len(self.ns)
+
+
+def pack_batch(Qs) -> PackedBatch:
+    return PackedBatch(*_pack(Qs))
+
+
 def _pack(Qs):
+    if isinstance(Qs, PackedBatch):
+        return Qs.packed, Qs.ns, Qs.offs, Qs.dt
     mats = [as_qubo_matrix(Q) for Q in Qs]
     dts = {d for _, d in mats}
     if len(dts) != 1:

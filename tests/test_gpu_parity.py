@@ -280,6 +280,18 @@ def test_batched_matches_per_instance(q):
         assert r.info["states_scanned"] == 1 << Q.shape[0]
 
 
+def test_batched_prepacked_input_equals_list(q):
+    """A batch packed once (pack_batch) gives the same results as the list of matrices."""
+    insts = wl.config4(count=40, seed=7)
+    insts = [Q for Q in insts if Q.shape[0] <= 22]
+    a = q.solve_batched(insts, topk=2, states_cap=16)
+    b = q.solve_batched(q.pack_batch(insts), topk=2, states_cap=16)
+    assert len(a) == len(b) == len(insts)
+    for ra, rb in zip(a, b):
+        assert ra.min == rb.min and ra.n_ties == rb.n_ties
+        assert np.array_equal(ra.ties, rb.ties) and np.array_equal(ra.topk, rb.topk)
+
+
 def test_batched_float(q):
     insts = [wl.sk_float32(n, seed=n) for n in (10, 15, 18, 20, 16)]
     rs = q.solve_batched(insts, topk=2)
