@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -75,6 +76,42 @@ struct HostInst {
     bool no_factored = false;   // the factored FP32 scan used up its margin: plan the dense one
     int anchor_bits = kFloatAnchorBits;  // ACC_F32: re-anchoring period (log2 of walk steps)
 };
+
+// The plan part of a HostInst (what plan() and the exactness checks set), saved and restored
+// without copying the matrices.
+struct PlanFields {
+    Acc acc;
+    int variant, B, L, k, small, fix_bits;
+    uint64_t fix_value, unit_begin, units, sub_base, sub_count, items, states;
+    int32_t clampC, col_lo, col_hi;
+};
+
+PlanFields plan_fields(const HostInst &h)
+{
+    return {h.acc,        h.variant, h.B,     h.L,        h.k,         h.small,  h.fix_bits, h.fix_value, h.unit_begin,
+            h.units,      h.sub_base, h.sub_count, h.items, h.states, h.clampC, h.col_lo,   h.col_hi};
+}
+
+void set_plan_fields(HostInst &h, const PlanFields &p)
+{
+    h.acc = p.acc;
+    h.variant = p.variant;
+    h.B = p.B;
+    h.L = p.L;
+    h.k = p.k;
+    h.small = p.small;
+    h.fix_bits = p.fix_bits;
+    h.fix_value = p.fix_value;
+    h.unit_begin = p.unit_begin;
+    h.units = p.units;
+    h.sub_base = p.sub_base;
+    h.sub_count = p.sub_count;
+    h.items = p.items;
+    h.states = p.states;
+    h.clampC = p.clampC;
+    h.col_lo = p.col_lo;
+    h.col_hi = p.col_hi;
+}
 
 bool dtype_ok(qubo_dtype dt) { return dt == QUBO_I16 || dt == QUBO_I32 || dt == QUBO_F32 || dt == QUBO_F64; }
 bool dtype_float(qubo_dtype dt) { return dt == QUBO_F32 || dt == QUBO_F64; }
@@ -557,7 +594,16 @@ double threshold_bound(const HostInst &h, int K, int restarts = 24)
     };
     std::vector<std::pair<double, uint64_t>> seen;
     std::unordered_set<uint64_t> codes;
+    double best1 = std::numeric_limits<double>::infinity();  // K = 1: the lowest state met
+    uint64_t best1_x = 0;
     auto offer = [&](double E, uint64_t x) {
+        if (K <= 1) {
+            if (E < best1) {
+                best1 = E;
+                best1_x = x;
+            }
+            return;
+        }
         if (codes.insert(x).second)
             seen.emplace_back(E, x);
     };
@@ -597,6 +643,9 @@ double threshold_bound(const HostInst &h, int K, int restarts = 24)
         for (int v = 0; v < free_bits; ++v)
             offer(E + (((x >> v) & 1) ? -(U(v, v) + hf[v]) : (U(v, v) + hf[v])), x ^ (1ull << v));
     }
+    if (K <= 1 && restarts > 0)
+        seen.emplace_back(best1, best1_x);
+    K = std::max(K, 1);
     if ((int)seen.size() < K)
         return h.beta;
     std::nth_element(seen.begin(), seen.begin() + (K - 1), seen.end());
@@ -1767,7 +1816,10 @@ int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
             break;
         if (!(alt_acc == ACC_I16P ? i16p_allowed() : i32f_allowed()))
             continue;
-        std::vector<HostInst> alt = hs;
+        // plan in place; the previous plans are kept (not the matrices) to restore on failure
+        std::vector<PlanFields> saved(count);
+        for (int i = 0; i < count; ++i)
+            saved[i] = plan_fields(hs[i]);
         int v2 = pick_variant(alt_acc, -1);
         int tv = 0, tw = 0;
         if (tuned_plan(alt_acc, 0, &tv, &tw))
@@ -1775,7 +1827,7 @@ int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
         std::atomic<bool> all{true};
         auto alt_range = [&](int lo, int hi) {
             for (int i = lo; i < hi && all.load(std::memory_order_relaxed); ++i) {
-                HostInst &h = alt[i];
+                HostInst &h = hs[i];
                 h.acc = alt_acc;
                 h.variant = v2;
                 const int B = acc_suffix_bits(alt_acc, v2);
@@ -1788,13 +1840,10 @@ int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
             }
         };
         parallel(alt_range);
-        if (all) {
-            for (size_t i = 0; i < hs.size(); ++i) {
-                alt[i].thr0 = hs[i].thr0;
-                hs[i] = std::move(alt[i]);
-            }
+        if (all)
             break;
-        }
+        for (int i = 0; i < count; ++i)
+            set_plan_fields(hs[i], saved[i]);
     }
     // longest work first (LPT order) so the tail of the persistent launch is short
     order.resize(count);
