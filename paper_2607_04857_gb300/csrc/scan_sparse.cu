@@ -359,79 +359,97 @@ __global__ void __launch_bounds__(kScanThreads, 3) zscan_kernel(const ScanArgs a
 // ---- one block per unit: every walked row factored out (Z = L >= 7) --------------------------
 // The columns are used once (their minimum, and in a hit unit each column again), so they are
 // not kept in registers: the kernel runs at more warps per SM to hide the E_L reads' latency.
+// A warp takes the units it claims two at a time: both units' minima of e are formed in one pass
+// over E_L, which halves the L1 traffic of that pass (it ran near the L1 load bandwidth).
 
-// Minimum over the 2^Z walk steps of a unit of e(i) = E_L(g(i)) + sum of the zero-row couplings
-// of the set bits of g(i) (Z >= 7; the same decomposition as zscan_unit's block minima, parity 0).
-template <class X>
-__device__ __forceinline__ X walk_min_one(const X *EL, int Z, int lane, const X *wsm, X *wt, X *gs)
+// Minima over the 2^Z walk steps of U units of e_u(i) = E_L(g(i)) + the sum of unit u's
+// zero-row couplings of the set bits of g(i) (Z >= 7; the same decomposition as zscan_unit's
+// block minima, parity 0), one read of E_L for all U units.  out[u] is the warp's minimum.
+template <class X, int U>
+__device__ __forceinline__ void walk_min_units(const X *EL, int Z, int lane, X *const (&wsm)[U], X *const (&wt)[U],
+                                               X *gs, X (&out)[U])
 {
     const int zt = Z - 7;
-    if (lane == 0)
-        gs[0] = 0;
-    __syncwarp();
-    for (int b = 0; b < zt; ++b) {
-        const X wb = wsm[7 + b];
-        for (int m = lane; m < (1 << b); m += 32)
-            gs[m + (1 << b)] = gs[m] + wb;
-        __syncwarp();
-    }
-    for (int e = lane; e < (1 << zt); e += 32)  // parity 0: only the lower half of the table
-        wt[e] = gs[(e ^ (e >> 1)) & ((1 << zt) - 1)];
-    X a = 0;
-    for (int r = 0; r < 4; ++r)
-        if (((lane >> r) ^ (lane >> (r + 1))) & 1)
-            a += wsm[2 + r];
-    const bool l0 = lane & 1, l4 = (lane >> 4) & 1;
-    X ae[4], ao[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const bool g0 = (k ^ (k >> 1)) & 1, g1 = ((k >> 1) & 1) ^ l0;
-        const X base = a + (g0 ? wsm[0] : 0) + (g1 ? wsm[1] : 0);
-        ae[k] = base + (l4 ? wsm[6] : 0);
-        ao[k] = base + (l4 ? 0 : wsm[6]);
+    for (int u = 0; u < U; ++u) {  // the high-bit table of unit u, built by doubling in gs
+        if (lane == 0)
+            gs[0] = 0;
+        __syncwarp();
+        for (int b = 0; b < zt; ++b) {
+            const X wb = wsm[u][7 + b];
+            for (int m = lane; m < (1 << b); m += 32)
+                gs[m + (1 << b)] = gs[m] + wb;
+            __syncwarp();
+        }
+        for (int e = lane; e < (1 << zt); e += 32)  // parity 0: only the lower half of the table
+            wt[u][e] = gs[(e ^ (e >> 1)) & ((1 << zt) - 1)];
+        __syncwarp();  // gs is rebuilt for the next unit
     }
-    __syncwarp();
+    const bool l0 = lane & 1, l4 = (lane >> 4) & 1;
+    X ae[U][4], ao[U][4];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        X a = 0;
+        for (int r = 0; r < 4; ++r)
+            if (((lane >> r) ^ (lane >> (r + 1))) & 1)
+                a += wsm[u][2 + r];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool g0 = (k ^ (k >> 1)) & 1, g1 = ((k >> 1) & 1) ^ l0;
+            const X base = a + (g0 ? wsm[u][0] : 0) + (g1 ? wsm[u][1] : 0);
+            ae[u][k] = base + (l4 ? wsm[u][6] : 0);
+            ao[u][k] = base + (l4 ? 0 : wsm[u][6]);
+        }
+    }
     const X *e = EL + 4 * lane;
-    X acc;
     if (zt == 0) {
         X v[4];
         vload<X>(e, v);
-        acc = emin(emin3(v[0] + ae[0], v[1] + ae[1], v[2] + ae[2]), v[3] + ae[3]);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            out[u] = emin(emin3(v[0] + ae[u][0], v[1] + ae[u][1], v[2] + ae[u][2]), v[3] + ae[u][3]);
     } else {
-        X me = zbig<X>(), mo = zbig<X>();
+        X me[U], mo[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            me[u] = mo[u] = zbig<X>();
         const int nt = 1 << zt;
 #pragma unroll 4
         for (int t = 0; t < nt; t += 2) {
-            X v[4], u[4];
+            X v[4], w[4];
             vload<X>(e + (t << 7), v);
-            vload<X>(e + ((t + 1) << 7), u);
-            const X mv = emin(emin3(v[0] + ae[0], v[1] + ae[1], v[2] + ae[2]), v[3] + ae[3]);
-            const X mw = emin(emin3(u[0] + ao[0], u[1] + ao[1], u[2] + ao[2]), u[3] + ao[3]);
-            me = emin(me, mv + wt[t]);
-            mo = emin(mo, mw + wt[t + 1]);
+            vload<X>(e + ((t + 1) << 7), w);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const X mv = emin(emin3(v[0] + ae[u][0], v[1] + ae[u][1], v[2] + ae[u][2]), v[3] + ae[u][3]);
+                const X mw = emin(emin3(w[0] + ao[u][0], w[1] + ao[u][1], w[2] + ao[u][2]), w[3] + ao[u][3]);
+                me[u] = emin(me[u], mv + wt[u][t]);
+                mo[u] = emin(mo[u], mw + wt[u][t + 1]);
+            }
         }
-        acc = emin(me, mo);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            out[u] = emin(me[u], mo[u]);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        acc = emin(acc, __shfl_xor_sync(kFull, acc, o));
-    return acc;
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            out[u] = emin(out[u], __shfl_xor_sync(kFull, out[u], o));
 }
 
-template <class T, int S, bool K1>
-__device__ void zscan_unit_one(const ScanArgs &a, const Inst &d, int inst, uint64_t unit, typename Tr<T>::TP &Treg,
-                               int lane, typename Tr<T>::TC *wsm, typename Tr<T>::TC *wt, typename Tr<T>::TC *gs,
-                               typename Tr<T>::TC *lin_sm)
+// Set-up of one unit x_f: the fields of its set fixed bits (f0, one variable per lane), c(x_f),
+// the zero-row couplings w_r into wsm, and the lane's minimum over its columns
+// E_s(j) + lin(j), j = (g * 32 + lane) * 4 + e.
+template <class T, int S>
+__device__ __forceinline__ void unit_one_setup(const Inst &d, uint64_t unit, int lane, typename Tr<T>::TC *wsm,
+                                               typename Tr<T>::TC &f0, typename Tr<T>::TC &cx, typename Tr<T>::TC &cm)
 {
     using X = typename Tr<T>::TC;
     constexpr int V = 4, G = S / V, LOGG = ilog2c(G);
     constexpr int B = 2 + 5 + LOGG;
-    const int n = d.n, Z = d.L, k = d.k, BL = B + Z, nz = 1 << Z;
-    InstState *st = a.state + inst;
-    const X *W = unit_matrix<T>(d);
-
-    X f0, cx;
-    unit_fields<T>(W, n, k, BL, unit, lane, f0, cx);
+    const int BL = B + d.L;
+    unit_fields<T>(unit_matrix<T>(d), d.n, d.k, BL, unit, lane, f0, cx);
     __syncwarp();
     if (lane >= B && lane < BL)
         wsm[lane - B] = f0;
@@ -439,101 +457,194 @@ __device__ void zscan_unit_one(const ScanArgs &a, const Inst &d, int inst, uint6
     X lin_t, lin_e[V], lin_g[G];
     column_fields<X, V, G>(f0, lane, lin_t, lin_e, lin_g);
     const X *Es = (const X *)d.Es;
-    // column j = E_s(j) + lin(j), j = (g * 32 + lane) * 4 + e; only its minimum is kept
-    auto column = [&](int g, int e, const X (&ev)[V]) { return ev[e] + lin_e[e] + lin_t + lin_g[g]; };
-    X cm = zbig<X>();
+    cm = zbig<X>();
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         X ev[V];
         vload<X>(Es + (g * 32 + lane) * V, ev);
-        cm = emin(cm, emin3(column(g, 0, ev), column(g, 1, ev), emin(column(g, 2, ev), column(g, 3, ev))));
+        const X l = lin_t + lin_g[g];
+        cm = emin(cm, emin3(ev[0] + lin_e[0] + l, ev[1] + lin_e[1] + l,
+                            emin(ev[2] + lin_e[2] + l, ev[3] + lin_e[3] + l)));
     }
-    const X *EL = (const X *)d.EL;
-    const X mel = walk_min_one(EL, Z, lane, wsm, wt, gs);
+}
+
+// Threshold test of a unit whose walk minimum of e is mel; a unit that reaches the threshold is
+// enumerated by the whole warp, as in zscan_unit: lanes take consecutive steps, each lane
+// recomputes its columns at a broadcast step.
+template <class T, int S, bool K1>
+__device__ void unit_one_finish(const ScanArgs &a, const Inst &d, int inst, uint64_t unit, typename Tr<T>::TP &Treg,
+                                int lane, const typename Tr<T>::TC *wsm, typename Tr<T>::TC *lin_sm,
+                                typename Tr<T>::TC f0, typename Tr<T>::TC cx, typename Tr<T>::TC cm,
+                                typename Tr<T>::TC mel)
+{
+    using X = typename Tr<T>::TC;
+    constexpr int V = 4, G = S / V, LOGG = ilog2c(G);
+    constexpr int B = 2 + 5 + LOGG;
+    const int Z = d.L, BL = B + Z, nz = 1 << Z;
+    InstState *st = a.state + inst;
     {
         const X tg = Tr<T>::thr_load(st);
         Treg = K1 ? emin(Treg, tg) : tg;
     }
     const X mu = (X)a.margin;
     const X P = cx;
+    if (!__any_sync(kFull, cm + mel <= Treg + mu - P))
+        return;
+    X lin_t, lin_e[V], lin_g[G];
+    column_fields<X, V, G>(f0, lane, lin_t, lin_e, lin_g);
+    const X *Es = (const X *)d.Es;
+    const X *EL = (const X *)d.EL;
     const uint64_t cbase = unit << BL;
-    if (__any_sync(kFull, cm + mel <= Treg + mu - P)) {
-        // rare: as in zscan_unit, the warp enumerates the unit's steps together; each lane
-        // recomputes its columns at a broadcast step
-        X cmin = cm, tmax = Treg;
+    X cmin = cm, tmax = Treg;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            cmin = emin(cmin, __shfl_xor_sync(kFull, cmin, o));
-            tmax = emax(tmax, __shfl_xor_sync(kFull, tmax, o));
-        }
-        const X umax = tmax + mu - P;
+    for (int o = 16; o > 0; o >>= 1) {
+        cmin = emin(cmin, __shfl_xor_sync(kFull, cmin, o));
+        tmax = emax(tmax, __shfl_xor_sync(kFull, tmax, o));
+    }
+    const X umax = tmax + mu - P;
 #pragma unroll
-        for (int g = 0; g < G; ++g)  // the slow path indexes the column groups at run time
-            lin_sm[g * 32 + lane] = lin_g[g];
-        int ii = lane;
-        int gi = ii ^ (ii >> 1);
-        X zs = zero_row_sum(gi & (nz - 1), wsm, Z);
-        for (int off = 0; off < nz; off += 32) {
-            if (off > 0) {
-                ii += 32;
-                const int gn = ii ^ (ii >> 1);
-                int diff = (gi ^ gn) & (nz - 1);
-                while (diff) {
-                    const int r = __ffs(diff) - 1;
-                    diff &= diff - 1;
-                    zs = ((gn >> r) & 1) ? zs + wsm[r] : zs - wsm[r];
-                }
-                gi = gn;
+    for (int g = 0; g < G; ++g)  // the enumeration indexes the column groups at run time
+        lin_sm[g * 32 + lane] = lin_g[g];
+    int ii = lane;
+    int gi = ii ^ (ii >> 1);
+    X zs = zero_row_sum(gi & (nz - 1), wsm, Z);
+    for (int off = 0; off < nz; off += 32) {
+        if (off > 0) {
+            ii += 32;
+            const int gn = ii ^ (ii >> 1);
+            int diff = (gi ^ gn) & (nz - 1);
+            while (diff) {
+                const int r = __ffs(diff) - 1;
+                diff &= diff - 1;
+                zs = ((gn >> r) & 1) ? zs + wsm[r] : zs - wsm[r];
             }
-            const X el = __ldg(EL + ii) + zs;
-            unsigned m = __ballot_sync(kFull, cmin + el <= umax);
-            while (m) {
-                const int src = __ffs(m) - 1;
-                m &= m - 1;
-                const X els = __shfl_sync(kFull, el, src);
-                const int is = off + src;
-                X tp = Treg + mu - P - els;
-                if (cm > tp)
-                    continue;
-                const uint64_t cb = cbase | ((uint64_t)(is ^ (is >> 1)) << B);
-                for (int g = 0; g < G; ++g) {
-                    X ev[V];
-                    vload<X>(Es + (g * 32 + lane) * V, ev);
-                    const X lg = lin_sm[g * 32 + lane];
+            gi = gn;
+        }
+        const X el = __ldg(EL + ii) + zs;
+        unsigned m = __ballot_sync(kFull, cmin + el <= umax);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const X els = __shfl_sync(kFull, el, src);
+            const int is = off + src;
+            X tp = Treg + mu - P - els;
+            if (cm > tp)
+                continue;
+            const uint64_t cb = cbase | ((uint64_t)(is ^ (is >> 1)) << B);
+            for (int g = 0; g < G; ++g) {
+                X ev[V];
+                vload<X>(Es + (g * 32 + lane) * V, ev);
+                const X lg = lin_sm[g * 32 + lane];
 #pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        const X c = ev[e] + lin_e[e] + lin_t + lg;
-                        if (c <= tp) {
-                            const X Et = c + els + P;
-                            const uint32_t j = (uint32_t)((g * 32 + lane) * V + e);
-                            record<T>(a, inst, Et, unpermute(cb | j, d.perm));
-                            if (K1 && Et < Treg) {
-                                Treg = Et;
-                                tp = Treg + mu - P - els;
-                                Tr<T>::thr_min(st, Et);
-                            }
+                for (int e = 0; e < V; ++e) {
+                    const X c = ev[e] + lin_e[e] + lin_t + lg;
+                    if (c <= tp) {
+                        const X Et = c + els + P;
+                        const uint32_t j = (uint32_t)((g * 32 + lane) * V + e);
+                        record<T>(a, inst, Et, unpermute(cb | j, d.perm));
+                        if (K1 && Et < Treg) {
+                            Treg = Et;
+                            tp = Treg + mu - P - els;
+                            Tr<T>::thr_min(st, Et);
                         }
                     }
                 }
             }
         }
     }
+    __syncwarp();
 }
+
+// Per-warp shared memory of the one-block kernel: two units' zero-row couplings and high-bit
+// tables, the doubling scratch, and the column groups' fields of a hit unit.
+template <class X, int S>
+struct OneSmem {
+    X wsm[2][kMaxWalkBits];
+    X wt[2][1 << (kZMaxRows - 7)];
+    X gs[1 << (kZMaxRows - 7)];
+    X lin[S / 4 * 32];
+};
 
 template <class T, int S, bool K1>
 __global__ void __launch_bounds__(kScanThreads, 6) zscan_one_kernel(const ScanArgs a)
 {
     using X = typename Tr<T>::TC;
-    __shared__ X wsm_all[kScanThreads / 32][kMaxWalkBits];
-    __shared__ X wt_all[kScanThreads / 32][1 << (kZMaxRows - 7)];
-    __shared__ X gs_all[kScanThreads / 32][1 << (kZMaxRows - 7)];
-    __shared__ X lin_all[kScanThreads / 32][S / 4 * 32];
+    __shared__ OneSmem<X, S> sm_all[kScanThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    OneSmem<X, S> &sm = sm_all[warp];
     typename Tr<T>::TP Treg = 0;
-    persistent_units<T, 8>(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
-        zscan_unit_one<T, S, K1>(a, d, inst, unit, Treg, lane, wsm_all[warp], wt_all[warp], gs_all[warp],
-                              lin_all[warp]);
-    });
+    // the persistent loop of persistent_units, taking the units of a claim two at a time
+    constexpr unsigned long long kChunk = 8;
+    int cur = -1;
+    unsigned long long done = 0;
+    unsigned long long next = lane == 0 ? atomicAdd(a.queue, kChunk) : 0ull;
+    for (;;) {
+        unsigned long long base = 0;
+        int stop = 0;
+        if (lane == 0) {
+            stop = *a.abort_flag != 0;
+            base = next;
+            if (!stop && base < a.total_items)
+                next = atomicAdd(a.queue, kChunk);
+        }
+        stop = __shfl_sync(kFull, stop, 0);
+        base = __shfl_sync(kFull, base, 0);
+        if (stop || base >= a.total_items)
+            break;
+        const unsigned long long end = base + kChunk < a.total_items ? base + kChunk : (unsigned long long)a.total_items;
+        for (unsigned long long item = base; item < end;) {
+            int inst = 0;
+            if (a.n_inst > 1) {
+                int lo = 0, hi = a.n_inst;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (a.item_base[mid] <= item)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                inst = lo;
+            }
+            if (inst != cur) {
+                if (lane == 0 && done)
+                    atomicAdd(&a.state[cur].scanned, done);
+                done = 0;
+                cur = inst;
+                Treg = Tr<T>::thr_load(a.state + inst);
+            }
+            const Inst d = a.inst[inst];
+            if (d.small) {
+                small_unit<T>(a, d, inst, lane);  // counts its own states
+                ++item;
+                continue;
+            }
+            const uint64_t unit = d.unit_begin + (item - a.item_base[inst]);
+            const bool pair = item + 1 < end && a.item_base[inst + 1] > item + 1;
+            X f0a, cxa, cma, f0b = 0, cxb = 0, cmb = 0;
+            unit_one_setup<T, S>(d, unit, lane, sm.wsm[0], f0a, cxa, cma);
+            if (pair) {
+                unit_one_setup<T, S>(d, unit + 1, lane, sm.wsm[1], f0b, cxb, cmb);
+                X *const w[2] = {sm.wsm[0], sm.wsm[1]};
+                X *const t[2] = {sm.wt[0], sm.wt[1]};
+                X mel[2];
+                walk_min_units<X, 2>((const X *)d.EL, d.L, lane, w, t, sm.gs, mel);
+                unit_one_finish<T, S, K1>(a, d, inst, unit, Treg, lane, sm.wsm[0], sm.lin, f0a, cxa, cma, mel[0]);
+                unit_one_finish<T, S, K1>(a, d, inst, unit + 1, Treg, lane, sm.wsm[1], sm.lin, f0b, cxb, cmb, mel[1]);
+                done += 2ull << (d.B + d.L);
+                item += 2;
+            } else {
+                X *const w[1] = {sm.wsm[0]};
+                X *const t[1] = {sm.wt[0]};
+                X mel[1];
+                walk_min_units<X, 1>((const X *)d.EL, d.L, lane, w, t, sm.gs, mel);
+                unit_one_finish<T, S, K1>(a, d, inst, unit, Treg, lane, sm.wsm[0], sm.lin, f0a, cxa, cma, mel[0]);
+                done += 1ull << (d.B + d.L);
+                item += 1;
+            }
+        }
+    }
+    if (lane == 0 && done)
+        atomicAdd(&a.state[cur].scanned, done);
 }
 
 template <class T, bool K1>
