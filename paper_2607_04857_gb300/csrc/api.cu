@@ -1809,9 +1809,11 @@ int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
     for (int i = 0; i < count; ++i)
         if (pst[i])
             return pst[i];
-    // One accumulator for the batch: packed 16-bit lanes, else FP32 lanes, when every
-    // instance's plan is exact in it (instances evaluated directly need nothing).
-    for (const Acc alt_acc : {ACC_I16P, ACC_I32F}) {
+    // One accumulator for the batch: packed 16-bit lanes, else FP32 lanes (2^14-step walks, else
+    // 2^12), when every instance's plan is exact in it (instances evaluated directly need nothing).
+    const std::pair<Acc, int> alts[] = {
+        {ACC_I16P, kDefaultMaxWalkBits}, {ACC_I32F, kI32FMaxWalkBits}, {ACC_I32F, kDefaultMaxWalkBits}};
+    for (const auto &[alt_acc, alt_walk] : alts) {
         if (acc != ACC_I32)
             break;
         if (!(alt_acc == ACC_I16P ? i16p_allowed() : i32f_allowed()))
@@ -1831,8 +1833,7 @@ int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
                 h.acc = alt_acc;
                 h.variant = v2;
                 const int B = acc_suffix_bits(alt_acc, v2);
-                const int walk =
-                    h.n - B >= variant_reg_rows(h) + 1 ? std::min(kDefaultMaxWalkBits, h.n - B) : 0;
+                const int walk = h.n - B >= variant_reg_rows(h) + 1 ? std::min(alt_walk, h.n - B) : 0;
                 const bool ok = plan(h, 0, 0, 0, walk) == QUBO_OK &&
                                 (h.small || (alt_acc == ACC_I16P ? i16p_exact(h) : i32f_exact(h, &h.clampC)));
                 if (!ok)
