@@ -240,7 +240,7 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
         if (kb > 0) {  // walked row Z + kk flips (Gray step over the blocks)
             const int kk = __ffs(kb) - 1;
             const int r = Z + kk;
-            const bool neg = (kb >> (kk + 1)) & 1;
+            const X sg = ((kb >> (kk + 1)) & 1) ? (X)-1 : (X)1;  // one multiply-add per column
             const X *row = Mt + (size_t)r * NB;
 #pragma unroll
             for (int g = 0; g < G; ++g) {
@@ -248,9 +248,9 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
                 vload<X>(row + (g * 32 + lane) * V, mv);
 #pragma unroll
                 for (int e = 0; e < V; ++e)
-                    E[g * V + e] = neg ? E[g * V + e] - mv[e] : E[g * V + e] + mv[e];
+                    E[g * V + e] = E[g * V + e] + sg * mv[e];
             }
-            P = neg ? P - wsm[r] : P + wsm[r];
+            P = P + sg * wsm[r];
         }
         const X cm = tree_min<X, 3, S>(E);
         if (__any_sync(kFull, cm + mel[kb] <= Treg + mu - P)) {
