@@ -236,82 +236,192 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
     const X *Mt = (const X *)d.M;
     const uint64_t cbase = unit << BL;
 
-    for (int kb = 0; kb < nblk; ++kb) {
-        if (kb > 0) {  // walked row Z + kk flips (Gray step over the blocks)
-            const int kk = __ffs(kb) - 1;
-            const int r = Z + kk;
-            const X sg = ((kb >> (kk + 1)) & 1) ? (X)-1 : (X)1;  // one multiply-add per column
-            const X *row = Mt + (size_t)r * NB;
+    // Enumeration of block kb whose columns are staged in `stage` (prefix Pb, lane minimum cmb):
+    // the warp enumerates the block together.  Lanes take consecutive walk steps (coalesced E_L
+    // reads); a step whose e(i) plus the smallest column of any lane reaches the largest
+    // threshold of any lane is broadcast, and every lane checks its own columns at that step.
+    auto enumerate_block = [&](int kb, X Pb, X cmb) {
+        X cmin = cmb, tmax = Treg;
 #pragma unroll
-            for (int g = 0; g < G; ++g) {
-                X mv[V];
-                vload<X>(row + (g * 32 + lane) * V, mv);
-#pragma unroll
-                for (int e = 0; e < V; ++e)
-                    E[g * V + e] = E[g * V + e] + sg * mv[e];
-            }
-            P = P + sg * wsm[r];
+        for (int o = 16; o > 0; o >>= 1) {
+            cmin = emin(cmin, __shfl_xor_sync(kFull, cmin, o));
+            tmax = emax(tmax, __shfl_xor_sync(kFull, tmax, o));
         }
-        const X cm = tree_min<X, 3, S>(E);
-        if (__any_sync(kFull, cm + mel[kb] <= Treg + mu - P)) {
-            // rare: the warp enumerates the block together.  Lanes take consecutive walk steps
-            // (coalesced E_L reads); a step whose e(i) plus the smallest column of any lane
-            // reaches the largest threshold of any lane is broadcast, and every lane checks its
-            // own columns at that step.
-#pragma unroll
-            for (int q = 0; q < S; ++q)
-                stage[q * 32 + lane] = E[q];
-            X cmin = cm, tmax = Treg;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                cmin = emin(cmin, __shfl_xor_sync(kFull, cmin, o));
-                tmax = emax(tmax, __shfl_xor_sync(kFull, tmax, o));
-            }
-            const X umax = tmax + mu - P;
-            const int i0 = kb << Z;
-            int ii = i0 + lane;
-            int gi = ii ^ (ii >> 1);
-            X zs = zero_row_sum(gi & (nz - 1), wsm, Z);
-            for (int off = 0; off < nz; off += 32) {
-                if (off > 0) {  // ii advances by 32: refresh the zero-row bits that changed
-                    ii += 32;
-                    const int gn = ii ^ (ii >> 1);
-                    int diff = (gi ^ gn) & (nz - 1);
-                    while (diff) {
-                        const int r = __ffs(diff) - 1;
-                        diff &= diff - 1;
-                        zs = ((gn >> r) & 1) ? zs + wsm[r] : zs - wsm[r];
-                    }
-                    gi = gn;
+        const X umax = tmax + mu - Pb;
+        const int i0 = kb << Z;
+        int ii = i0 + lane;
+        int gi = ii ^ (ii >> 1);
+        X zs = zero_row_sum(gi & (nz - 1), wsm, Z);
+        for (int off = 0; off < nz; off += 32) {
+            if (off > 0) {  // ii advances by 32: refresh the zero-row bits that changed
+                ii += 32;
+                const int gn = ii ^ (ii >> 1);
+                int diff = (gi ^ gn) & (nz - 1);
+                while (diff) {
+                    const int r = __ffs(diff) - 1;
+                    diff &= diff - 1;
+                    zs = ((gn >> r) & 1) ? zs + wsm[r] : zs - wsm[r];
                 }
-                const bool valid = off + lane < nz;
-                const X el = valid ? __ldg(EL + ii) + zs : 0;
-                unsigned m = __ballot_sync(kFull, valid && cmin + el <= umax);
-                while (m) {
-                    const int src = __ffs(m) - 1;
-                    m &= m - 1;
-                    const X els = __shfl_sync(kFull, el, src);
-                    const int is = i0 + off + src;
-                    X tp = Treg + mu - P - els;
-                    if (cm > tp)
-                        continue;
-                    const uint64_t cb = cbase | ((uint64_t)(is ^ (is >> 1)) << B);
-                    for (int q = 0; q < S; ++q) {
-                        const X ev = stage[q * 32 + lane];
-                        if (ev <= tp) {
-                            const X Et = ev + els + P;
-                            const uint32_t j = (uint32_t)(((q / V) * 32 + lane) * V + (q % V));
-                            record<T>(a, inst, Et, unpermute(cb | j, d.perm));
-                            if (K1 && Et < Treg) {
-                                Treg = Et;
-                                tp = Treg + mu - P - els;
-                                Tr<T>::thr_min(st, Et);
-                            }
+                gi = gn;
+            }
+            const bool valid = off + lane < nz;
+            const X el = valid ? __ldg(EL + ii) + zs : 0;
+            unsigned m = __ballot_sync(kFull, valid && cmin + el <= umax);
+            while (m) {
+                const int src = __ffs(m) - 1;
+                m &= m - 1;
+                const X els = __shfl_sync(kFull, el, src);
+                const int is = i0 + off + src;
+                X tp = Treg + mu - Pb - els;
+                if (cmb > tp)
+                    continue;
+                const uint64_t cb = cbase | ((uint64_t)(is ^ (is >> 1)) << B);
+                for (int q = 0; q < S; ++q) {
+                    const X ev = stage[q * 32 + lane];
+                    if (ev <= tp) {
+                        const X Et = ev + els + Pb;
+                        const uint32_t j = (uint32_t)(((q / V) * 32 + lane) * V + (q % V));
+                        record<T>(a, inst, Et, unpermute(cb | j, d.perm));
+                        if (K1 && Et < Treg) {
+                            Treg = Et;
+                            tp = Treg + mu - Pb - els;
+                            Tr<T>::thr_min(st, Et);
                         }
                     }
                 }
             }
-            __syncwarp();
+        }
+        __syncwarp();
+    };
+    // Flip of walked row Z + kk before block kb (Gray step over the blocks), row from L1.
+    auto flip_from_memory = [&](int kb) {
+        const int kk = __ffs(kb) - 1;
+        const int r = Z + kk;
+        const X sg = ((kb >> (kk + 1)) & 1) ? (X)-1 : (X)1;  // one multiply-add per column
+        const X *row = Mt + (size_t)r * NB;
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            X mv[V];
+            vload<X>(row + (g * 32 + lane) * V, mv);
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                E[g * V + e] = E[g * V + e] + sg * mv[e];
+        }
+        P = P + sg * wsm[r];
+    };
+
+    // With 16 columns per thread, walked rows Z and Z+1 stay in registers and bodies of 8 blocks
+    // are unrolled, so their flips have compile-time rows and signs; row Z+2 flips at a body's
+    // middle and the rows above at body starts, from L1.  Per block one tree min and the block
+    // minimum cm + mel + P go into a running minimum, compared once per body.
+    constexpr int RB = S == 16 ? 2 : 0;
+    constexpr int NBODY = 2 << RB;
+    bool walked = false;
+    if constexpr (RB > 0) {
+        if (nblk >= NBODY) {
+            walked = true;
+            X Mr[RB][S], wr[RB];
+#pragma unroll
+            for (int r = 0; r < RB; ++r) {
+                const X *row = Mt + (size_t)(Z + r) * NB;
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    X mv[V];
+                    vload<X>(row + (g * 32 + lane) * V, mv);
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        Mr[r][g * V + e] = mv[e];
+                }
+                wr[r] = wsm[Z + r];
+            }
+            const X *rowMid = Mt + (size_t)(Z + RB) * NB;
+            for (int kb0 = 0; kb0 < nblk; kb0 += NBODY) {
+                if (kb0 > 0)
+                    flip_from_memory(kb0);
+                const X sgMid = ((kb0 >> (RB + 1)) & 1) ? (X)-1 : (X)1;
+                X acc;
+                static_for<NBODY>([&](auto pc) {
+                    constexpr int p = decltype(pc)::value;
+                    if constexpr (p > 0) {
+                        constexpr int kk = ctzc(p);
+                        if constexpr (kk < RB) {
+                            constexpr bool neg = (p >> (kk + 1)) & 1;
+#pragma unroll
+                            for (int q = 0; q < S; ++q)
+                                E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
+                            P = neg ? P - wr[kk] : P + wr[kk];
+                        } else {
+#pragma unroll
+                            for (int g = 0; g < G; ++g) {
+                                X mv[V];
+                                vload<X>(rowMid + (g * 32 + lane) * V, mv);
+#pragma unroll
+                                for (int e = 0; e < V; ++e)
+                                    E[g * V + e] = E[g * V + e] + sgMid * mv[e];
+                            }
+                            P = P + sgMid * wsm[Z + RB];
+                        }
+                    }
+                    const X m = tree_min<X, 3, S>(E) + (mel[kb0 + p] + P);
+                    if constexpr (p == 0)
+                        acc = m;
+                    else
+                        acc = emin(acc, m);
+                });
+                if (__any_sync(kFull, acc <= Treg + mu)) {
+                    // rare: rebuild each block of the body from the body-end registers (the rows
+                    // whose Gray bits differ) and enumerate the blocks that reach the threshold
+                    const int kend = kb0 + NBODY - 1;
+                    const int gend = kend ^ (kend >> 1);
+#pragma unroll 1
+                    for (int p = 0; p < NBODY; ++p) {
+                        const int kb = kb0 + p;
+                        const int gp = kb ^ (kb >> 1);
+                        X sr[RB + 1];
+#pragma unroll
+                        for (int r = 0; r <= RB; ++r)
+                            sr[r] = (X)(((gp >> r) & 1) - ((gend >> r) & 1));
+                        X Pb = P;
+#pragma unroll
+                        for (int r = 0; r < RB; ++r)
+                            Pb = Pb + sr[r] * wr[r];
+                        Pb = Pb + sr[RB] * wsm[Z + RB];
+                        X cmb = zbig<X>();
+#pragma unroll
+                        for (int g = 0; g < G; ++g) {
+                            X mv[V];
+                            vload<X>(rowMid + (g * 32 + lane) * V, mv);
+#pragma unroll
+                            for (int e = 0; e < V; ++e) {
+                                const int q = g * V + e;
+                                X ev = E[q];
+#pragma unroll
+                                for (int r = 0; r < RB; ++r)
+                                    ev = ev + sr[r] * Mr[r][q];
+                                ev = ev + sr[RB] * mv[e];
+                                stage[q * 32 + lane] = ev;
+                                cmb = emin(cmb, ev);
+                            }
+                        }
+                        if (__any_sync(kFull, cmb + (mel[kb] + Pb) <= Treg + mu))
+                            enumerate_block(kb, Pb, cmb);
+                        __syncwarp();
+                    }
+                }
+            }
+        }
+    }
+    if (!walked) {
+        for (int kb = 0; kb < nblk; ++kb) {
+            if (kb > 0)
+                flip_from_memory(kb);
+            const X cm = tree_min<X, 3, S>(E);
+            if (__any_sync(kFull, cm + mel[kb] <= Treg + mu - P)) {
+#pragma unroll
+                for (int q = 0; q < S; ++q)
+                    stage[q * 32 + lane] = E[q];
+                enumerate_block(kb, P, cm);
+            }
         }
     }
 
@@ -343,7 +453,7 @@ __device__ void zscan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t 
 }
 
 template <class T, int S, bool K1>
-__global__ void __launch_bounds__(kScanThreads, 3) zscan_kernel(const ScanArgs a)
+__global__ void __launch_bounds__(kScanThreads, S == 16 ? 4 : 3) zscan_kernel(const ScanArgs a)
 {
     using X = typename Tr<T>::TC;
     __shared__ X stage_all[kScanThreads / 32][S * 32 > kZTableEntries ? S * 32 : kZTableEntries];
