@@ -134,3 +134,18 @@ def build_c_client(q, out_dir):
 
 def test_c_client_compiles_and_links_against_the_header(q, tmp_path):
     assert os.path.exists(build_c_client(q, tmp_path))
+
+
+def test_pack_batch_layout(q):
+    """pack_batch lays the matrices out row-major one after another, with their sizes and element
+    offsets, in one dtype; a packed batch passes through unchanged."""
+    mats = [wl.upper_int(n, -9, 9, seed=n, dtype=np.int16) for n in (3, 5, 4)]
+    p = q.pack_batch(mats)
+    assert len(p) == 3 and p.ns.tolist() == [3, 5, 4] and p.offs.tolist() == [0, 9, 34]
+    assert p.packed.dtype == np.int16 and p.packed.size == 9 + 25 + 16
+    for M, o in zip(mats, p.offs.tolist()):
+        n = M.shape[0]
+        assert np.array_equal(p.packed[o:o + n * n].reshape(n, n), M)
+    assert q.pack_batch(p).packed is p.packed
+    with pytest.raises(ValueError):
+        q.pack_batch([mats[0], mats[1].astype(np.int32)])
