@@ -155,6 +155,17 @@ int qubo_solve_ex(const void *Q_host, int n, qubo_dtype dtype, const qubo_option
                   void *out_topk_E, qubo_result *info, void *stream);
 
 /*
+ * The plan qubo_solve_ex would run for Q_host and opt, computed on the host alone (no device
+ * work; no GPU needed): info->acc, n, split_k, walk_bits, suffix_bits, cols_per_thread,
+ * zero_rows and anchor_bits are filled, the other fields are zero.  It is the choice a solve with
+ * the same options and the same tuned plans makes: the split of Sec. 3.3, the accumulator (the
+ * exactness checks of the packed 16-bit and FP32-lane scans, the factored scan's variable order
+ * for sparse instances), the kernel shape.
+ * Returns QUBO_OK, or QUBO_ERR_ARG / QUBO_ERR_OVERFLOW as qubo_solve_ex would.
+ */
+int qubo_plan_query(const void *Q_host, int n, qubo_dtype dtype, const qubo_options *opt, qubo_result *info);
+
+/*
  * Low-energy spectrum (Sec. 6.2: the k lowest energies, Sec. 1.4: brute force yields the
  * low-energy spectrum): every state with E <= E_min + window, in (E, code) ascending order.
  *   window     >= 0, in energy units (integer Q: the integer part is used; < 2^30).

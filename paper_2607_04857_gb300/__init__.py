@@ -33,7 +33,7 @@ EXPORTS = (
     "qubo_abort_clear", "qubo_device_sm_count", "qubo_version", "qubo_solve_noalloc",
     "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_batch_destroy",
     "qubo_autotune", "qubo_autotune_batched", "qubo_autotune_clear", "qubo_solve_window", "qubo_solve_wide",
-    "qubo_merge_wide", "qubo_autotune_save", "qubo_autotune_load",
+    "qubo_merge_wide", "qubo_autotune_save", "qubo_autotune_load", "qubo_plan_query",
 )
 WIDE_MAX_N = 128
 QUBO_MAX_TOPK = 1024
@@ -128,6 +128,7 @@ def load_library(path: str = LIB_PATH):
     lib.qubo_merge_wide.argtypes = [P, P, SZ, I, P]
     lib.qubo_autotune_save.argtypes = [ctypes.c_char_p]
     lib.qubo_autotune_load.argtypes = [ctypes.c_char_p]
+    lib.qubo_plan_query.argtypes = [P, I, I, P, P]
     lib.qubo_autotune_clear.restype = None
     lib.qubo_strerror.argtypes = [I]
     lib.qubo_strerror.restype = ctypes.c_char_p
@@ -414,6 +415,21 @@ def solve_wide(Q, n_inner: int, outer_begin: int = 0, outer_count: int | None = 
     k = int(info.n_topk)
     return Result(float(mn[0]) if isf else int(mn[0]), int(nt[0]), wide(st_codes, int(info.n_written)),
                   wide(tk, k), tkE[:k].copy(), st, info.as_dict())
+
+
+def plan_query(Q, topk: int = 0, split_k: int = 0, walk_bits: int = 0, fix_bits: int = 0, fix_value: int = 0,
+               plain: bool = False) -> dict:
+    """The plan a solve with these options would run (qubo_plan_query), computed on the host alone:
+    accumulator, split, walk, suffix bits, columns per thread, factored rows, anchoring period."""
+    lib = load_library()
+    Qm, dt = as_qubo_matrix(Q)
+    o = Options(split_k=split_k, topk=topk, fix_bits=fix_bits, walk_bits=walk_bits, fix_value=fix_value,
+                flags=QUBO_FLAG_PLAIN if plain else 0)
+    info = ResultInfo()
+    _check(lib.qubo_plan_query(_ptr(Qm), Qm.shape[0], dt, ctypes.byref(o), ctypes.byref(info)), "qubo_plan_query")
+    d = info.as_dict()
+    return {k: d[k] for k in ("acc", "n", "split_k", "walk_bits", "suffix_bits", "cols_per_thread", "zero_rows",
+                              "anchor_bits")}
 
 
 def solve_window(Q, window: float, cap: int = 1 << 16, fix_bits: int = 0, fix_value: int = 0, plain: bool = False,

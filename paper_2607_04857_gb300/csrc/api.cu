@@ -1646,8 +1646,9 @@ int check_opts(const qubo_options *o, size_t states_cap, const uint64_t *out_sta
     return QUBO_OK;
 }
 
-int solve_one(Workspace &ws, HostInst &h, const qubo_options &o, size_t states_cap, cudaStream_t stream, Part &p,
-              SolveStats &stats, double window = -1.0)
+// Configuration of one solve from the caller's options: the tuned plan for this size (when the
+// caller fixes neither split_k nor walk_bits) or the accumulator's default variant.
+SolveCfg solve_cfg(const HostInst &h, const qubo_options &o, size_t states_cap, double window)
 {
     SolveCfg c;
     c.window = window;
@@ -1670,6 +1671,13 @@ int solve_one(Workspace &ws, HostInst &h, const qubo_options &o, size_t states_c
                 c.walk_bits = tw;
         }
     }
+    return c;
+}
+
+int solve_one(Workspace &ws, HostInst &h, const qubo_options &o, size_t states_cap, cudaStream_t stream, Part &p,
+              SolveStats &stats, double window = -1.0)
+{
+    SolveCfg c = solve_cfg(h, o, states_cap, window);
     const double deadline = o.time_limit_s > 0 ? now_s() + o.time_limit_s : 0.0;
     int st = solve_range(ws, h, o.fix_bits, o.fix_value, c, stream, p, stats, deadline);
     if (st)
@@ -2125,6 +2133,29 @@ int qubo_solve_ex(const void *Q_host, int n, qubo_dtype dtype, const qubo_option
     fill_outputs(h, p, o.topk, states_cap, out_min, out_states, out_topk, out_topk_E, info);
     fill_plan_info(h, stats, t0, info);
     return p.n_ties > states_cap ? QUBO_TRUNCATED : QUBO_OK;
+}
+
+int qubo_plan_query(const void *Q_host, int n, qubo_dtype dtype, const qubo_options *opt, qubo_result *info)
+{
+    const double t0 = now_s();
+    qubo_options o{};
+    if (opt)
+        o = *opt;
+    if (!info || o.topk < 0 || o.topk > QUBO_MAX_TOPK)
+        return QUBO_ERR_ARG;
+    HostInst h;
+    int st = prepare(Q_host, n, dtype, o.flags, h);
+    if (st)
+        return st;
+    if (o.fix_bits < 0 || o.fix_bits > n)
+        return QUBO_ERR_ARG;
+    const SolveCfg c = solve_cfg(h, o, 0, -1.0);
+    if ((st = plan_run(h, o.fix_bits, o.fix_value, c.split_k, c.walk_bits, c.variant, c.flags)))
+        return st;
+    std::memset(info, 0, sizeof(*info));
+    info->acc = (int32_t)h.acc;
+    fill_plan_info(h, SolveStats(), t0, info);
+    return QUBO_OK;
 }
 
 int qubo_solve_window(const void *Q_host, int n, qubo_dtype dtype, double window, const qubo_options *opt,

@@ -9,6 +9,7 @@ import pytest
 
 import oracle
 from paper_2607_04857_gb300 import workloads as wl
+from plan_checks import column_range
 
 pytestmark = pytest.mark.gpu
 
@@ -39,23 +40,6 @@ def check_int(r, o):
     assert np.array_equal(r.ties, o.ties), (r.ties[:8], o.ties[:8])
     assert np.array_equal(r.topk, o.topk), (r.topk, o.topk)
     assert np.array_equal(r.topk_E, o.topk_E), (r.topk_E, o.topk_E)
-
-
-def column_range(Q, B, L, RC):
-    """Range of the column values a packed scan with B suffix bits, L walked bits and RC
-    register rows can hold: for every suffix pattern j, E_s(j) plus each outside coupling sum
-    c_i(j) and each register-row/fixed coupling at its sign's extreme."""
-    U = oracle.fold(np.asarray(Q).astype(np.int64)).astype(np.int64)
-    n = U.shape[0]
-    W = np.triu(U, 1) + np.triu(U, 1).T
-    j = np.arange(1 << B, dtype=np.int64)
-    J = (j[:, None] >> np.arange(B)) & 1
-    Es = J @ np.diag(U)[:B] + ((J @ W[:B, :B]) * J).sum(1) // 2
-    c = J @ W[:B, B:]
-    hi = Es + np.clip(c, 0, None).sum(1)
-    lo = Es + np.clip(c, None, 0).sum(1)
-    wr = W[B:B + RC, B + L:]
-    return int(lo.min() + np.clip(wr, None, 0).sum()), int(hi.max() + np.clip(wr, 0, None).sum())
 
 
 @pytest.mark.parametrize("n", [15, 18, 24, 28, 31])

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from paper_2607_04857_gb300 import workloads as wl
+from plan_checks import fp32_lanes_fit
 
 pytestmark = pytest.mark.gpu
 
@@ -528,43 +529,6 @@ def test_int32_kernel_when_fp32_lanes_disabled(q, monkeypatch):
         r = q.solve(Q, topk=16)
         assert r.info["acc"] == "i32"
         check_int(r, oracle.solve(Q, topk=16))
-
-
-def plan_bound(Q, suffix_bits, walk_bits):
-    """S_nf + 2 S_ww of a plan: the crude bound on the magnitudes the FP32-lane scan forms."""
-    U = np.abs(oracle.fold(Q)).astype(np.float64)
-    nf = suffix_bits + walk_bits
-    return U[:nf, :].sum() + 2 * U[suffix_bits:nf, suffix_bits:nf].sum()
-
-
-def fp32_lanes_fit(Q, B, L, RC):
-    """Whether every value an FP32-lane scan with B suffix bits, L walked bits and RC register
-    rows holds stays below 2^24: the crude bound, else the exact column range (every outside
-    coupling sum at its sign's extreme, per suffix pattern), the walked energies E_L by brute
-    force, and each table row's sum of |U|."""
-    if plan_bound(Q, B, L) + 2 < 2**24:
-        return True
-    U = oracle.fold(np.asarray(Q).astype(np.int64)).astype(np.int64)
-    nf = B + L
-    W = np.triu(U, 1) + np.triu(U, 1).T
-    for r in range(B, nf):
-        row = np.abs(W[r, :B]).sum() + (np.abs(W[r, nf:]).sum() if r < B + RC else 0)
-        if row >= 2**24:
-            return False
-    j = np.arange(1 << B, dtype=np.int64)
-    J = (j[:, None] >> np.arange(B)) & 1
-    Es = J @ np.diag(U)[:B] + ((J @ W[:B, :B]) * J).sum(1) // 2
-    c = J @ W[:B, B:]
-    wr = W[B:B + RC, nf:]
-    hi = int((Es + np.clip(c, 0, None).sum(1)).max() + np.clip(wr, 0, None).sum())
-    lo = int((Es + np.clip(c, None, 0).sum(1)).min() + np.clip(wr, None, 0).sum())
-    g = np.arange(1 << L, dtype=np.int64)
-    G = (g[:, None] >> np.arange(L)) & 1
-    Uw = U[B:nf, B:nf]
-    EL = G @ np.diag(Uw) + ((G @ np.triu(Uw, 1)) * G).sum(1)
-    el = int(np.abs(EL).max())
-    C = max(-lo, hi, 0) + el + 1
-    return C + el + 1 < 2**24
 
 
 def test_fp32_lanes_rejected_when_out_of_range(q):

@@ -1,0 +1,96 @@
+"""The host's planning (qubo_plan_query), which needs no GPU: the accumulator and kernel shape
+each benchmark instance gets, and the admission of the packed 16-bit and FP32-lane scans checked
+against numpy restatements of their exactness conditions."""
+import numpy as np
+import pytest
+
+from paper_2607_04857_gb300 import workloads as wl
+from plan_checks import column_range, fp32_lanes_fit
+
+
+@pytest.fixture(scope="module")
+def q():
+    from paper_2607_04857_gb300 import build as qbuild
+
+    qbuild.build()
+    import paper_2607_04857_gb300 as q
+
+    q.load_library()
+    return q
+
+
+def shape(p):
+    return p["acc"], p["walk_bits"], p["suffix_bits"]
+
+
+def test_benchmark_plans(q, monkeypatch):
+    monkeypatch.delenv("QUBO_SCAN_VARIANT", raising=False)
+    q.autotune_clear()
+    # n = 50 int32 (2^43-state steps): integers in FP32 lanes, 2^14-step walks, 16 columns
+    p = q.plan_query(wl.config5(), topk=16, fix_bits=7)
+    assert shape(p) == ("i32f", 14, 9) and p["split_k"] == 27
+    # n = 44 FP32 (2^42): FP32, 2^14-step walks re-anchored every 2^10 steps
+    p = q.plan_query(wl.config3(), fix_bits=2)
+    assert shape(p) == ("f32", 14, 9) and p["anchor_bits"] == 10
+    # Max-Cut n = 48 (2^42): factored scan, 3 factored rows, 64 columns
+    p = q.plan_query(wl.maxcut_qubo(48, 0.5, seed=48), topk=16, fix_bits=6)
+    assert shape(p) == ("i32z", 12, 11) and p["zero_rows"] == 3
+    # sparse n = 56 (2^46): every walked row factored (one block per unit)
+    for Q, acc in ((wl.sparse_int(56, 0.05, -1000, 1000, seed=56), "i32z"), (wl.sparse_float32(56, 0.05, seed=56), "f32z")):
+        p = q.plan_query(Q, topk=16, fix_bits=10)
+        assert shape(p) == (acc, 14, 11) and p["zero_rows"] == 14
+    # the plain form runs in the plain accumulators
+    assert q.plan_query(wl.config5(), fix_bits=7, plain=True)["acc"] == "i64"
+    assert q.plan_query(wl.config3(), fix_bits=2, plain=True)["acc"] == "f64"
+
+
+@pytest.mark.parametrize("lim", [60000, 120000, 350000, 400000, 1000000])
+def test_fp32_lane_admission(q, lim, monkeypatch):
+    """The FP32-lane scan is planned exactly when every value its plan forms stays below 2^24."""
+    monkeypatch.setenv("QUBO_NO_I16P", "1")
+    monkeypatch.setenv("QUBO_NO_I32Z", "1")
+    Q = wl.upper_int(27, -lim, lim, seed=9)
+    p = q.plan_query(Q, topk=8, walk_bits=5)
+    assert (p["suffix_bits"], p["walk_bits"]) == (9, 5)
+    assert p["acc"] == ("i32f" if fp32_lanes_fit(Q, 9, 5, 4) else "i32")
+
+
+@pytest.mark.parametrize("lim", [300, 900, 1400, 2000, 3000])
+def test_packed_admission(q, lim, monkeypatch):
+    """The packed 16-bit scan is planned exactly when the plan's column range fits 16 bits."""
+    monkeypatch.setenv("QUBO_NO_I32Z", "1")
+    Q = wl.upper_int(24, -lim, lim, seed=11)
+    p = q.plan_query(Q, topk=8, walk_bits=6)
+    lo, hi = column_range(Q, 10, 6, 3)  # default packed variant: 10 suffix bits, 3 register rows
+    assert (p["acc"] == "i16p") == (lo >= -32768 and hi <= 32767), (lo, hi, p)
+
+
+def test_fp32_lanes_fall_back_to_shorter_walks(q, monkeypatch):
+    """Large couplings among variables 13..22 only: with 2^14-step walks variables 21 and 22 are
+    walked and E_L leaves the FP32 lanes' exact range, with 2^12-step walks they are fixed and
+    those couplings go to the int32 prefix part.  The planner takes the shorter walk rather than
+    the int32 kernel; with moderate couplings it keeps the longer one."""
+    monkeypatch.setenv("QUBO_NO_I16P", "1")
+    monkeypatch.setenv("QUBO_NO_I32Z", "1")
+    for big, expect in ((400000, 14), (600000, 12), (800000, 12)):
+        Q = wl.upper_int(40, -1000, 1000, seed=40)
+        Q[13:21, 21:23] = big
+        Q[21, 22] = big
+        assert fp32_lanes_fit(Q, 9, 14, 4) == (expect == 14) and fp32_lanes_fit(Q, 9, 12, 4)
+        p = q.plan_query(Q, fix_bits=2)
+        assert (p["acc"], p["walk_bits"]) == ("i32f", expect), (big, p)
+
+
+def test_factored_rows_of_a_diagonal_instance(q):
+    """A diagonal instance has no couplings at all: every walked row is factored out."""
+    Q = np.diag(np.arange(-15, 15, dtype=np.int32))
+    p = q.plan_query(Q)
+    assert p["acc"] == "i32z" and p["zero_rows"] == p["walk_bits"]
+
+
+def test_plan_query_rejects_bad_arguments(q):
+    Q = wl.upper_int(20, -5, 5, seed=1)
+    for kw in (dict(fix_bits=21), dict(topk=q.QUBO_MAX_TOPK + 1)):
+        with pytest.raises(q.QuboError) as e:
+            q.plan_query(Q, **kw)
+        assert e.value.status == q.QUBO_ERR_ARG
