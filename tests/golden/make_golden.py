@@ -4,6 +4,7 @@
     python tests/golden/make_golden.py cfg4      # 4096 batched instances (~1 h, 8 cores)
     python tests/golden/make_golden.py cfg5_sub  # n=50, one 2^40-state sub-cube (~1 h, 8 cores)
     python tests/golden/make_golden.py cfg3_sub  # n=44 FP32, one 2^40-state sub-cube (~1 h, 8 cores)
+    python tests/golden/make_golden.py cfg3_step # n=44 FP32, one benchmark step of 2^42 states (~4 h)
 
 The inputs come from the seeded generators in paper_2607_04857_gb300/workloads.py; the paper's
 benchmark matrices are uniformly random (Sec. 5.3), so the instances are synthetic stand-ins of
@@ -78,6 +79,10 @@ def cfg3_sub():
     subcube("cfg3_n44_sub40.json", wl.config3(), 44, 3, "workloads.config3()", 4, 9, True)
 
 
+def cfg3_step():
+    subcube("cfg3_n44_step42.json", wl.config3(), 44, 3, "workloads.config3()", 2, 1, True)
+
+
 if __name__ == "__main__":
     for what in sys.argv[1:]:
-        {"cfg2": cfg2, "cfg4": cfg4, "cfg5_sub": cfg5_sub, "cfg3_sub": cfg3_sub}[what]()
+        {"cfg2": cfg2, "cfg4": cfg4, "cfg5_sub": cfg5_sub, "cfg3_sub": cfg3_sub, "cfg3_step": cfg3_step}[what]()
