@@ -45,6 +45,26 @@ constexpr int kFloatMaxWalkBits = 14;
 // L1 and amortise the unit set-up (measured against 2^11..2^16).
 constexpr int kZMaxWalkBits = 14;
 
+// Run fn(lo, hi) over [0, count) split into contiguous ranges on up to one host thread per core,
+// at least min_per_thread items per thread (small counts run on the calling thread).
+template <class F>
+void parallel_ranges(int count, int min_per_thread, F &&fn)
+{
+    const int nt = std::max(1, std::min<int>(count / std::max(1, min_per_thread),
+                                             (int)std::thread::hardware_concurrency()));
+    if (nt <= 1) {
+        fn(0, count);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&fn, count, nt, t] {
+            fn((int)((int64_t)count * t / nt), (int)((int64_t)count * (t + 1) / nt));
+        });
+    for (auto &x : th)
+        x.join();
+}
+
 double now_s()
 {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -1241,20 +1261,10 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
         s.gmin = encode_max(j.acc);
         hs[i] = s;
     };
-    const int nt = ni < 64 ? 1 : std::max(1, std::min<int>(ni / 64, (int)std::thread::hardware_concurrency()));
-    if (nt == 1) {
-        for (int i = 0; i < ni; ++i)
+    parallel_ranges(ni, 64, [&](int lo, int hi) {
+        for (int i = lo; i < hi; ++i)
             stage_one(i);
-    } else {
-        std::vector<std::thread> th;
-        for (int t = 0; t < nt; ++t)
-            th.emplace_back([&, t] {
-                for (int i = (int)((int64_t)ni * t / nt); i < (int)((int64_t)ni * (t + 1) / nt); ++i)
-                    stage_one(i);
-            });
-        for (auto &x : th)
-            x.join();
-    }
+    });
     j.total_items = total;
     j.rec_cap = std::min(ws.rec_cap, record_capacity());
     int bps = scan_blocks_per_sm(j.acc, j.K <= 1, j.variant);
@@ -1754,14 +1764,7 @@ int batch_prepare(const void *Q_packed, const int *n, const size_t *offsets, int
         for (int i = lo; i < hi; ++i)
             pst[i] = prepare((const char *)Q_packed + offsets[i] * esz, n[i], dtype, 0, hs[i]);
     };
-    auto parallel = [&](auto &&fn) {
-        const int nt = std::max(1, std::min<int>(count / 64 + 1, (int)std::thread::hardware_concurrency()));
-        std::vector<std::thread> th;
-        for (int t = 0; t < nt; ++t)
-            th.emplace_back(fn, (int)((int64_t)count * t / nt), (int)((int64_t)count * (t + 1) / nt));
-        for (auto &x : th)
-            x.join();
-    };
+    auto parallel = [&](auto &&fn) { parallel_ranges(count, 64, fn); };
     parallel(prep_range);
     for (int i = 0; i < count; ++i)
         if (pst[i])
@@ -1776,14 +1779,7 @@ int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
 {
     const int count = (int)hs.size();
     std::vector<int> pst(count, QUBO_OK);
-    auto parallel = [&](auto &&fn) {
-        const int nt = std::max(1, std::min<int>(count / 64 + 1, (int)std::thread::hardware_concurrency()));
-        std::vector<std::thread> th;
-        for (int t = 0; t < nt; ++t)
-            th.emplace_back(fn, (int)((int64_t)count * t / nt), (int)((int64_t)count * (t + 1) / nt));
-        for (auto &x : th)
-            x.join();
-    };
+    auto parallel = [&](auto &&fn) { parallel_ranges(count, 64, fn); };
     // one accumulator for the whole batch: the widest any instance needs
     Acc acc = hs[0].acc;
     for (auto &h : hs)
