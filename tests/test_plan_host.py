@@ -94,3 +94,28 @@ def test_plan_query_rejects_bad_arguments(q):
         with pytest.raises(q.QuboError) as e:
             q.plan_query(Q, **kw)
         assert e.value.status == q.QUBO_ERR_ARG
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_plan_shapes_are_consistent(q, seed):
+    """For random instances and sub-cubes: n = split_k + walk_bits + suffix_bits whenever the scan
+    is split (else the sub-cube is evaluated directly), a dense walk covers at least one unrolled
+    body (a factored one at least its 3 factored rows), and the fixed bits of a unit include the
+    sub-cube's."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(12, 64))
+    kind = seed % 3
+    Q = (wl.upper_int(n, -300, 300, seed=seed) if kind == 0 else
+         wl.sparse_int(n, 0.1, -300, 300, seed=seed) if kind == 1 else wl.sk_float32(n, seed=seed))
+    for fb in sorted({0, n // 4, n // 2, max(0, n - 30)}):
+        if n - fb > 63:
+            continue
+        p = q.plan_query(Q, fix_bits=fb)
+        if p["suffix_bits"] == 0:  # evaluated directly
+            assert p["walk_bits"] == 0
+            continue
+        assert p["split_k"] + p["walk_bits"] + p["suffix_bits"] == n, p
+        factored = p["acc"] in ("i32z", "f32z")
+        assert p["split_k"] >= fb and p["walk_bits"] >= (3 if factored else 4), p
+        if factored:
+            assert 3 <= p["zero_rows"] <= p["walk_bits"], p
