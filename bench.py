@@ -344,6 +344,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
     if rank == 0:
         qbuild.build()
     dist = None
@@ -351,10 +352,9 @@ def main():
         import torch.distributed as dist
 
         dist.init_process_group(backend="nccl")
-        dist.barrier(device_ids=[local]) if torch.cuda.is_available() else dist.barrier()
+        dist.barrier(device_ids=[local])  # the other ranks wait for rank 0's build
         if rank != 0:
             qbuild.build()
-    torch.cuda.set_device(local)
     q.load_library()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
