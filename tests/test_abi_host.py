@@ -64,6 +64,36 @@ def test_bad_arguments_are_rejected_before_any_device_work(q):
     assert lib.qubo_solve(Q.ctypes.data, 4, 2, 0, 5000, out.ctypes.data, None, 0, None, None, None, None) == -1
 
 
+def test_every_entry_point_rejects_bad_arguments_on_the_host(q):
+    """Argument errors are QUBO_ERR_ARG and are found before any device work (no GPU here)."""
+    import ctypes
+
+    lib = q.load_library()
+    ARG = q.QUBO_ERR_ARG
+    Q = np.zeros((4, 4), dtype=np.int32)
+    Q70 = np.zeros((70, 70), dtype=np.int32)
+    out = np.zeros(1, dtype=np.int64)
+    codes, E, cnt = np.zeros(8, dtype=np.uint64), np.zeros(8, dtype=np.int64), np.zeros(1, dtype=np.uint64)
+    o = q.Options(fix_bits=9)
+    assert lib.qubo_solve_ex(Q.ctypes.data, 4, 2, ctypes.byref(o), out.ctypes.data, None, 0, None, None, None, None) == ARG
+    assert lib.qubo_solve_ex(Q.ctypes.data, 4, 2, None, None, None, 0, None, None, None, None) == ARG
+    for window in (-1.0, float("nan"), float("inf")):
+        assert lib.qubo_solve_window(Q.ctypes.data, 4, 2, window, None, codes.ctypes.data, E.ctypes.data, 8,
+                                     cnt.ctypes.data, None, None) == ARG
+    assert lib.qubo_solve_window(Q.ctypes.data, 4, 2, 1.0, None, codes.ctypes.data, E.ctypes.data, 8, None, None,
+                                 None) == ARG
+    w = np.zeros(16, dtype=np.uint64)
+    for n, inner, count in ((70, 65, 1), (70, 30, 0), (129, 30, 1), (70, 0, 1)):
+        assert lib.qubo_solve_wide(Q70.ctypes.data, n, 2, inner, 0, count, None, out.ctypes.data, w.ctypes.data, 8,
+                                   None, None, None, None, None) == ARG
+    ns, offs, Qb = np.array([45], dtype=np.int32), np.zeros(1, dtype=np.uint64), np.zeros(45 * 45, dtype=np.int32)
+    for count in (1, 0):  # n = 45 is beyond the batched limit; an empty batch
+        assert lib.qubo_solve_batched(Qb.ctypes.data, ns.ctypes.data, offs.ctypes.data, count, 2, 0, out.ctypes.data,
+                                      None, 0, None, None, None, None) == ARG
+    assert lib.qubo_plan_query(Q.ctypes.data, 4, 2, None, None) == ARG
+    assert lib.qubo_merge(None, None, 8, 0, None) == ARG
+
+
 def _as_result(q, o, scanned):
     return q.Result(o.min, o.n_ties, o.ties, o.topk, o.topk_E, 0, {"states_scanned": scanned})
 
