@@ -18,8 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqubo.so")
 
-SOURCES = ["scan_i32.cu", "scan_i64.cu", "scan_f32.cu", "scan_f64.cu", "scan_i32f.cu", "scan_i16p.cu", "scan_sparse.cu", "finalize.cu", "api.cu", "noalloc.cu"]
-HEADERS = ["internal.h", "scan_impl.cuh", "zscan.h"]
+SOURCES = ["scan_i32.cu", "scan_i64.cu", "scan_f32.cu", "scan_f64.cu", "scan_i32f.cu", "scan_i16p.cu", "scan_sparse.cu", "finalize.cu", "plan.cu", "api.cu", "noalloc.cu"]
+HEADERS = ["internal.h", "scan_impl.cuh", "zscan.h", "host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++20", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 
