@@ -292,7 +292,9 @@ typedef struct {
 /* out = merge(a, b) over disjoint state sets: the smaller minimum wins, tie counts add when
  * the minima are equal, tie codes are merged ascending and cut at cap, the K lowest are
  * merged by (E, code).  out's arrays must hold cap and topk entries; out may alias neither
- * input.  Host only. */
+ * input.  Host only.  QUBO_ERR_ARG for mixed dtypes, topk outside 0..QUBO_MAX_TOPK, missing
+ * output arrays, or an input whose counts its arrays cannot hold (n_written > 0 without ties,
+ * n_topk > 0 without topk / topk_E, n_written > n_ties). */
 int qubo_merge(const qubo_partial *a, const qubo_partial *b, size_t cap, int topk, qubo_partial *out);
 
 /* The same merge for results of qubo_solve_wide (128-bit codes, two words each: bits 0..63

@@ -2368,6 +2368,10 @@ int qubo_merge_wide(const qubo_partial_wide *a, const qubo_partial_wide *b, size
         return QUBO_ERR_ARG;
     if ((cap > 0 && !out->ties) || (topk > 0 && (!out->topk || !out->topk_E)))
         return QUBO_ERR_ARG;
+    for (const qubo_partial_wide *x : {a, b})  // the inputs' arrays must hold what their counts say
+        if (x->n_topk < 0 || x->n_topk > QUBO_MAX_TOPK || (x->n_topk > 0 && (!x->topk || !x->topk_E)) ||
+            (x->n_written > 0 && !x->ties) || x->n_written > x->n_ties)
+            return QUBO_ERR_ARG;
     const bool fl = a->is_float != 0;
     using Code = std::pair<uint64_t, uint64_t>;  // (bits 64..127, bits 0..63): ordered as the code
     auto code = [](const uint64_t *w, size_t t) { return Code(w[2 * t + 1], w[2 * t]); };
@@ -2430,6 +2434,10 @@ int qubo_merge(const qubo_partial *a, const qubo_partial *b, size_t cap, int top
         return QUBO_ERR_ARG;
     if ((cap > 0 && !out->ties) || (topk > 0 && (!out->topk || !out->topk_E)))
         return QUBO_ERR_ARG;
+    for (const qubo_partial *x : {a, b})  // the inputs' arrays must hold what their counts say
+        if (x->n_topk < 0 || x->n_topk > QUBO_MAX_TOPK || (x->n_topk > 0 && (!x->topk || !x->topk_E)) ||
+            (x->n_written > 0 && !x->ties) || x->n_written > x->n_ties)
+            return QUBO_ERR_ARG;
     auto to_part = [&](const qubo_partial *x) {
         Part p;
         p.has = x->states_scanned > 0;

@@ -179,3 +179,29 @@ def test_pack_batch_layout(q):
     assert q.pack_batch(p).packed is p.packed
     with pytest.raises(ValueError):
         q.pack_batch([mats[0], mats[1].astype(np.int32)])
+
+
+def test_merge_rejects_inputs_whose_counts_exceed_their_arrays(q):
+    """qubo_merge / qubo_merge_wide check the inputs' counts against their arrays on the host."""
+    import ctypes
+
+    lib = q.load_library()
+    ties = np.zeros(4, dtype=np.uint64)
+    tk = np.zeros(4, dtype=np.uint64)
+    tkE = np.zeros(4, dtype=np.int64)
+
+    def part(cls=q.Partial, **kw):
+        p = cls(is_float=0, n_topk=0, min_i=0, min_f=0.0, n_ties=1, n_written=1, states_scanned=8,
+                ties=ties.ctypes.data, topk=tk.ctypes.data, topk_E=tkE.ctypes.data)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return p
+
+    for merge, cls in ((lib.qubo_merge, q.Partial), (lib.qubo_merge_wide, q.PartialWide)):
+        out = part(cls)
+        good = part(cls)
+        assert merge(ctypes.byref(good), ctypes.byref(part(cls)), 4, 0, ctypes.byref(out)) == 0
+        for bad in (dict(ties=None), dict(n_topk=2, topk=None), dict(n_topk=2, topk_E=None), dict(n_topk=-1),
+                    dict(n_written=2, n_ties=1)):
+            assert merge(ctypes.byref(good), ctypes.byref(part(cls, **bad)), 4, 0, ctypes.byref(out)) == \
+                q.QUBO_ERR_ARG, bad
