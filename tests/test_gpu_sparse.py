@@ -65,6 +65,19 @@ def test_sparse_plan_shapes(q, walk_bits):
     check_int(r, oracle.solve(Q, topk=12))
 
 
+@pytest.mark.parametrize("n,units", [(25, 1), (26, 2), (28, 8), (29, 16)])
+def test_one_block_kernel_unit_pairing(q, n, units):
+    """The one-block kernel scans the units of a claim two at a time (one E_L pass for both); a
+    claim with a single unit left is scanned alone.  Diagonal-dominated instances factor every
+    walked row, so the kernel runs with 1, 2, 8 and 16 units of 2^25 states."""
+    Q = wl.sparse_int(n, 0.02, -100, 100, seed=n)
+    Q[np.arange(n), np.arange(n)] = np.random.default_rng(n).integers(-400, 400, size=n)
+    r = q.solve(Q, topk=12, walk_bits=14)
+    i = r.info
+    assert (i["acc"], i["zero_rows"], 1 << i["split_k"]) == ("i32z", 14, units), i
+    check_int(r, oracle.solve(Q, topk=12))
+
+
 def test_sparse_subcubes(q):
     Q = wl.sparse_int(40, 0.06, -1000, 1000, seed=40)
     for v in (0, 3, 1000, (1 << 14) - 1):
