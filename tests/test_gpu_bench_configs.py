@@ -158,3 +158,17 @@ def test_n44_fp32_bench_plan_subcube_golden(q):
     assert abs(r.min - g["min"]) <= FLOAT_RTOL * max(1.0, abs(g["min"]))
     assert r.n_ties == g["n_ties"] and r.ties.tolist() == g["ties"] and r.topk.tolist() == g["topk"]
     assert np.allclose(r.topk_E, g["topk_E"], rtol=FLOAT_RTOL, atol=FLOAT_RTOL)
+
+
+def test_n44_fp32_bench_step_golden(q):
+    """One whole benchmark step of the n = 44 FP32 instance (2^42 states, top 2 bits = 1), in the
+    benchmark's plan, against the oracle's stored FP64 result."""
+    g = load_golden("cfg3_n44_step42.json")
+    Q = wl.config3()
+    r = q.solve(Q, topk=16, states_cap=4096, fix_bits=g["fix_bits"], fix_value=g["fix_value"])
+    i = r.info
+    assert (i["acc"], i["walk_bits"], i["anchor_bits"]) == ("f32", 14, 10), i
+    assert i["states_scanned"] == 1 << 42
+    assert abs(r.min - g["min"]) <= FLOAT_RTOL * max(1.0, abs(g["min"]))
+    assert r.n_ties == g["n_ties"] and r.ties.tolist() == g["ties"] and r.topk.tolist() == g["topk"]
+    assert np.allclose(r.topk_E, g["topk_E"], rtol=FLOAT_RTOL, atol=FLOAT_RTOL)
