@@ -102,6 +102,25 @@ def planted(n: int, seed: int, x_star: int | None = None, dtype=np.int32):
     return Q, x_star
 
 
+def decimal_pairs(n: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """Float Q made of n//2 uncoupled variable pairs {a, b} on shuffled positions, each with
+    Q_aa = Q_bb = -v and Q_ab = v for v drawn from {0.1, 0.2, 0.3, 0.7}; an odd n leaves one
+    variable with Q_ii = -v alone.  In exact arithmetic every pair has the three minimisers 01,
+    10 and 11, so the real minimum is taken by 3^(n//2) states; in floating point their sums,
+    formed in different orders, differ in the last bits (near-ties one rounding apart)."""
+    rng = _rng(seed)
+    perm = rng.permutation(n)
+    vals = rng.choice(np.array([0.1, 0.2, 0.3, 0.7]), size=(n + 1) // 2)
+    Q = np.zeros((n, n), dtype=dtype)
+    for p in range(n // 2):
+        a, b = sorted((int(perm[2 * p]), int(perm[2 * p + 1])))
+        Q[a, a] = Q[b, b] = -vals[p]
+        Q[a, b] = vals[p]
+    if n % 2:
+        Q[perm[-1], perm[-1]] = -vals[-1]
+    return Q
+
+
 def diagonal(n: int, seed: int, zeros: int, dtype=np.int32) -> np.ndarray:
     """Diagonal Q with `zeros` zero entries (at random positions) and the rest nonzero."""
     rng = _rng(seed)

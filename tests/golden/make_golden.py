@@ -5,6 +5,7 @@
     python tests/golden/make_golden.py cfg5_sub  # n=50, one 2^40-state sub-cube (~1 h, 8 cores)
     python tests/golden/make_golden.py cfg3_sub  # n=44 FP32, one 2^40-state sub-cube (~1 h, 8 cores)
     python tests/golden/make_golden.py cfg3_step # n=44 FP32, one benchmark step of 2^42 states (~4 h)
+    python tests/golden/make_golden.py cfg5_step # n=50, one benchmark step of 2^43 states (~8 h)
 
 The inputs come from the seeded generators in paper_2607_04857_gb300/workloads.py; the paper's
 benchmark matrices are uniformly random (Sec. 5.3), so the instances are synthetic stand-ins of
@@ -83,6 +84,12 @@ def cfg3_step():
     subcube("cfg3_n44_step42.json", wl.config3(), 44, 3, "workloads.config3()", 2, 1, True)
 
 
+def cfg5_step():
+    # the first timed step of the default benchmark: top 7 bits fixed, sub-cube 5 (after 5 warm-ups)
+    subcube("cfg5_n50_step43.json", wl.config5(), 50, 5, "workloads.config5()", 7, 5, False)
+
+
 if __name__ == "__main__":
     for what in sys.argv[1:]:
-        {"cfg2": cfg2, "cfg4": cfg4, "cfg5_sub": cfg5_sub, "cfg3_sub": cfg3_sub, "cfg3_step": cfg3_step}[what]()
+        {"cfg2": cfg2, "cfg4": cfg4, "cfg5_sub": cfg5_sub, "cfg3_sub": cfg3_sub, "cfg3_step": cfg3_step,
+         "cfg5_step": cfg5_step}[what]()

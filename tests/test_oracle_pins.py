@@ -151,6 +151,60 @@ def test_float_gray_equals_direct_n18():
     assert b.n_candidates < (1 << 18) // 8  # the walk really pre-selects
 
 
+def fixed_order_energies(Q):
+    """FP64 energies of every state summed in the direct evaluator's defining order (i
+    ascending, then j ascending over the folded upper triangle), by numpy over all states at
+    once.  A term of an unset variable adds nothing (adding 0.0 leaves every FP64 value
+    unchanged), so this is the same rounding sequence, written independently."""
+    Q = np.asarray(Q, dtype=np.float64)
+    n = Q.shape[0]
+    U = np.triu(Q + Q.T, 1) + np.diag(np.diag(Q))
+    codes = np.arange(1 << n, dtype=np.int64)
+    X = ((codes[:, None] >> np.arange(n)[None, :]) & 1).astype(bool)
+    acc = np.zeros(1 << n)
+    for i in range(n):
+        acc = np.where(X[:, i], acc + U[i, i], acc)
+        for j in range(i + 1, n):
+            acc = np.where(X[:, i] & X[:, j], acc + U[i, j], acc)
+    return codes, acc
+
+
+@pytest.mark.parametrize("n,seed", [(16, 0), (17, 1), (18, 0), (18, 1), (18, 2)])
+@pytest.mark.parametrize("K", [1, 16])
+def test_float_gray_preselection_keeps_ulp_near_ties(n, seed, K):
+    """Brute force defines the answer (Sec. 1.4): with the FP64 energy fixed by the direct
+    order, the Gray walk's candidate pre-selection must keep every state of the tie set and
+    of the K lowest although its own running energies round differently.  The instances have
+    3^(n//2) exact-arithmetic minimisers split by one or two roundings, and 2^16-step walks
+    cross the re-anchoring period many times.  A pre-selection without its rounding
+    tolerance drops many of them."""
+    Q = wl.decimal_pairs(n, seed=seed)
+    codes, E = fixed_order_energies(Q)
+    emin = E.min()
+    ties = codes[E == emin]
+    near = np.count_nonzero(np.abs(E - emin) <= 1e-12)
+    assert near == 3 ** (n // 2) and len(ties) < near  # rounding really splits the real ties
+    order = np.lexsort((codes, E))
+    for method in (oracle.GRAY, oracle.DIRECT):
+        r = oracle.solve(Q, method=method, topk=K, cap=1 << 16)
+        assert r.min == emin and r.n_ties == len(ties)
+        assert np.array_equal(r.ties, ties)
+        assert np.array_equal(r.topk, codes[order[:K]])
+        assert np.array_equal(r.topk_E, E[order[:K]])
+
+
+@pytest.mark.parametrize("method", [oracle.DIRECT, oracle.GRAY])
+def test_float_zero_matrix_every_state_ties(method):
+    """Float Q = 0: every state has energy exactly 0 and ties with the minimum; the Gray
+    pre-selection's tolerance is then 0 and only a non-strict comparison keeps the states."""
+    n = 16
+    Q = np.zeros((n, n), dtype=np.float32)
+    r = oracle.solve(Q, method=method, topk=5, cap=100)
+    assert r.min == 0.0 and r.n_ties == 1 << n and r.truncated
+    assert np.array_equal(r.ties, np.arange(100, dtype=np.uint64))
+    assert np.array_equal(r.topk, np.arange(5, dtype=np.uint64))
+
+
 # --- special cases with known answers -------------------------------------------------------
 
 @pytest.mark.parametrize("method", [oracle.DIRECT, oracle.GRAY])
