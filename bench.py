@@ -249,6 +249,114 @@ def cpu_oracle_rate_one_core(Q, n: int, target_s: float):
 
 
 # ---------------------------------------------------------------------------------------------
+# secondary measurements on the same GPU (default workload, one GPU)
+# ---------------------------------------------------------------------------------------------
+
+def _timed_problem(q, torch, stream, l2buf, Q, fix_bits, values, **kw):
+    """Device-resident problem over the sub-cubes `values` (first one untimed): states/s from CUDA
+    events on the launching stream around run + fetch, and the last result's info."""
+    prob = q.Problem(Q, **kw)
+    prob.run(fix_bits, values[0], stream)
+    prob.fetch()
+    ev = []
+    infos = []
+    for v in values[1:]:
+        flush_l2(l2buf)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        prob.run(fix_bits, v, stream)
+        r = prob.fetch()
+        b.record(stream)
+        ev.append((a, b))
+        infos.append(r.info)
+    torch.cuda.synchronize()
+    prob.close()
+    secs = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+    states = sum(i["states_scanned"] for i in infos)
+    scan = sum(i["seconds_scan"] for i in infos)
+    return {"value": states / secs, "unit": "states/s", "states_per_step": infos[0]["states_scanned"],
+            "steps": len(infos), "scan_kernel_states_per_s": states / scan if scan > 0 else None,
+            "acc": infos[-1]["acc"]}, infos[-1]
+
+
+def _timed_batch(q, torch, stream, l2buf, mats, reps):
+    """The 4096-instance batch resident on the device, replayed as its CUDA graph: instances/s
+    from CUDA events around replay + fetch, and the per-instance plans used."""
+    batch = q.Batch(mats, topk=0, states_cap=64)
+    batch.run(stream)
+    batch.fetch()
+    ev = []
+    for _ in range(reps):
+        flush_l2(l2buf)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        batch.run(stream)
+        rs = batch.fetch()
+        b.record(stream)
+        ev.append((a, b))
+    torch.cuda.synchronize()
+    secs = sum(a.elapsed_time(b) for a, b in ev) / 1000.0
+    walks = {}
+    for i, Q in enumerate(mats):
+        walks.setdefault(int(Q.shape[0]), set()).add(int(rs[i].info["walk_bits"]))
+    mins = [int(rs[i].min) for i in range(len(mats))]
+    batch.close()
+    return {"value": reps * len(mats) / secs, "unit": "instances/s", "steps": reps,
+            "walk_bits_per_n": {n: sorted(w) for n, w in sorted(walks.items())}}, mins
+
+
+def secondary(q, torch, stream, l2buf, dev, gpu_index):
+    """The same-GPU comparisons: the int32 kernel on the default n=50 step; the n=44 FP32 scan
+    with FP64 rescoring against the plain FP64 scan; the 4096-instance batch as one graph replay
+    (with the default and the autotuned per-n plans) against a host loop of single solves."""
+    out = {}
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    # int32 kernel on the benchmark's own n=50 step (2^43 states, top 7 bits fixed)
+    r, _ = _timed_problem(q, torch, stream, l2buf, wl.config5(), 7, [4, 5, 6, 7], topk=16, int32=True)
+    r["how"] = "QUBO_FLAG_INT32 (int32 lanes), 2^43-state sub-cubes 5..7 of the n=50 instance, top 16"
+    out["n50_int32_kernel"] = r
+    # n=44 FP32 + FP64 rescore on 2^40-state sub-cubes; plain FP64 on 2^36-state sub-cubes
+    Q3 = wl.config3()
+    r32, i32 = _timed_problem(q, torch, stream, l2buf, Q3, 4, [0, 1, 2, 3])
+    r32["how"] = "FP32 scan + FP64 rescore (margin 1e-3), 2^40-state sub-cubes 1..3 of the n=44 instance"
+    r32["fp32_max_abs_err"] = i32["fp32_max_abs_err"]
+    r32["fp32_max_drift"] = i32["fp32_max_drift"]
+    r32["anchor_bits"] = i32["anchor_bits"]
+    r64, _ = _timed_problem(q, torch, stream, l2buf, Q3, 8, [16, 17, 18], plain=True)
+    r64["how"] = "plain FP64 scan (QUBO_FLAG_PLAIN), 2^36-state sub-cubes 17..18 of the n=44 instance"
+    out["n44_fp32_rescore"] = r32
+    out["n44_fp64_plain"] = r64
+    out["fp32_rescore_over_fp64"] = r32["value"] / r64["value"]
+    # 4096-instance batch: graph replay, default plans, then autotuned; host loop of single solves
+    mats = [q.as_qubo_matrix(Q)[0] for Q in wl.config4()]
+    q.autotune_clear()
+    rb, mins0 = _timed_batch(q, torch, stream, l2buf, mats, 3)
+    rb["how"] = "one CUDA-graph replay per step over all 4096 instances (qubo_batch_run), default plans"
+    t = time.perf_counter()
+    tuned = q.autotune_batched(mats)
+    tune_s = time.perf_counter() - t
+    rt, mins1 = _timed_batch(q, torch, stream, l2buf, mats, 3)
+    rt["how"] = "as batched_graph, after qubo_autotune_batched on the batch"
+    rt["tuner"] = dict(tuned, seconds=tune_s)
+    rt["same_minima_as_default"] = mins0 == mins1
+    q.autotune_clear()
+    torch.cuda.synchronize(dev)
+    t = time.perf_counter()
+    for Q in mats:
+        q.solve(Q, states_cap=64, stream=stream)
+    torch.cuda.synchronize(dev)
+    loop = len(mats) / (time.perf_counter() - t)
+    out["batched_graph"] = rb
+    out["batched_graph_tuned"] = rt
+    out["batched_loop"] = {"value": loop, "unit": "instances/s",
+                           "how": "qubo_solve per instance, looped on the host (host clock)"}
+    out["batched_over_loop"] = max(rb["value"], rt["value"]) / loop
+    out["clocks"] = sampler.stop()
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------------------------
 
@@ -329,6 +437,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-loop", action="store_true",
                     help="batched workload: also time a host loop of single solves")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default workload: skip the same-GPU comparisons (int32 kernel, FP32 vs FP64, batched)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -584,6 +694,10 @@ def main():
             roof["issue_roofline"] = {"inst_per_state": ips, "states_per_s": issue,
                                       "frac": (per_launch_states / mean_scan) / issue}
 
+    sec = None
+    if W["name"] == "n50_int32" and world == 1 and not args.no_secondary:
+        sec = secondary(q, torch, stream, l2buf, dev, local)
+
     if rank == 0:
         line = {"metric": W["metric"], "value": value, "unit": W["unit"], "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000 * t_max / args.steps, "higher_is_better": True,
@@ -597,6 +711,8 @@ def main():
                 "scan_kernel_ms_mean": mean_scan * 1000, "context": PAPER_CONTEXT}
         if cpu:
             line["cpu_baseline"] = cpu
+        if sec:
+            line["secondary"] = sec
         if loop_rate:
             line["loop_baseline"] = {"value": loop_rate, "unit": "instances/s",
                                      "how": "qubo_solve per instance, looped on the host"}

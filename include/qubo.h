@@ -79,6 +79,17 @@ typedef enum {
 #define QUBO_FLAG_PLAIN 0x1u  /* scan in the wide accumulator (int64 for integer Q, FP64 for
                                  float Q) instead of int32 / FP32: the plain form used as the
                                  comparison baseline */
+#define QUBO_FLAG_INT32 0x2u  /* integer Q: scan in the int32 kernel, never in packed 16-bit
+                                 lanes, FP32 lanes or the factored scan (all of which give the
+                                 same exact results when the library admits them); the int32
+                                 arithmetic of the paper's method, kept selectable for
+                                 comparison.  int64 is still used when the bound needs it */
+#define QUBO_FLAG_RIGOROUS 0x4u /* float Q: re-anchor the FP32 scan at the longest period whose
+                                 worst-case rounding bound alone guarantees that every state of
+                                 the answer reaches the FP64 rescoring (qubo_result.
+                                 fp32_rigorous_anchor_bits); when no period does, scan in FP64.
+                                 Without it the period is 2^10 steps and the guarantee rests on
+                                 the drift measured at every re-anchoring (fp32_max_drift) */
 
 /*
  * Per-call options.  Zero-initialise and set what you need; zero means "default".
@@ -130,6 +141,15 @@ typedef struct {
     int32_t zero_rows;        /* QUBO_ACC_I32Z: walked variables factored out of the column walk */
     uint64_t h2d_bytes;       /* bytes copied host -> device by this call */
     uint64_t d2h_bytes;       /* bytes copied device -> host by this call */
+    double fp32_err_bound;    /* QUBO_ACC_F32: worst-case rounding error of any state's FP32
+                                 decision value at the run's re-anchoring period (from the folded
+                                 matrix and the plan, every FP32 operation rounded to nearest);
+                                 the candidates are proven complete when 2 * fp32_err_bound <=
+                                 margin.  0 for other accumulators */
+    int32_t fp32_rigorous_anchor_bits; /* QUBO_ACC_F32: longest re-anchoring period (log2 of walk
+                                 steps) at which 2 * fp32_err_bound <= margin; -1 if none, or for
+                                 other accumulators */
+    int32_t reserved_bound;
 } qubo_result;
 
 /*
@@ -342,6 +362,12 @@ int qubo_merge_wide(const qubo_partial_wide *a, const qubo_partial_wide *b, size
  * (sum |U_ij| < 2^30), no K-lowest output.  Beyond them it returns QUBO_ERR_ARG
  * (QUBO_ERR_OVERFLOW for the energy bound); an instance with more than 65536 states at or below
  * the running minimum (massive ties) returns QUBO_ERR_NOMEM instead of results.
+ * qubo_abort() is honoured between kernels, not inside the scan: a call made while the abort is
+ * in force returns QUBO_ERR_TIMEOUT without launching, and one whose scan was running when it
+ * was raised lets that scan finish (at most 2^40 states, well under a second on one GPU) and then
+ * returns QUBO_ERR_TIMEOUT.  (The abort word the scan polls lives in the fixed array and is
+ * cleared by every call; a host-mapped word, as the other entry points use, would need a pinned
+ * allocation.)
  * The first call on each device performs a one-time set-up (it looks up the device address of
  * the array); make that first call before any stream capture.  All calls share the array and it
  * keeps the last call's contents; each call clears what must start at zero.  Calls that overlap
@@ -374,8 +400,23 @@ typedef struct {
  * installed plan. */
 int qubo_autotune(const void *Q_host, int n, qubo_dtype dtype, int fix_bits, qubo_plan *best);
 
-/* Time every compiled variant on a whole batch (inputs as qubo_solve_batched) and install the
- * fastest for later batches of this accumulator on the current device. */
+/* Tune the launch plan of a batch (inputs as qubo_solve_batched) on the current device, the
+ * empirical launch tuning of Sec. 4.2 done per instance size.  The batch runs in one persistent
+ * launch, so one kernel variant (block shape, columns per thread, register rows) serves every
+ * instance; the split is per instance: n = split_k + walk_bits + suffix_bits with the suffix
+ * fixed by the variant.  Step 1 times every compiled variant on the whole batch with the default
+ * walks (each as long as the instance allows).  Step 2 takes the sizes present in the batch in
+ * order of their share of the work and, for each size n, times the whole batch with every
+ * instance of that size walking 1 to 4 bits less (2^1..2^4 times more, shorter work units),
+ * keeping a change only when the batch's device time (tables, scan, reduction) falls by more than
+ * 0.2%.  The winners are installed for (device, accumulator) and per size n; later batches on
+ * this device use them (qubo_solve_batched, qubo_batch_create), single solves do not.
+ * *best receives the variant and the tuned batch rate (states/s); per_n, when not NULL, is an
+ * array of 65 plans indexed by n whose walk_bits is the tuned walk of size n (0 for sizes not in
+ * the batch or evaluated directly) and whose states_per_s is the rate of the final plan.
+ * qubo_autotune_batched is this call with per_n = NULL. */
+int qubo_autotune_batched_ex(const void *Q_packed, const int *n, const size_t *offsets, int count, qubo_dtype dtype,
+                             qubo_plan *best, qubo_plan *per_n);
 int qubo_autotune_batched(const void *Q_packed, const int *n, const size_t *offsets, int count, qubo_dtype dtype,
                           qubo_plan *best);
 
@@ -384,7 +425,7 @@ void qubo_autotune_clear(void);
 
 /* Keep tuned plans across processes: qubo_autotune_save writes the plans installed for the
  * current device to a text file (one line per plan: device name, SM count, accumulator, n,
- * variant, walk bits); qubo_autotune_load installs, for the current device, every plan of the
+ * variant, walk bits; n = 0 is a batch's variant and -n a batch's plan for size n); qubo_autotune_load installs, for the current device, every plan of the
  * file whose device name and SM count match it.  Both return the number of plans written or
  * installed, or a negative qubo_status (QUBO_ERR_ARG for an unreadable file or a bad line). */
 int qubo_autotune_save(const char *path);
@@ -398,7 +439,9 @@ int qubo_autotune_load(const char *path);
 const char *qubo_strerror(int status);
 
 /* Ask every running call on this process to stop at its next work unit (returns
- * QUBO_ERR_TIMEOUT).  Safe from any thread.  qubo_abort_clear() re-arms. */
+ * QUBO_ERR_TIMEOUT); calls made before qubo_abort_clear() return QUBO_ERR_TIMEOUT as well.
+ * qubo_solve_noalloc checks it between its kernels only (see there).  Safe from any thread.
+ * qubo_abort_clear() re-arms. */
 void qubo_abort(void);
 void qubo_abort_clear(void);
 

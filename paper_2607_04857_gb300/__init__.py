@@ -24,6 +24,8 @@ QUBO_OK, QUBO_TRUNCATED = 0, 1
 QUBO_ERR_ARG, QUBO_ERR_OVERFLOW, QUBO_ERR_CUDA = -1, -2, -3
 QUBO_ERR_NOMEM, QUBO_ERR_TIMEOUT, QUBO_ERR_INTERNAL = -4, -5, -6
 QUBO_FLAG_PLAIN = 0x1
+QUBO_FLAG_INT32 = 0x2
+QUBO_FLAG_RIGOROUS = 0x4
 MAX_TOPK = 1024
 
 # every entry point declared in include/qubo.h
@@ -33,7 +35,7 @@ EXPORTS = (
     "qubo_abort_clear", "qubo_device_sm_count", "qubo_version", "qubo_solve_noalloc",
     "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_batch_destroy",
     "qubo_autotune", "qubo_autotune_batched", "qubo_autotune_clear", "qubo_solve_window", "qubo_solve_wide",
-    "qubo_merge_wide", "qubo_autotune_save", "qubo_autotune_load", "qubo_plan_query",
+    "qubo_merge_wide", "qubo_autotune_save", "qubo_autotune_load", "qubo_plan_query", "qubo_autotune_batched_ex",
 )
 WIDE_MAX_N = 128
 QUBO_MAX_TOPK = 1024
@@ -68,6 +70,8 @@ class ResultInfo(ctypes.Structure):
         ("cols_per_thread", ctypes.c_int32), ("threads", ctypes.c_int32), ("blocks", ctypes.c_int32),
         ("passes", ctypes.c_int32), ("kernel_launches", ctypes.c_int32), ("zero_rows", ctypes.c_int32),
         ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
+        ("fp32_err_bound", ctypes.c_double), ("fp32_rigorous_anchor_bits", ctypes.c_int32),
+        ("reserved_bound", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -124,6 +128,7 @@ def load_library(path: str = LIB_PATH):
     lib.qubo_autotune.argtypes = [P, I, I, I, P]
     lib.qubo_solve_window.argtypes = [P, I, I, ctypes.c_double, P, P, P, SZ, P, P, P]
     lib.qubo_autotune_batched.argtypes = [P, P, P, I, I, P]
+    lib.qubo_autotune_batched_ex.argtypes = [P, P, P, I, I, P, P]
     lib.qubo_solve_wide.argtypes = [P, I, I, I, U64, U64, P, P, P, SZ, P, P, P, P, P]
     lib.qubo_merge_wide.argtypes = [P, P, SZ, I, P]
     lib.qubo_autotune_save.argtypes = [ctypes.c_char_p]
@@ -138,7 +143,7 @@ def load_library(path: str = LIB_PATH):
     for name in ("qubo_solve", "qubo_solve_ex", "qubo_solve_batched", "qubo_problem_create", "qubo_problem_run",
                  "qubo_problem_fetch", "qubo_merge", "qubo_device_sm_count", "qubo_solve_noalloc",
                  "qubo_batch_create", "qubo_batch_run", "qubo_batch_fetch", "qubo_autotune",
-                 "qubo_autotune_batched", "qubo_solve_window", "qubo_solve_wide", "qubo_merge_wide",
+                 "qubo_autotune_batched", "qubo_autotune_batched_ex", "qubo_solve_window", "qubo_solve_wide", "qubo_merge_wide",
                  "qubo_autotune_save", "qubo_autotune_load"):
         getattr(lib, name).restype = I
     _lib = lib
@@ -224,6 +229,11 @@ class Result:
         return self.n_ties > len(self.ties)
 
 
+def _flags(plain: bool, int32: bool, rigorous: bool = False) -> int:
+    return (QUBO_FLAG_PLAIN if plain else 0) | (QUBO_FLAG_INT32 if int32 else 0) | \
+        (QUBO_FLAG_RIGOROUS if rigorous else 0)
+
+
 def _check(st: int, where: str) -> int:
     if st < 0:
         raise QuboError(st, where)
@@ -232,15 +242,17 @@ def _check(st: int, where: str) -> int:
 
 def solve(Q, topk: int = 0, states_cap: int = 1 << 16, split_k: int = 0, walk_bits: int = 0, fix_bits: int = 0,
           fix_value: int = 0, plain: bool = False, margin: float = 0.0, time_limit: float = 0.0,
-          stream=None) -> Result:
-    """Exact minimum, tie set and K lowest states (qubo_solve_ex)."""
+          stream=None, int32: bool = False, rigorous: bool = False) -> Result:
+    """Exact minimum, tie set and K lowest states (qubo_solve_ex).  plain: the wide accumulator
+    (QUBO_FLAG_PLAIN); int32: integer Q in the int32 kernel only (QUBO_FLAG_INT32); rigorous:
+    float Q re-anchored where the rounding bound proves the candidates (QUBO_FLAG_RIGOROUS)."""
     lib = load_library()
     Qm, dt = as_qubo_matrix(Q)
     n = Qm.shape[0]
     isf = dt in (QUBO_F32, QUBO_F64)
     edt = np.float64 if isf else np.int64
     o = Options(split_k=split_k, topk=topk, fix_bits=fix_bits, walk_bits=walk_bits, fix_value=fix_value,
-                flags=QUBO_FLAG_PLAIN if plain else 0, margin=margin, time_limit_s=time_limit)
+                flags=_flags(plain, int32, rigorous), margin=margin, time_limit_s=time_limit)
     mn = np.zeros(1, dtype=edt)
     ties = np.zeros(max(states_cap, 0), dtype=np.uint64)
     tk = np.zeros(max(topk, 0), dtype=np.uint64)
@@ -306,13 +318,19 @@ def autotune(Q, fix_bits: int) -> dict:
 
 
 def autotune_batched(Qs) -> dict:
-    """Time the compiled variants on a whole batch and install the fastest (qubo_autotune_batched)."""
+    """Tune a batch's plan on the current device and install it (qubo_autotune_batched_ex): the
+    kernel variant for the whole batch, then the walk length per instance size.  Returns the
+    variant, the tuned batch rate (states/s), the number of timed launches and, per size n
+    present in the batch, the tuned walk (`walk_bits_per_n`)."""
     lib = load_library()
     packed, ns, offs, dt = _pack(Qs)
     p = Plan()
-    _check(lib.qubo_autotune_batched(_ptr(packed), _ptr(ns), _ptr(offs), len(ns), dt, ctypes.byref(p)),
-           "qubo_autotune_batched")
-    return {"variant": p.variant, "walk_bits": p.walk_bits, "states_per_s": p.states_per_s, "trials": p.trials}
+    per_n = (Plan * 65)()
+    _check(lib.qubo_autotune_batched_ex(_ptr(packed), _ptr(ns), _ptr(offs), len(ns), dt, ctypes.byref(p), per_n),
+           "qubo_autotune_batched_ex")
+    walks = {m: per_n[m].walk_bits for m in range(65) if per_n[m].walk_bits > 0}
+    return {"variant": p.variant, "walk_bits": p.walk_bits, "states_per_s": p.states_per_s, "trials": p.trials,
+            "walk_bits_per_n": walks}
 
 
 def autotune_clear() -> None:
@@ -418,18 +436,18 @@ def solve_wide(Q, n_inner: int, outer_begin: int = 0, outer_count: int | None = 
 
 
 def plan_query(Q, topk: int = 0, split_k: int = 0, walk_bits: int = 0, fix_bits: int = 0, fix_value: int = 0,
-               plain: bool = False) -> dict:
+               plain: bool = False, int32: bool = False, rigorous: bool = False, margin: float = 0.0) -> dict:
     """The plan a solve with these options would run (qubo_plan_query), computed on the host alone:
     accumulator, split, walk, suffix bits, columns per thread, factored rows, anchoring period."""
     lib = load_library()
     Qm, dt = as_qubo_matrix(Q)
     o = Options(split_k=split_k, topk=topk, fix_bits=fix_bits, walk_bits=walk_bits, fix_value=fix_value,
-                flags=QUBO_FLAG_PLAIN if plain else 0)
+                flags=_flags(plain, int32, rigorous), margin=margin)
     info = ResultInfo()
     _check(lib.qubo_plan_query(_ptr(Qm), Qm.shape[0], dt, ctypes.byref(o), ctypes.byref(info)), "qubo_plan_query")
     d = info.as_dict()
     return {k: d[k] for k in ("acc", "n", "split_k", "walk_bits", "suffix_bits", "cols_per_thread", "zero_rows",
-                              "anchor_bits")}
+                              "anchor_bits", "fp32_err_bound", "fp32_rigorous_anchor_bits")}
 
 
 def solve_window(Q, window: float, cap: int = 1 << 16, fix_bits: int = 0, fix_value: int = 0, plain: bool = False,
@@ -485,13 +503,13 @@ class Problem:
     """Device-resident problem: upload once, run sub-cubes, fetch (qubo_problem_*)."""
 
     def __init__(self, Q, topk: int = 0, split_k: int = 0, walk_bits: int = 0, plain: bool = False,
-                 margin: float = 0.0, time_limit: float = 0.0):
+                 margin: float = 0.0, time_limit: float = 0.0, int32: bool = False, rigorous: bool = False):
         self._lib = load_library()
         Qm, dt = as_qubo_matrix(Q)
         self.n = Qm.shape[0]
         self.topk = topk
         self.is_float = dt in (QUBO_F32, QUBO_F64)
-        o = Options(split_k=split_k, topk=topk, walk_bits=walk_bits, flags=QUBO_FLAG_PLAIN if plain else 0,
+        o = Options(split_k=split_k, topk=topk, walk_bits=walk_bits, flags=_flags(plain, int32, rigorous),
                     margin=margin, time_limit_s=time_limit)
         h = ctypes.c_void_p()
         _check(self._lib.qubo_problem_create(_ptr(Qm), self.n, dt, ctypes.byref(o), ctypes.byref(h)),

@@ -31,7 +31,6 @@ namespace {
 
 constexpr unsigned long long kDefaultRecCap = 1ull << 22;  // candidate records per job (64 MiB)
 constexpr unsigned long long kBatchGraphRecords = 1ull << 18;  // candidate records of a replayed batch
-constexpr double kDefaultMargin = 1e-3;
 // Run fn(lo, hi) over [0, count) split into contiguous ranges on up to one host thread per core,
 // at least min_per_thread items per thread (small counts run on the calling thread).
 template <class F>
@@ -911,7 +910,7 @@ struct SolveStats {
 int solve_range(Workspace &ws, HostInst &h, int fix_bits, uint64_t fix_value, const SolveCfg &c,
                 cudaStream_t stream, Part &out, SolveStats &stats, double t_deadline)
 {
-    int st = plan_run(h, fix_bits, fix_value, c.split_k, c.walk_bits, c.variant, c.flags);
+    int st = plan_run(h, fix_bits, fix_value, c.split_k, c.walk_bits, c.variant, c.flags, c.margin);
     if (st)
         return st;
     h.thr0 = threshold_bound(h, std::max(1, c.K));
@@ -1114,7 +1113,37 @@ void fill_plan_info(const HostInst &h, const SolveStats &stats, double t0, qubo_
     info->passes = stats.passes;
 }
 
+// The FP32 scan's worst-case rounding bound at the run's re-anchoring period and the longest
+// period at which it alone proves the candidates (single-instance results).
+void fill_fp32_bound(const HostInst &h, double margin, qubo_result *info)
+{
+    if (!info)
+        return;
+    info->fp32_err_bound = 0.0;
+    info->fp32_rigorous_anchor_bits = -1;
+    if (h.acc != ACC_F32 || h.small)
+        return;
+    info->fp32_err_bound = fp32_error_bound(h, std::min(h.anchor_bits, h.L), margin);
+    info->fp32_rigorous_anchor_bits = fp32_rigorous_anchor_bits(h, margin);
+}
+
 int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order);
+
+// Walk length of a batched instance in (acc, variant): the walk the batch autotuner installed
+// for its size under this variant, else as long as the instance allows (at most wmax); 0 when
+// the instance is too small to split.  h.acc and h.variant must be set.
+int batch_walk(Acc acc, int variant, const HostInst &h, int wmax)
+{
+    const int B = acc_suffix_bits(acc, variant);
+    const int rmin = variant_reg_rows(h) + 1;
+    if (h.n - B < rmin)
+        return 0;
+    int walk = std::min(wmax, h.n - B);
+    int tv = 0, tw = 0;
+    if (tuned_plan(acc, -h.n, &tv, &tw) && tv == variant && tw >= rmin && tw <= walk)
+        walk = tw;
+    return walk;
+}
 
 // Fold, bound, plan and threshold every instance of a batch (in parallel on the host), one
 // accumulator for all, and the launch order (longest work first, so the persistent launch's
@@ -1171,10 +1200,8 @@ int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
         for (int i = lo; i < hi; ++i) {
             HostInst &h = hs[i];
             h.variant = acc_bytes(acc) == 4 ? variant : 0;
-            const int B = acc_suffix_bits(acc, h.variant);
             const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
-            const int walk = h.n - B >= variant_reg_rows(h) + 1 ? std::min(wmax, h.n - B) : 0;
-            pst[i] = plan(h, 0, 0, 0, walk);
+            pst[i] = plan(h, 0, 0, 0, batch_walk(acc, h.variant, h, wmax));
             // batches are many small instances: fewer descents (K = 1 thresholds also tighten on
             // the device as soon as a lower state is found)
             if (!pst[i])
@@ -1208,9 +1235,7 @@ int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
                 HostInst &h = hs[i];
                 h.acc = alt_acc;
                 h.variant = v2;
-                const int B = acc_suffix_bits(alt_acc, v2);
-                const int walk = h.n - B >= variant_reg_rows(h) + 1 ? std::min(alt_walk, h.n - B) : 0;
-                const bool ok = plan(h, 0, 0, 0, walk) == QUBO_OK &&
+                const bool ok = plan(h, 0, 0, 0, batch_walk(alt_acc, v2, h, alt_walk)) == QUBO_OK &&
                                 (h.small || (alt_acc == ACC_I16P ? i16p_exact(h) : i32f_exact(h, &h.clampC)));
                 if (!ok)
                     all = false;
@@ -1375,6 +1400,8 @@ void wide_add(WideAcc &w, const Part &p, int n_in, uint64_t outer, int64_t ci, d
 
 }  // namespace
 
+bool qubo::abort_requested() { return g_abort_all.load() != 0; }
+
 // ================================================================================================
 // C ABI
 // ================================================================================================
@@ -1500,6 +1527,7 @@ int qubo_solve_ex(const void *Q_host, int n, qubo_dtype dtype, const qubo_option
         std::memset(info, 0, sizeof(*info));
     fill_outputs(h, p, o.topk, states_cap, out_min, out_states, out_topk, out_topk_E, info);
     fill_plan_info(h, stats, t0, info);
+    fill_fp32_bound(h, o.margin > 0 ? o.margin : kDefaultMargin, info);
     return p.n_ties > states_cap ? QUBO_TRUNCATED : QUBO_OK;
 }
 
@@ -1518,11 +1546,12 @@ int qubo_plan_query(const void *Q_host, int n, qubo_dtype dtype, const qubo_opti
     if (o.fix_bits < 0 || o.fix_bits > n)
         return QUBO_ERR_ARG;
     const SolveCfg c = solve_cfg(h, o, 0, -1.0);
-    if ((st = plan_run(h, o.fix_bits, o.fix_value, c.split_k, c.walk_bits, c.variant, c.flags)))
+    if ((st = plan_run(h, o.fix_bits, o.fix_value, c.split_k, c.walk_bits, c.variant, c.flags, c.margin)))
         return st;
     std::memset(info, 0, sizeof(*info));
     info->acc = (int32_t)h.acc;
     fill_plan_info(h, SolveStats(), t0, info);
+    fill_fp32_bound(h, c.margin, info);
     return QUBO_OK;
 }
 
@@ -1563,6 +1592,7 @@ int qubo_solve_window(const void *Q_host, int n, qubo_dtype dtype, double window
         std::memset(info, 0, sizeof(*info));
     fill_outputs(h, p, 0, 0, nullptr, nullptr, nullptr, nullptr, info);
     fill_plan_info(h, stats, t0, info);
+    fill_fp32_bound(h, o.margin > 0 ? o.margin : kDefaultMargin, info);
     *out_count = p.win.size();
     const size_t nw = std::min(cap, p.win.size());
     for (size_t t = 0; t < nw; ++t) {
@@ -1849,7 +1879,8 @@ int qubo_problem_run(qubo_problem *p, int fix_bits, uint64_t fix_value, void *st
     p->fix_value = fix_value;
     p->stream = (cudaStream_t)stream;
     int st = plan_run(p->h, fix_bits, fix_value, p->opt.split_k, p->opt.walk_bits,
-                      std::getenv("QUBO_SCAN_VARIANT") ? scan_variant(p->h.acc) : -1, p->opt.flags);
+                      std::getenv("QUBO_SCAN_VARIANT") ? scan_variant(p->h.acc) : -1, p->opt.flags,
+                      p->opt.margin > 0 ? p->opt.margin : kDefaultMargin);
     if (st)
         return st;
     p->h.thr0 = threshold_bound(p->h, std::max(1, p->opt.topk));
@@ -1900,6 +1931,7 @@ int qubo_problem_fetch(qubo_problem *p, void *out_min, uint64_t *out_states, siz
         std::memset(info, 0, sizeof(*info));
     fill_outputs(p->h, part, p->opt.topk, states_cap, out_min, out_states, out_topk, out_topk_E, info);
     fill_plan_info(p->h, stats, p->t0, info);
+    fill_fp32_bound(p->h, p->opt.margin > 0 ? p->opt.margin : kDefaultMargin, info);
     (void)cap;
     return part.n_ties > states_cap ? QUBO_TRUNCATED : QUBO_OK;
 }
@@ -2210,19 +2242,36 @@ int qubo_autotune(const void *Q_host, int n, qubo_dtype dtype, int fix_bits, qub
     return QUBO_OK;
 }
 
-int qubo_autotune_batched(const void *Q_packed, const int *n, const size_t *offsets, int count, qubo_dtype dtype,
-                          qubo_plan *best)
+int qubo_autotune_batched_ex(const void *Q_packed, const int *n, const size_t *offsets, int count, qubo_dtype dtype,
+                             qubo_plan *best, qubo_plan *per_n)
 {
     if (!best)
         return QUBO_ERR_ARG;
     std::memset(best, 0, sizeof(*best));
+    if (per_n)
+        std::memset(per_n, 0, sizeof(qubo_plan) * 65);
+    // start from the untuned plans: forget the batch plans installed on this device
+    {
+        int d = -1;
+        if (cudaGetDevice(&d) != cudaSuccess) {
+            cudaGetLastError();
+            return QUBO_ERR_CUDA;
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto it = g_tuned.begin(); it != g_tuned.end();)
+            it = (std::get<0>(it->first) == d && std::get<2>(it->first) <= 0) ? g_tuned.erase(it) : std::next(it);
+    }
     std::vector<HostInst> hs;
     std::vector<int> order;
     int st = batch_prepare(Q_packed, n, offsets, count, dtype, 0, hs, order);
     if (st)
         return st;
     const Acc acc = hs[0].acc;
-    const int nvar = acc_bytes(acc) == 4 ? kScanVariants : 1;
+    const bool lanes4 = acc_bytes(acc) == 4;
+    const int nvar = lanes4 ? kScanVariants : 1;
+    // the untuned walk, as in batch_plan: as long as the instance allows, at most wmax (integers
+    // in FP32 lanes: 2^14 steps when exact, else 2^12)
+    const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : (acc == ACC_I32F ? kI32FMaxWalkBits : kDefaultMaxWalkBits);
     Workspace *ws = nullptr;
     if ((st = resolve_device(&ws)))
         return st;
@@ -2231,49 +2280,152 @@ int qubo_autotune_batched(const void *Q_packed, const int *n, const size_t *offs
     cudaGetDevice(&dev);
     if ((st = ws->init(dev)))
         return st;
-    double best_t = 0.0;
-    for (int v = 0; v < nvar; ++v) {
-        std::vector<HostInst> hv = hs;
-        bool ok = true;
-        for (auto &h : hv) {
-            h.variant = acc_bytes(acc) == 4 ? v : 0;
-            const int B = acc_suffix_bits(acc, h.variant);
-            const int wmax = acc == ACC_F32 ? kFloatMaxWalkBits : kDefaultMaxWalkBits;
-            const int walk = h.n - B >= reg_rows_of(acc, v) + 1 ? std::min(wmax, h.n - B) : 0;
+    uint64_t states = 0;
+    for (auto &h : hs)
+        states += 1ull << h.n;
+
+    // Plan instance h under variant v with walk w (0: the untuned rule); false when the plan is
+    // not admitted (too short a walk, or lanes that would not stay exact).
+    auto plan_one = [&](HostInst &h, int v, int w) -> bool {
+        h.acc = acc;
+        h.variant = lanes4 ? v : 0;
+        const int B = acc_suffix_bits(acc, h.variant);
+        const int rmin = reg_rows_of(acc, h.variant) + 1;
+        const int wd = h.n - B >= rmin ? std::min(wmax, h.n - B) : 0;
+        if (w > 0 && (w < rmin || w > wd))
+            return false;
+        auto admitted = [&](int walk) {
             if (plan(h, 0, 0, 0, walk))
-                ok = false;
-            else if (!h.small && ((acc == ACC_I16P && !i16p_exact(h)) || (acc == ACC_I32F && !i32f_exact(h, &h.clampC))))
-                ok = false;  // this variant's plan leaves the batch's lanes inexact
-        }
-        if (!ok)
-            continue;
-        double t = 0.0;
+                return false;
+            if (h.small)
+                return true;
+            if (acc == ACC_I16P)
+                return i16p_exact(h);
+            if (acc == ACC_I32F)
+                return i32f_exact(h, &h.clampC);
+            return true;
+        };
+        if (w > 0)
+            return admitted(w);
+        if (admitted(wd))
+            return true;
+        return acc == ACC_I32F && wd > kDefaultMaxWalkBits && admitted(kDefaultMaxWalkBits);
+    };
+    // Device time (tables, scan, reduction) of one launch over the whole batch, best of two.
+    auto time_batch = [&](std::vector<HostInst> &hv, int v, double *t) -> int {
+        *t = 0.0;
         for (int rep = 0; rep < 2; ++rep) {
             Job j;
             for (int i : order)
                 j.insts.push_back(&hv[i]);
             j.acc = acc;
-            j.variant = acc_bytes(acc) == 4 ? v : 0;
+            j.variant = lanes4 ? v : 0;
             j.margin = kDefaultMargin;
             std::vector<Part> parts;
             double gs = 0.0;
-            if ((st = job_launch(*ws, j)) || (st = job_finish(*ws, j, parts, &gs)))
-                return st;
-            t = j.scan_seconds;
+            int e;
+            if ((e = job_launch(*ws, j)) || (e = job_finish(*ws, j, parts, &gs)))
+                return e;
+            if (gs > 0 && (*t == 0.0 || gs < *t))
+                *t = gs;
         }
         best->trials += 1;
+        return QUBO_OK;
+    };
+
+    // Step 1: the kernel variant, every instance on the untuned walk.
+    double best_t = 0.0;
+    int vbest = -1;
+    std::vector<HostInst> hbest;
+    for (int v = 0; v < nvar; ++v) {
+        std::vector<HostInst> hv = hs;
+        bool ok = true;
+        for (auto &h : hv)
+            ok = ok && plan_one(h, v, 0);
+        if (!ok)
+            continue;
+        double t = 0.0;
+        if ((st = time_batch(hv, v, &t)))
+            return st;
         if (t > 0 && (best_t == 0.0 || t < best_t)) {
             best_t = t;
-            best->variant = v;
-            uint64_t states = 0;
-            for (auto &h : hv)
-                states += h.states;
-            best->states_per_s = (double)states / t;
+            vbest = v;
+            hbest = std::move(hv);
         }
     }
-    if (best_t > 0)
-        install_plan(acc, 0, best->variant, 0);
+    if (vbest < 0)
+        return QUBO_OK;  // no variant admitted: nothing installed
+
+    // Step 2: per instance size, in order of the size's share of the work, shorter walks for
+    // every instance of that size; a change is kept when the batch's device time falls by more
+    // than 0.2%.
+    std::map<int, uint64_t> work;
+    for (auto &h : hbest)
+        if (!h.small)
+            work[h.n] += 1ull << h.n;
+    std::vector<std::pair<uint64_t, int>> sizes;
+    for (auto &kv : work)
+        sizes.push_back({kv.second, kv.first});
+    std::sort(sizes.rbegin(), sizes.rend());
+    std::map<int, int> walk_of;  // n -> tuned walk
+    std::map<int, int> trials_of;
+    for (auto &sz : sizes) {
+        const int nn = sz.second;
+        int wcur = 0;
+        for (auto &h : hbest)
+            if (h.n == nn) {
+                wcur = h.L;
+                break;
+            }
+        const int w0 = wcur;
+        for (int w = w0 - 1; w >= w0 - 4; --w) {
+            std::vector<PlanFields> saved;
+            std::vector<int> idx;
+            bool ok = true;
+            for (int i = 0; i < (int)hbest.size() && ok; ++i)
+                if (hbest[i].n == nn) {
+                    idx.push_back(i);
+                    saved.push_back(plan_fields(hbest[i]));
+                    ok = plan_one(hbest[i], vbest, w);
+                }
+            double t = 0.0;
+            if (ok) {
+                if ((st = time_batch(hbest, vbest, &t)))
+                    return st;
+                trials_of[nn] += 1;
+            }
+            if (ok && t > 0 && t < best_t * (1.0 - 2e-3)) {
+                best_t = t;
+                wcur = w;
+            } else {
+                for (size_t q = 0; q < idx.size(); ++q)
+                    set_plan_fields(hbest[idx[q]], saved[q]);
+                if (!ok)
+                    break;  // shorter walks are not admitted either
+            }
+        }
+        walk_of[nn] = wcur;
+    }
+    install_plan(acc, 0, vbest, 0);
+    for (auto &kv : walk_of)
+        install_plan(acc, -kv.first, vbest, kv.second);
+    best->variant = vbest;
+    best->walk_bits = 0;
+    best->states_per_s = (double)states / best_t;
+    if (per_n)
+        for (auto &kv : walk_of) {
+            per_n[kv.first].variant = vbest;
+            per_n[kv.first].walk_bits = kv.second;
+            per_n[kv.first].states_per_s = best->states_per_s;
+            per_n[kv.first].trials = trials_of[kv.first];
+        }
     return QUBO_OK;
+}
+
+int qubo_autotune_batched(const void *Q_packed, const int *n, const size_t *offsets, int count, qubo_dtype dtype,
+                          qubo_plan *best)
+{
+    return qubo_autotune_batched_ex(Q_packed, n, offsets, count, dtype, best, nullptr);
 }
 
 void qubo_autotune_clear(void)
@@ -2341,7 +2493,7 @@ int qubo_autotune_load(const char *path)
         char *tab = std::strchr(line, '\t');
         int fs = 0, acc = 0, n = 0, variant = 0, walk = 0;
         if (!tab || std::sscanf(tab + 1, "%d\t%d\t%d\t%d\t%d", &fs, &acc, &n, &variant, &walk) != 5 ||
-            acc < ACC_I32 || acc > ACC_F32Z || n < 0 || n > 64 || variant < 0 || variant >= kScanVariants ||
+            acc < ACC_I32 || acc > ACC_F32Z || n < -64 || n > 64 || variant < 0 || variant >= kScanVariants ||
             walk < 0 || walk > kMaxWalkBits) {
             st = QUBO_ERR_ARG;
             break;

@@ -14,6 +14,7 @@ namespace qubo {
 namespace host {
 
 constexpr int kTargetUnitsLog2 = 15;   // aim for >= 2^15 work units per scan
+constexpr double kDefaultMargin = 1e-3; // FP32 scans: candidate margin above the running minimum
 constexpr int kDefaultMaxWalkBits = 12;
 // Integers in FP32 lanes: 2^14-step walks (n=50: 0.7% faster than 2^12) when the plan stays exact
 // in FP32 lanes, else the default length is tried.
@@ -32,6 +33,14 @@ inline double now_s()
 {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
+
+// Plan-dependent magnitudes of the FP32 scan's rounding bound (fp32_error_bound), cached per plan.
+struct Fp32BoundTerms {
+    bool valid = false;
+    int n = 0, B = 0, L = 0, rc = 0;
+    double margin = 0.0;
+    double Cc = 0.0, CP = 0.0, Ecol0 = 0.0, EP0 = 0.0, rest = 0.0;
+};
 
 // One instance prepared on the host and the plan of its current run.
 struct HostInst {
@@ -55,6 +64,7 @@ struct HostInst {
     std::vector<uint8_t> perm;  // ACC_I32Z / ACC_F32Z: caller's variable at each scan position
     bool no_factored = false;   // the factored FP32 scan used up its margin: plan the dense one
     int anchor_bits = kFloatAnchorBits;  // ACC_F32: re-anchoring period (log2 of walk steps)
+    mutable Fp32BoundTerms fp32_terms;   // ACC_F32: cached magnitudes of the rounding bound
 };
 
 // The plan part of a HostInst (what plan() and the exactness checks set), saved and restored
@@ -99,10 +109,17 @@ int zero_rows_search(HostInst &h);
 bool i32z_allowed();
 bool plan_factored(HostInst &h, Acc acc, int fix_bits, uint64_t fix_value, int split_k, int walk_bits);
 int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bits, int variant_req,
-             uint32_t flags);
+             uint32_t flags, double margin = kDefaultMargin);
 
 // Initial threshold: a bound on the K-th lowest energy of the run's sub-cube from greedy descents.
 double threshold_bound(const HostInst &h, int K, int restarts = 24);
+
+// Dense FP32 scan: worst-case rounding error of a state's decision value at a re-anchoring period
+// of 2^anchor_bits walk steps, and the longest period whose bound alone guarantees the candidates
+// (2 bound <= margin; -1 if none).  0 / -1 for other accumulators.
+const Fp32BoundTerms &fp32_bound_terms(const HostInst &h, double margin);
+double fp32_error_bound(const HostInst &h, int anchor_bits, double margin);
+int fp32_rigorous_anchor_bits(const HostInst &h, double margin);
 
 }  // namespace host
 }  // namespace qubo

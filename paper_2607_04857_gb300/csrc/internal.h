@@ -175,4 +175,8 @@ cudaError_t launch_extract(const Inst *d_inst, const Rec *rec, const unsigned lo
                            ResOut *res, uint64_t *ties, uint64_t *topk_codes, int64_t *topk_e,
                            unsigned long long *d_starts, cudaStream_t s);
 
+// ---- host state shared by the entry points (api.cu) --------------------------------------------
+// True while qubo_abort() is in force (until qubo_abort_clear()).
+bool abort_requested();
+
 }  // namespace qubo

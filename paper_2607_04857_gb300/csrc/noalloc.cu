@@ -47,14 +47,14 @@ int scratch_for_device(int dev, unsigned char **out)
     return QUBO_OK;
 }
 
-size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Byte offsets of the regions inside the scratch array.
 struct Layout {
     size_t inst, state, items, ctr, abort, W, Es, M, EL, rec, res, starts, ties, end;
 };
 
-Layout layout(int n, int L, size_t cap)
+constexpr Layout layout(int n, int L, size_t cap)
 {
     Layout l{};
     size_t o = 0;
@@ -87,6 +87,21 @@ Layout layout(int n, int L, size_t cap)
     l.end = o;
     return l;
 }
+
+// Walk length of the plan at n variables (the largest layout is the one at the largest n).
+constexpr int walk_bits_of(int n)
+{
+    const int L = n - kB - 15;
+    return L < kRegRows + 1 ? kRegRows + 1 : (L > kMaxWalk ? kMaxWalk : L);
+}
+
+// The header (Inst, InstState, item bases, counters, abort word, symmetric int32 matrix) is staged
+// in one stack buffer of this size.
+constexpr size_t kHeaderBytes = 8192;
+constexpr Layout kLargest = layout(QUBO_NOALLOC_MAX_N, walk_bits_of(QUBO_NOALLOC_MAX_N), QUBO_NOALLOC_MAX_TIES);
+static_assert(kLargest.end <= kScratchBytes, "the largest admitted problem must fit the scratch array");
+static_assert(kLargest.W + sizeof(int32_t) * QUBO_NOALLOC_MAX_N * QUBO_NOALLOC_MAX_N <= kHeaderBytes,
+              "the largest admitted header must fit its stack buffer");
 
 // Energy of one state with the folded matrix (fixed summation order).
 int64_t energy_host(const int64_t (*U)[QUBO_NOALLOC_MAX_N], int n, uint64_t x)
@@ -182,13 +197,14 @@ extern "C" int qubo_solve_noalloc(const void *Q_host, int n, qubo_dtype dtype, i
     const int small = n < kB + kRegRows + 1;
     int L = 0, k = 0;
     if (!small) {
-        L = n - kB - 15;
-        L = L < kRegRows + 1 ? kRegRows + 1 : (L > kMaxWalk ? kMaxWalk : L);
+        L = walk_bits_of(n);
         k = n - kB - L;
     }
     const Layout lo = layout(n, small ? 1 : L, states_cap);
     if (lo.end > kScratchBytes)
-        return QUBO_ERR_ARG;
+        return QUBO_ERR_INTERNAL;  // excluded at compile time for every admitted n and states_cap
+    if (abort_requested())
+        return QUBO_ERR_TIMEOUT;
 
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -201,10 +217,10 @@ extern "C" int qubo_solve_noalloc(const void *Q_host, int n, qubo_dtype dtype, i
         return st;
 
     // header staged in one stack buffer: Inst, InstState, item bases, symmetric int32 matrix
-    alignas(16) unsigned char hdr[8192];
+    alignas(16) unsigned char hdr[kHeaderBytes];
     const size_t hdr_bytes = lo.W + sizeof(int32_t) * n * n;
     if (hdr_bytes > sizeof(hdr))
-        return QUBO_ERR_ARG;
+        return QUBO_ERR_INTERNAL;  // excluded at compile time for every admitted n
     std::memset(hdr, 0, hdr_bytes);
     Inst d{};
     d.n = n;
@@ -274,6 +290,8 @@ extern "C" int qubo_solve_noalloc(const void *Q_host, int n, qubo_dtype dtype, i
     unsigned long long nrec = 0;
     NA_CK(cudaMemcpyAsync(&nrec, base + lo.ctr + sizeof(unsigned long long), sizeof(nrec), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
+    if (abort_requested())
+        return QUBO_ERR_TIMEOUT;  // raised while the scan ran; its abort word is not watched
     if (nrec > kRecords)
         return QUBO_ERR_NOMEM;  // more candidates than the fixed scratch holds
     unsigned long long P = 1;

@@ -463,15 +463,31 @@ bool plan_factored(HostInst &h, Acc acc, int fix_bits, uint64_t fix_value, int s
 }
 
 int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int walk_bits, int variant_req,
-             uint32_t flags)
+             uint32_t flags, double margin)
 {
     if ((h.acc == ACC_F32 || h.acc == ACC_F32Z) && !(flags & QUBO_FLAG_PLAIN)) {
-        if (i32z_allowed() && !h.no_factored && plan_factored(h, ACC_F32Z, fix_bits, fix_value, split_k, walk_bits))
+        // the rounding bound is derived for the dense FP32 scan only
+        if (!(flags & QUBO_FLAG_RIGOROUS) && i32z_allowed() && !h.no_factored &&
+            plan_factored(h, ACC_F32Z, fix_bits, fix_value, split_k, walk_bits))
             return QUBO_OK;
         h.acc = ACC_F32;
+        if (flags & QUBO_FLAG_RIGOROUS) {
+            h.variant = pick_variant(h.acc, variant_req);
+            int st = plan(h, fix_bits, fix_value, split_k, walk_bits);
+            if (st)
+                return st;
+            if (h.small)
+                return QUBO_OK;
+            const int a = fp32_rigorous_anchor_bits(h, margin);
+            if (a >= 0) {
+                h.anchor_bits = std::min(h.anchor_bits, a);
+                return QUBO_OK;
+            }
+            h.acc = ACC_F64;  // no period is short enough: the FP64 scan
+        }
     }
     if ((h.acc == ACC_I32 || h.acc == ACC_I32F || h.acc == ACC_I16P || h.acc == ACC_I32Z) &&
-        !(flags & QUBO_FLAG_PLAIN)) {
+        !(flags & (QUBO_FLAG_PLAIN | QUBO_FLAG_INT32))) {
         Acc chosen = ACC_I32;
         // sparse instances: at least 3 walked rows factored out (8x fewer column updates)
         if (i32z_allowed() && plan_factored(h, ACC_I32Z, fix_bits, fix_value, split_k, walk_bits))
@@ -590,6 +606,163 @@ double threshold_bound(const HostInst &h, int K, int restarts)
         t = std::nearbyint(t);
     }
     return std::min(t, h.beta);
+}
+
+}  // namespace host
+}  // namespace qubo
+
+namespace qubo {
+namespace host {
+
+// ---- rigorous rounding bound of the dense FP32 scan ----------------------------------------------
+// The FP32 scan (Sec. 6.2, mixed precision with periodic correction) decides per state whether
+// it reaches the threshold: column (E_s(j) + lin(j) + rows of the set walked bits, updated by one
+// FP32 add or FMA per Gray step) + E_L(g) <= T + margin - P.  Every FP32 operation rounds to
+// nearest, so its error is at most u = 2^-24 times the magnitude of its result; the tables are
+// summed in FP64 and rounded once.  With magnitudes computed from the folded matrix for the
+// run's split (suffix S = bits [0, B), walked bits [B, B + L), fixed bits F = the rest):
+//   Cc    = max_j |E_s(j)| + sum_{i outside S} |c_i(j)| + sum_{r < RC} rF(r), with
+//           c_i(j) = sum_{b in j} U_bi: bounds every column value (the register rows carry their
+//           fixed couplings w_r) and every partial sum that forms one;
+//   CL    = max_g |E_L(g)|;  bF = sum |U| within F;  rF(v) = sum_{f in F} |U_vf|;
+//   rS(r) = sum_{b in S} |U_rb|;  CabsF = sum_{b in S} rF(b);  CP = bF + sum_{r >= RC} rF(r);
+//   CT    = beta (1 + 2^-20) + margin (any threshold is a state's energy, rounded);
+//   e64   = n^2 2^-52 beta (error of one FP64-summed table entry before its FP32 rounding),
+// the error of the decision value of any state is at most
+//   Ecol0 = 2u Cc + e64 + (k + B + 2) u CabsF                      base column (E_s, fields, lin)
+//         + sum_{r < RC} [2u (rS(r) + rF(r)) + k u rF(r) + e64]    register rows M_r + w_r
+//         + sum_{r >= RC} [u rS(r) + e64]                         table rows
+//         + (L - RC) u Cc                                         rows added at a re-anchoring
+//   Ecol  = Ecol0 + ((1 + u)^t - 1) (Cc + Ecol0)                    t = 2^a steps since the anchor
+//   EP0   = (k + 8) u bF + sum_{r >= RC} k u rF(r) + (L - RC) u CP  c(x_f), couplings, re-anchoring
+//   EP    = EP0 + ((1 + u)^(t / 2^(RC+1) + 1) - 1) (CP + EP0)        one add per row-RC-or-higher flip
+//   Edec  = Ecol + (RC + 1) u (Cc + Ecol) + EP + (u CL + e64) + u (Cc + CL)
+//         + u CT + u (CT + CP) + u (CT + CP + CL)                  slow-path rebuild, E_L, threshold
+// (a fields' error k u rF covers its FP32 representation and summation of k terms; the warp sum
+// of c(x_f) adds five levels).  A state x of the answer has E(x) <= E(y) for the state y whose
+// computed energy set the threshold, so it is recorded whenever 2 Edec <= margin; its FP64
+// rescoring then decides.  The bound is a worst case over every state of the run.
+// The plan-dependent magnitudes of the bound, computed once per (B, L, RC, margin) and kept in h.
+const Fp32BoundTerms &fp32_bound_terms(const HostInst &h, double margin)
+{
+    Fp32BoundTerms &m = h.fp32_terms;
+    const int rc = variant_reg_rows(h);
+    if (m.valid && m.B == h.B && m.L == h.L && m.rc == rc && m.n == h.n && m.margin == margin)
+        return m;
+    const int n = h.n, B = h.B, L = h.L, k = h.k, nf = B + L;
+    const double u = std::ldexp(1.0, -24);
+    auto U = [&](int i, int j) { return i <= j ? h.Uf[(size_t)i * n + j] : h.Uf[(size_t)j * n + i]; };
+    double beta = 0.0, bF = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) {
+            beta += std::fabs(U(i, j));
+            if (i >= nf)
+                bF += std::fabs(U(i, j));
+        }
+    std::vector<double> rF(nf, 0.0), rS(nf, 0.0);
+    for (int v = 0; v < nf; ++v) {
+        for (int f = nf; f < n; ++f)
+            rF[v] += std::fabs(U(v, f));
+        for (int b = 0; b < B; ++b)
+            if (b != v)
+                rS[v] += std::fabs(U(v, b));
+    }
+    double CabsF = 0.0;
+    for (int b = 0; b < B; ++b)
+        CabsF += rF[b];
+    double CP = bF;
+    for (int r = rc; r < L; ++r)
+        CP += rF[B + r];
+    // Cc: E_s(j) and c_i(j) by adding the lowest set bit of j to j without it
+    const size_t NB = 1ull << B;
+    std::vector<double> Es(NB, 0.0), absc(NB, 0.0), c(NB, 0.0);
+    for (size_t j = 1; j < NB; ++j) {
+        const int b0 = __builtin_ctzll(j);
+        const size_t jp = j & (j - 1);
+        double e = Es[jp] + U(b0, b0);
+        for (int b = b0 + 1; b < B; ++b)
+            if ((jp >> b) & 1)
+                e += U(b0, b);
+        Es[j] = e;
+    }
+    for (int i = B; i < n; ++i) {
+        for (size_t j = 1; j < NB; ++j) {
+            const int b0 = __builtin_ctzll(j);
+            c[j] = c[j & (j - 1)] + U(b0, i);
+            absc[j] += std::fabs(c[j]);
+        }
+    }
+    double Cc = 0.0;
+    for (size_t j = 0; j < NB; ++j)
+        Cc = std::max(Cc, std::fabs(Es[j]) + absc[j]);
+    for (int r = 0; r < rc; ++r)  // the register rows carry their fixed couplings w_r
+        Cc += rF[B + r];
+    // CL: E_L over every walked pattern in Gray order with a field vector
+    double CL = 0.0;
+    {
+        std::vector<double> field(L, 0.0);
+        std::vector<int> x(L, 0);
+        double e = 0.0;
+        for (uint64_t i = 1; i < (1ull << L); ++i) {
+            const int r = __builtin_ctzll(i);
+            const double s = x[r] ? -1.0 : 1.0;
+            e += s * (U(B + r, B + r) + field[r]);
+            x[r] ^= 1;
+            for (int t = 0; t < L; ++t)
+                if (t != r)
+                    field[t] += s * U(B + r, B + t);
+            CL = std::max(CL, std::fabs(e));
+        }
+        // the walk's own rounding is far below the slack of the bound; widen by it anyway
+        CL *= 1.0 + std::ldexp(1.0, -30);
+    }
+    const double CT = beta * (1.0 + std::ldexp(1.0, -20)) + margin;
+    const double e64 = (double)n * n * std::ldexp(1.0, -52) * beta;
+    double Ecol0 = 2 * u * Cc + e64 + (k + B + 2) * u * CabsF + (L - rc) * u * Cc;
+    for (int r = 0; r < L; ++r)
+        Ecol0 += r < rc ? 2 * u * (rS[B + r] + rF[B + r]) + k * u * rF[B + r] + e64 : u * rS[B + r] + e64;
+    double EP0 = (k + 8) * u * bF + (L - rc) * u * CP;
+    for (int r = rc; r < L; ++r)
+        EP0 += k * u * rF[B + r];
+    m.valid = true;
+    m.n = n;
+    m.B = B;
+    m.L = L;
+    m.rc = rc;
+    m.margin = margin;
+    m.Cc = Cc;
+    m.CP = CP;
+    m.Ecol0 = Ecol0;
+    m.EP0 = EP0;
+    m.rest = (u * CL + e64) + u * (Cc + CL) + u * CT + u * (CT + CP) + u * (CT + CP + CL);
+    return m;
+}
+
+double fp32_error_bound(const HostInst &h, int anchor_bits, double margin)
+{
+    if (h.acc != ACC_F32 || h.small || h.Uf.empty())
+        return 0.0;
+    const Fp32BoundTerms &m = fp32_bound_terms(h, margin);
+    const double u = std::ldexp(1.0, -24);
+    const int a = std::min(std::max(anchor_bits, m.rc + 1), m.L);
+    const double Ecol = m.Ecol0 + std::expm1(std::ldexp(1.0, a) * std::log1p(u)) * (m.Cc + m.Ecol0);
+    const double tP = std::ldexp(1.0, std::max(0, a - m.rc - 1)) + 1.0;
+    const double EP = m.EP0 + std::expm1(tP * std::log1p(u)) * (m.CP + m.EP0);
+    return Ecol + (m.rc + 1) * u * (m.Cc + Ecol) + EP + m.rest;
+}
+
+// Longest re-anchoring period (log2 of walk steps, from one unrolled body up to the whole walk)
+// whose rounding bound alone guarantees the FP32 scan's candidates: 2 fp32_error_bound <= margin.
+// -1 when even one body is too long.
+int fp32_rigorous_anchor_bits(const HostInst &h, double margin)
+{
+    if (h.acc != ACC_F32 || h.small || h.Uf.empty())
+        return -1;
+    const int rc = variant_reg_rows(h);
+    for (int a = h.L; a >= rc + 1; --a)
+        if (2.0 * fp32_error_bound(h, a, margin) <= margin)
+            return a;
+    return -1;
 }
 
 }  // namespace host

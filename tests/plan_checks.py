@@ -58,3 +58,50 @@ def fp32_lanes_fit(Q, B, L, RC):
     el = int(np.abs(EL).max())
     C = max(-lo, hi, 0) + el + 1
     return C + el + 1 < 2**24
+
+
+def fp32_bound(Q, B, L, RC, anchor_bits, margin=1e-3):
+    """Worst-case rounding error of the dense FP32 scan's decision value for a plan with B suffix
+    bits, L walked bits (suffix = variables 0..B-1, walked = B..B+L-1, fixed = the rest), RC
+    register rows, re-anchored every 2^anchor_bits walk steps: every FP32 operation rounds to
+    nearest (error <= u |result|, u = 2^-24), the tables are FP64 sums rounded once, and each
+    quantity's magnitude is bounded from |U| over the variables it involves (column values Cc,
+    walked energies CL, prefix energy CP, thresholds CT)."""
+    U = oracle.fold(np.asarray(Q, dtype=np.float64))
+    n = U.shape[0]
+    nf = B + L
+    k = n - nf
+    u = 2.0 ** -24
+    A = np.abs(U)
+    S = A + np.triu(A, 1).T  # |W|, symmetric, diagonal |U_ii|
+    beta = A.sum()
+    bF = np.triu(A)[nf:, nf:].sum()
+    rF = np.array([S[v, nf:].sum() for v in range(nf)])
+    rS = np.array([S[v, :B].sum() - (S[v, v] if v < B else 0.0) for v in range(nf)])
+    CabsF = rF[:B].sum()
+    CP = bF + rF[B + RC:nf].sum()
+    W = np.triu(U, 1) + np.triu(U, 1).T
+    j = np.arange(1 << B, dtype=np.int64)
+    J = ((j[:, None] >> np.arange(B)) & 1).astype(np.float64)
+    Es = J @ np.diag(U)[:B] + ((J @ W[:B, :B]) * J).sum(1) / 2
+    c = J @ W[:B, B:]
+    Cc = (np.abs(Es) + np.abs(c).sum(1)).max() + rF[B:B + RC].sum()
+    g = np.arange(1 << L, dtype=np.int64)
+    G = ((g[:, None] >> np.arange(L)) & 1).astype(np.float64)
+    Uw = U[B:nf, B:nf]
+    CL = np.abs(G @ np.diag(Uw) + ((G @ np.triu(Uw, 1)) * G).sum(1)).max() * (1 + 2.0 ** -30)
+    CT = beta * (1 + 2.0 ** -20) + margin
+    e64 = n * n * 2.0 ** -52 * beta
+    Ecol0 = 2 * u * Cc + e64 + (k + B + 2) * u * CabsF + (L - RC) * u * Cc
+    for r in range(L):
+        if r < RC:
+            Ecol0 += 2 * u * (rS[B + r] + rF[B + r]) + k * u * rF[B + r] + e64
+        else:
+            Ecol0 += u * rS[B + r] + e64
+    a = min(max(anchor_bits, RC + 1), L)
+    Ecol = Ecol0 + np.expm1(2.0 ** a * np.log1p(u)) * (Cc + Ecol0)
+    EP0 = (k + 8) * u * bF + (L - RC) * u * CP + k * u * rF[B + RC:nf].sum()
+    tP = 2.0 ** max(0, a - RC - 1) + 1
+    EP = EP0 + np.expm1(tP * np.log1p(u)) * (CP + EP0)
+    return (Ecol + (RC + 1) * u * (Cc + Ecol) + EP + (u * CL + e64) + u * (Cc + CL) + u * CT + u * (CT + CP)
+            + u * (CT + CP + CL))

@@ -172,3 +172,25 @@ def test_n44_fp32_bench_step_golden(q):
     assert abs(r.min - g["min"]) <= FLOAT_RTOL * max(1.0, abs(g["min"]))
     assert r.n_ties == g["n_ties"] and r.ties.tolist() == g["ties"] and r.topk.tolist() == g["topk"]
     assert np.allclose(r.topk_E, g["topk_E"], rtol=FLOAT_RTOL, atol=FLOAT_RTOL)
+
+
+def test_n50_bench_step_golden(q):
+    """One whole timed step of the default benchmark (the n = 50 instance, 2^43 states, top 7 bits
+    = 5, the first sub-cube after the warm-ups) through the two calls the benchmark times: the
+    device-resident problem (value) and qubo_solve_ex from host buffers (e2e), against the
+    oracle's stored result."""
+    g = load_golden("cfg5_n50_step43.json")
+    Q = wl.config5()
+    prob = q.Problem(Q, topk=16)
+    try:
+        prob.run(g["fix_bits"], g["fix_value"])
+        rp = prob.fetch(states_cap=4096)
+    finally:
+        prob.close()
+    rs = q.solve(Q, topk=16, states_cap=4096, fix_bits=g["fix_bits"], fix_value=g["fix_value"])
+    for r in (rp, rs):
+        i = r.info
+        assert (i["acc"], i["walk_bits"], i["suffix_bits"]) == ("i32f", 14, 9), i
+        assert i["states_scanned"] == 1 << 43
+        assert r.min == g["min"] and r.n_ties == g["n_ties"]
+        assert r.ties.tolist() == g["ties"] and r.topk.tolist() == g["topk"] and r.topk_E.tolist() == g["topk_E"]

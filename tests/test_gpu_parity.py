@@ -214,6 +214,23 @@ def test_float_parity(q, n):
         assert r.info["acc"] == "f32" or n < 14
 
 
+@pytest.mark.parametrize("n", [18, 21, 24])
+@pytest.mark.parametrize("topk", [1, 16])
+def test_float_ulp_near_ties(q, n, topk):
+    """3^(n//2) exact-arithmetic minimisers split by FP64 rounding (FP64 input, weights 0.1, 0.2,
+    0.3, 0.7): the FP32 scan must pass all of them to the FP64 rescoring, whose fixed-order sums
+    (the oracle's) decide the tie set and the K lowest bit for bit; at n = 24 the 2^14-step
+    walks are re-anchored inside."""
+    Q = wl.decimal_pairs(n, seed=n)
+    r = q.solve(Q, topk=topk, states_cap=1 << 16)
+    o = oracle.solve(Q, topk=topk, cap=1 << 16)
+    assert r.info["acc"] == "f32"
+    assert 1 < o.n_ties < 3 ** (n // 2)
+    assert r.min == o.min
+    check_float(r, o)
+    assert np.array_equal(r.topk_E, o.topk_E)
+
+
 def test_float64_input_and_plain_fp64(q):
     Q = wl.sk_float32(21, seed=44).astype(np.float64)
     o = oracle.solve(Q, topk=8)
@@ -459,6 +476,39 @@ def test_autotune_batched(q):
         assert p["trials"] >= 1
         for Q, r in zip(insts, q.solve_batched(insts, topk=2)):
             check_int(r, oracle.solve(Q.astype(np.int32), topk=2, cap=64))
+    finally:
+        q.autotune_clear()
+
+
+def test_autotune_batched_per_size_plans_on_config4(q, tmp_path):
+    """The batch autotuner on the 4096-instance configuration: one variant for the launch, a walk
+    per instance size; the tuned plans are what the next batch runs (every instance's walk is its
+    size's tuned walk), they survive a save / clear / load, and the results equal the oracle's
+    stored ones."""
+    import json
+
+    path = os.path.join(GOLDEN_DIR, "cfg4_batched.json")
+    if not os.path.exists(path):
+        pytest.skip("cfg4 golden not generated")
+    g = json.load(open(path))
+    insts = wl.config4()
+    try:
+        p = q.autotune_batched(insts)
+        walks = p["walk_bits_per_n"]
+        assert set(walks) == {int(Q.shape[0]) for Q in insts}, walks
+        assert p["trials"] > len(walks) and p["states_per_s"] > 0
+        saved = str(tmp_path / "plans.txt")
+        assert q.autotune_save(saved) >= 1 + len(walks)
+        q.autotune_clear()
+        assert q.autotune_load(saved) >= 1 + len(walks)
+        b = q.Batch(insts, topk=0, states_cap=g["cap"])
+        b.run()
+        rs = b.fetch()
+        b.close()
+        for Q, row, r in zip(insts, g["instances"], rs):
+            assert r.info["walk_bits"] == walks[int(Q.shape[0])], (row["i"], r.info["walk_bits"])
+            assert r.min == row["min"] and r.n_ties == row["n_ties"], row["i"]
+            assert [int(c) for c in r.ties] == row["ties"], row["i"]
     finally:
         q.autotune_clear()
 
