@@ -323,6 +323,14 @@ def secondary(q, torch, stream, l2buf, dev, gpu_index):
     r32["fp32_max_abs_err"] = i32["fp32_max_abs_err"]
     r32["fp32_max_drift"] = i32["fp32_max_drift"]
     r32["anchor_bits"] = i32["anchor_bits"]
+    rr, ir = _timed_problem(q, torch, stream, l2buf, Q3, 4, [0, 1, 2, 3], rigorous=True)
+    rr["how"] = ("FP32 scan + FP64 rescore with QUBO_FLAG_RIGOROUS (re-anchored where the rounding bound "
+                 "proves the candidates), 2^40-state sub-cubes 1..3 of the n=44 instance")
+    rr["anchor_bits"] = ir["anchor_bits"]
+    rr["fp32_err_bound"] = ir["fp32_err_bound"]
+    rr["fp32_max_drift"] = ir["fp32_max_drift"]
+    out["n44_fp32_rigorous"] = rr
+    r32["fp32_err_bound"] = i32["fp32_err_bound"]
     r64, _ = _timed_problem(q, torch, stream, l2buf, Q3, 8, [16, 17, 18], plain=True)
     r64["how"] = "plain FP64 scan (QUBO_FLAG_PLAIN), 2^36-state sub-cubes 17..18 of the n=44 instance"
     out["n44_fp32_rescore"] = r32

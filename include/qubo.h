@@ -149,7 +149,8 @@ typedef struct {
     int32_t fp32_rigorous_anchor_bits; /* QUBO_ACC_F32: longest re-anchoring period (log2 of walk
                                  steps) at which 2 * fp32_err_bound <= margin; -1 if none, or for
                                  other accumulators */
-    int32_t reserved_bound;
+    int32_t reg_rows;         /* plan: walked rows the scan kernel keeps in registers (its
+                                 unrolled body is 2^(reg_rows + 1) Gray steps) */
 } qubo_result;
 
 /*

@@ -199,6 +199,29 @@ int scan_variant(Acc acc)
 // The variant a run uses: the caller's (tuned) choice, else the accumulator's default.
 int pick_variant(Acc acc, int requested) { return requested >= 0 ? requested : scan_variant(acc); }
 
+// The default variant keeps five walked rows in registers and needs walks of at least six bits.
+// When the walk is shorter (the caller's walk_bits, split_k leaving fewer walked bits, or a
+// (sub)cube with fewer free bits beyond the suffix) and the caller named no variant, the run
+// takes the measured best variant with fewer register rows and the same columns per thread, so
+// the suffix split is unchanged.
+int fit_variant(const HostInst &h, int fix_bits, int split_k, int walk_bits, int variant_req, int variant)
+{
+    if (variant_req >= 0 || std::getenv("QUBO_SCAN_VARIANT"))
+        return variant;
+    const int B = acc_suffix_bits(h.acc, variant);
+    const int L = split_k > 0 ? h.n - B - split_k : (walk_bits > 0 ? walk_bits : h.n - fix_bits - B);
+    if (L >= reg_rows_of(h.acc, variant) + 1)
+        return variant;
+    static constexpr int kShorter4[] = {8, 3};       // 4 register rows (interleaved), 3
+    static constexpr int kShorterP[] = {13, 8, 11};  // packed: 4, 3, 2 register rows (interleaved)
+    const int *cand = h.acc == ACC_I16P ? kShorterP : kShorter4;
+    const int nc = h.acc == ACC_I16P ? 3 : 2;
+    for (int c = 0; c < nc; ++c)
+        if (acc_suffix_bits(h.acc, cand[c]) == B && L >= reg_rows_of(h.acc, cand[c]) + 1)
+            return cand[c];
+    return variant;
+}
+
 // Integer energies can be scanned exactly in FP32 lanes when every value held in an FP32 lane stays
 // below 2^24 in magnitude: the column values, the stored tables (E_s, the walked rows M_r with the
 // register rows' fixed couplings folded in, E_L) and the clamped per-step threshold.  The unit
@@ -473,6 +496,7 @@ int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int wal
         h.acc = ACC_F32;
         if (flags & QUBO_FLAG_RIGOROUS) {
             h.variant = pick_variant(h.acc, variant_req);
+            h.variant = fit_variant(h, fix_bits, split_k, walk_bits, variant_req, h.variant);
             int st = plan(h, fix_bits, fix_value, split_k, walk_bits);
             if (st)
                 return st;
@@ -495,12 +519,14 @@ int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int wal
         if (i16p_allowed()) {
             h.acc = ACC_I16P;
             h.variant = pick_variant(h.acc, variant_req);
+            h.variant = fit_variant(h, fix_bits, split_k, walk_bits, variant_req, h.variant);
             if (plan(h, fix_bits, fix_value, split_k, walk_bits) == QUBO_OK && i16p_exact(h))
                 chosen = ACC_I16P;
         }
         if (chosen == ACC_I32 && i32f_allowed()) {
             h.acc = ACC_I32F;
             h.variant = pick_variant(h.acc, variant_req);
+            h.variant = fit_variant(h, fix_bits, split_k, walk_bits, variant_req, h.variant);
             if (plan(h, fix_bits, fix_value, split_k, walk_bits) == QUBO_OK && i32f_exact(h, &h.clampC))
                 chosen = ACC_I32F;
             else if (split_k <= 0 && walk_bits <= 0 && h.L > kDefaultMaxWalkBits &&
@@ -512,6 +538,8 @@ int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int wal
         h.acc = chosen;
     }
     h.variant = acc_bytes(h.acc) == 4 ? pick_variant(h.acc, variant_req) : 0;
+    if (acc_bytes(h.acc) == 4)
+        h.variant = fit_variant(h, fix_bits, split_k, walk_bits, variant_req, h.variant);
     return plan(h, fix_bits, fix_value, split_k, walk_bits);
 }
 
@@ -628,18 +656,22 @@ namespace host {
 //   rS(r) = sum_{b in S} |U_rb|;  CabsF = sum_{b in S} rF(b);  CP = bF + sum_{r >= RC} rF(r);
 //   CT    = beta (1 + 2^-20) + margin (any threshold is a state's energy, rounded);
 //   e64   = n^2 2^-52 beta (error of one FP64-summed table entry before its FP32 rounding),
+//   u64   = 2^-52 (a generous FP64 rounding unit, for the per-unit fields summed in FP64),
 // the error of the decision value of any state is at most
-//   Ecol0 = 2u Cc + e64 + (k + B + 2) u CabsF                      base column (E_s, fields, lin)
-//         + sum_{r < RC} [2u (rS(r) + rF(r)) + k u rF(r) + e64]    register rows M_r + w_r
+//   Ecol0 = 2u Cc + e64 + (B + 3) u CabsF + k u64 CabsF            base column: E_s + lin
+//         + sum_{r < RC} [2u (rS(r) + rF(r)) + (u + k u64) rF(r)   register rows M_r + w_r
+//                         + e64]
 //         + sum_{r >= RC} [u rS(r) + e64]                         table rows
 //         + (L - RC) u Cc                                         rows added at a re-anchoring
 //   Ecol  = Ecol0 + ((1 + u)^t - 1) (Cc + Ecol0)                    t = 2^a steps since the anchor
-//   EP0   = (k + 8) u bF + sum_{r >= RC} k u rF(r) + (L - RC) u CP  c(x_f), couplings, re-anchoring
+//   EP0   = (u + (k + 8) u64) bF + sum_{r >= RC} (u + k u64) rF(r)  c(x_f) and the couplings w_r,
+//         + (L - RC) u CP                                         each rounded once; re-anchoring
 //   EP    = EP0 + ((1 + u)^(t / 2^(RC+1) + 1) - 1) (CP + EP0)        one add per row-RC-or-higher flip
 //   Edec  = Ecol + (RC + 1) u (Cc + Ecol) + EP + (u CL + e64) + u (Cc + CL)
 //         + u CT + u (CT + CP) + u (CT + CP + CL)                  slow-path rebuild, E_L, threshold
-// (a fields' error k u rF covers its FP32 representation and summation of k terms; the warp sum
-// of c(x_f) adds five levels).  A state x of the answer has E(x) <= E(y) for the state y whose
+// (the fields and c(x_f) are FP64 sums of k terms, plus a five-level warp sum for c(x_f), each
+// rounded to FP32 once; lin(j) adds at most B of the rounded fields in FP32, B + 2 additions).
+// A state x of the answer has E(x) <= E(y) for the state y whose
 // computed energy set the threshold, so it is recorded whenever 2 Edec <= margin; its FP64
 // rescoring then decides.  The bound is a worst case over every state of the run.
 // The plan-dependent magnitudes of the bound, computed once per (B, L, RC, margin) and kept in h.
@@ -718,12 +750,13 @@ const Fp32BoundTerms &fp32_bound_terms(const HostInst &h, double margin)
     }
     const double CT = beta * (1.0 + std::ldexp(1.0, -20)) + margin;
     const double e64 = (double)n * n * std::ldexp(1.0, -52) * beta;
-    double Ecol0 = 2 * u * Cc + e64 + (k + B + 2) * u * CabsF + (L - rc) * u * Cc;
+    const double u64 = std::ldexp(1.0, -52);
+    double Ecol0 = 2 * u * Cc + e64 + (B + 3) * u * CabsF + k * u64 * CabsF + (L - rc) * u * Cc;
     for (int r = 0; r < L; ++r)
-        Ecol0 += r < rc ? 2 * u * (rS[B + r] + rF[B + r]) + k * u * rF[B + r] + e64 : u * rS[B + r] + e64;
-    double EP0 = (k + 8) * u * bF + (L - rc) * u * CP;
+        Ecol0 += r < rc ? 2 * u * (rS[B + r] + rF[B + r]) + (u + k * u64) * rF[B + r] + e64 : u * rS[B + r] + e64;
+    double EP0 = u * bF + (k + 8) * u64 * bF + (L - rc) * u * CP;
     for (int r = rc; r < L; ++r)
-        EP0 += k * u * rF[B + r];
+        EP0 += u * rF[B + r] + k * u64 * rF[B + r];
     m.valid = true;
     m.n = n;
     m.B = B;

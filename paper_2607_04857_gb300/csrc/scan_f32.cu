@@ -10,22 +10,21 @@ constexpr auto kernel_of()
     constexpr int kS = cols_per_thread(sizeof(float), VAR);
     static_assert(ilog2c(32 * kS) == suffix_bits(sizeof(float), VAR), "suffix bits must match the column layout");
     return scan_kernel<float, kS, kVariantRegRows[VAR], K1, kVariantMinBlocks[VAR], kVariantAddMode[VAR],
-                       kVariantMinInputs[VAR]>;
+                       kVariantMinInputs[VAR], kVariantInterleave[VAR]>;
+}
+
+template <bool K1, int... V>
+auto pick_of(int variant, std::integer_sequence<int, V...>)
+{
+    using Fn = decltype(kernel_of<0, K1>());
+    constexpr Fn table[] = {kernel_of<V, K1>()...};
+    return table[(variant >= 0 && variant < (int)sizeof...(V)) ? variant : 0];
 }
 
 template <bool K1>
 auto pick(int variant)
 {
-    switch (variant) {
-    case 1: return kernel_of<1, K1>();
-    case 2: return kernel_of<2, K1>();
-    case 3: return kernel_of<3, K1>();
-    case 4: return kernel_of<4, K1>();
-    case 5: return kernel_of<5, K1>();
-    case 6: return kernel_of<6, K1>();
-    case 7: return kernel_of<7, K1>();
-    default: return kernel_of<0, K1>();
-    }
+    return pick_of<K1>(variant, std::make_integer_sequence<int, kScanVariants>{});
 }
 }  // namespace
 

@@ -205,6 +205,7 @@ __device__ __forceinline__ const typename Tr<T>::FU *unit_matrix(const Inst &d)
     return (const typename Tr<T>::FU *)d.W;
 }
 
+
 __device__ __forceinline__ void vsplit(const int4 &v, int32_t (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
 __device__ __forceinline__ void vsplit(const float4 &v, float (&o)[4]) { o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w; }
 __device__ __forceinline__ void vsplit(const longlong2 &v, int64_t (&o)[2]) { o[0] = v.x; o[1] = v.y; }
@@ -434,11 +435,9 @@ __device__ void small_unit(const ScanArgs &a, const Inst &d, int inst, int lane)
 // Fields of the set fixed bits of unit x_f: lane l returns in f0 the coupling of variable l
 // (l < B + L) to the set fixed variables, and every lane returns c(x_f), the energy of the fixed
 // variables alone (Sec. 3.3.1: Q' = Q_rr + diag(x_f Q_fr), c(x_f) = x_f Q_ff x_f^T).
-template <class T>
-__device__ __forceinline__ void unit_fields(const typename Tr<T>::FU *W, int n, int k, int BL, uint64_t unit, int lane,
-                                            typename Tr<T>::FU &f0, typename Tr<T>::FU &cx)
+template <class T, class F = typename Tr<T>::FU>
+__device__ __forceinline__ void unit_fields(const F *W, int n, int k, int BL, uint64_t unit, int lane, F &f0, F &cx)
 {
-    using F = typename Tr<T>::FU;
     F a0 = 0, up0 = 0, up1 = 0;
     for (int f = 0; f < k; ++f) {
         if (!((unit >> f) & 1ull))
@@ -494,11 +493,53 @@ __device__ __forceinline__ void column_fields(F f0, int lane, F &lin_t, F (&lin_
     }
 }
 
+// One register-row Gray step of S columns fused with the min over them, in an interleaved order:
+// each triple of columns is reduced by a 3-input min as soon as its adds are issued, so the FMA
+// pipe (adds) and the ALU pipe (mins) receive alternating work from one warp.  Pair q of columns
+// is one f32x2 instruction where the add mode says so (as in scan_unit).  Returns the minimum.
+template <bool PAIRED, bool NEG, class TC>
+__device__ __forceinline__ void add_pair(TC &x, TC &y, TC a, TC b)
+{
+    if constexpr (PAIRED && std::is_same_v<TC, float>) {
+        if constexpr (NEG)
+            sub_f32x2(x, y, a, b);
+        else
+            add_f32x2(x, y, a, b);
+    } else {
+        x = NEG ? x - a : x + a;
+        y = NEG ? y - b : y + b;
+    }
+}
+
+template <class TC, int S, int ADDM, bool NEG>
+__device__ __forceinline__ TC add_min_interleaved(TC (&E)[S], const TC (&M)[S])
+{
+    constexpr int NT = S / 3, NL = NT + S % 3;
+    TC l1[NL];
+    static_for<S / 2>([&](auto pc) {
+        constexpr int pr = decltype(pc)::value, q = 2 * pr;
+        constexpr bool paired = ADDM == 4 || (ADDM == 5 && pr % 2 == 0) || (ADDM == 6 && pr % 4 == 0) ||
+                                (ADDM == 7 && pr % 4 != 0);
+        add_pair<paired, NEG>(E[q], E[q + 1], M[q], M[q + 1]);
+        // triples completed by this pair: (3t, 3t+1, 3t+2) with 3t+2 in {q, q+1}
+        static_for<2>([&](auto cc) {
+            constexpr int c = q + decltype(cc)::value;
+            if constexpr (c % 3 == 2 && c / 3 < NT)
+                l1[c / 3] = emin3(E[c - 2], E[c - 1], E[c]);
+        });
+    });
+    static_for<S % 3>([&](auto rc) {
+        constexpr int c = 3 * NT + decltype(rc)::value;
+        l1[NT + decltype(rc)::value] = E[c];
+    });
+    return tree_min<TC, 3, NL>(l1);
+}
+
 // ---- one work unit: all 2^(B+L) states with fixed bits x_f = unit --------------------------------
 // ADDM >= 4 issues some or all FP32 column adds as paired f32x2 operations (two columns per
 // instruction; 4: all pairs, 5: every second, 6: every fourth, 7: three in four); other modes
 // leave the adds to the compiler.  MINM selects 2- or 3-input mins.
-template <class T, int S, int RC, bool K1, int ADDM, int MINM>
+template <class T, int S, int RC, bool K1, int ADDM, int MINM, int ILV = 0>
 __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int inst, uint64_t unit,
                                           typename Tr<T>::TP &Treg, int lane, typename Tr<T>::TC *stage,
                                           typename Tr<T>::TP *wsm, typename Tr<T>::TC *anc)
@@ -515,11 +556,18 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
     constexpr int BODY = 1 << (RC + 1);
     const int n = d.n, L = d.L, k = d.k, BL = B + L;
     InstState *st = a.state + inst;
-    const F *W = unit_matrix<T>(d);
-
-    // Fields of the set fixed bits on every other variable and c(x_f) (Sec. 3.3.1).
+    // Fields of the set fixed bits on every other variable and c(x_f) (Sec. 3.3.1).  FP32 scans
+    // sum them in FP64 and round each once (their rounding bound then carries one rounding per
+    // field and per c(x_f), not one per term).
     F f0, cx;
-    unit_fields<T>(W, n, k, BL, unit, lane, f0, cx);
+    if constexpr (std::is_same_v<F, float>) {
+        double f0d, cxd;
+        unit_fields<T, double>(d.W64, n, k, BL, unit, lane, f0d, cxd);
+        f0 = (float)f0d;
+        cx = (float)cxd;
+    } else {
+        unit_fields<T, F>(unit_matrix<T>(d), n, k, BL, unit, lane, f0, cx);
+    }
     // Walked-row couplings w_r, read at every flip of a row >= RC.
     __syncwarp();
     if (lane >= B && lane < BL)
@@ -666,7 +714,12 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
         // E_L and half a 3-input min into the running minimum; one compare per half body.
         static_for<BODY>([&](auto pc) {
             constexpr int p = decltype(pc)::value;
-            if constexpr (p > 0) {
+            constexpr bool fused = ILV && MINM == 3 && p > 0 && ctzc(p) < RC;
+            TC mfused{};
+            if constexpr (fused) {
+                constexpr int kk = ctzc(p);
+                mfused = add_min_interleaved<TC, S, ADDM, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk]);
+            } else if constexpr (p > 0) {
                 constexpr int kk = ctzc(p);
                 if constexpr (kk < RC) {
                     constexpr bool neg = (p >> (kk + 1)) & 1;
@@ -698,7 +751,12 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
             }
             if constexpr (p % V == 0)
                 vload<TC>(ELp + i0 + p, elv);
-            const TC mp = tree_min<TC, MINM, S>(E) + elv[p % V];
+            TC mcols;
+            if constexpr (fused)
+                mcols = mfused;
+            else
+                mcols = tree_min<TC, MINM, S>(E);
+            const TC mp = mcols + elv[p % V];
             constexpr int HALF = BODY / 2, ph = p % HALF;
             TC &acc = p < HALF ? acc_lo : acc_hi;
             if constexpr (ph % 2 == 0)
@@ -790,7 +848,7 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
 // packed unsigned mins leaves the two lane minima in one word, and the step's test compares the
 // smaller lane with threshold - E_L (E_L is stored minus the bias, so that difference is already
 // in lane units).  Everything else follows scan_unit.
-template <int S, int RC, bool K1, int ADDM, int MINM>
+template <int S, int RC, bool K1, int ADDM, int MINM, int ILV = 0>
 __device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &d, int inst, uint64_t unit,
                                                  int32_t &Treg, int lane, uint32_t *stage, int32_t *wsm)
 {
@@ -884,7 +942,12 @@ __device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &
         int32_t acc_lo, acc_hi, mprev;  // as in scan_unit, in lane units
         static_for<BODY>([&](auto pc) {
             constexpr int p = decltype(pc)::value;
-            if constexpr (p > 0) {
+            constexpr bool fused = ILV && MINM == 3 && p > 0 && ctzc(p) < RC;
+            uint32_t mfused = 0;
+            if constexpr (fused) {
+                constexpr int kk = ctzc(p);
+                mfused = add_min_interleaved<uint32_t, S, 0, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk]);
+            } else if constexpr (p > 0) {
                 constexpr int kk = ctzc(p);
                 if constexpr (kk < RC) {
                     constexpr bool neg = (p >> (kk + 1)) & 1;
@@ -909,7 +972,11 @@ __device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &
             }
             if constexpr (p % V == 0)
                 vload<int32_t>(ELp + i0 + p, elv);
-            const uint32_t mw = tree_min<uint32_t, MINM, S>(E);
+            uint32_t mw;
+            if constexpr (fused)
+                mw = mfused;
+            else
+                mw = tree_min<uint32_t, MINM, S>(E);
             const int32_t mp = min((int32_t)(mw & 0xffffu), (int32_t)(mw >> 16)) + elv[p % V];
             constexpr int HALF = BODY / 2, ph = p % HALF;
             int32_t &acc = p < HALF ? acc_lo : acc_hi;
@@ -1044,7 +1111,7 @@ __device__ __forceinline__ void persistent_units(const ScanArgs &a, int lane, ty
         atomicAdd(&a.state[cur].scanned, done);
 }
 
-template <class T, int S, int RC, bool K1, int MINB, int ADDM, int MINM>
+template <class T, int S, int RC, bool K1, int MINB, int ADDM, int MINM, int ILV = 0>
 __global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs a)
 {
     using TC = typename Tr<T>::TC;
@@ -1061,9 +1128,9 @@ __global__ void __launch_bounds__(kScanThreads, MINB) scan_kernel(const ScanArgs
     // units take 0.1-30 ms here: one per claim keeps the end of a launch balanced
     persistent_units<T, 1>(a, lane, Treg, [&](const Inst &d, int inst, uint64_t unit) {
         if constexpr (Tr<T>::kPack == 2)
-            scan_unit_packed<S, RC, K1, ADDM, MINM>(a, d, inst, unit, Treg, lane, stage, wsm);
+            scan_unit_packed<S, RC, K1, ADDM, MINM, ILV>(a, d, inst, unit, Treg, lane, stage, wsm);
         else
-            scan_unit<T, S, RC, K1, ADDM, MINM>(a, d, inst, unit, Treg, lane, stage, wsm, anc);
+            scan_unit<T, S, RC, K1, ADDM, MINM, ILV>(a, d, inst, unit, Treg, lane, stage, wsm, anc);
     });
 }
 

@@ -66,7 +66,8 @@ def fp32_bound(Q, B, L, RC, anchor_bits, margin=1e-3):
     register rows, re-anchored every 2^anchor_bits walk steps: every FP32 operation rounds to
     nearest (error <= u |result|, u = 2^-24), the tables are FP64 sums rounded once, and each
     quantity's magnitude is bounded from |U| over the variables it involves (column values Cc,
-    walked energies CL, prefix energy CP, thresholds CT)."""
+    walked energies CL, prefix energy CP, thresholds CT); the per-unit fields and c(x_f) are
+    FP64 sums rounded to FP32 once, the column fields lin(j) FP32 sums of them."""
     U = oracle.fold(np.asarray(Q, dtype=np.float64))
     n = U.shape[0]
     nf = B + L
@@ -92,15 +93,16 @@ def fp32_bound(Q, B, L, RC, anchor_bits, margin=1e-3):
     CL = np.abs(G @ np.diag(Uw) + ((G @ np.triu(Uw, 1)) * G).sum(1)).max() * (1 + 2.0 ** -30)
     CT = beta * (1 + 2.0 ** -20) + margin
     e64 = n * n * 2.0 ** -52 * beta
-    Ecol0 = 2 * u * Cc + e64 + (k + B + 2) * u * CabsF + (L - RC) * u * Cc
+    u64 = 2.0 ** -52
+    Ecol0 = 2 * u * Cc + e64 + (B + 3) * u * CabsF + k * u64 * CabsF + (L - RC) * u * Cc
     for r in range(L):
         if r < RC:
-            Ecol0 += 2 * u * (rS[B + r] + rF[B + r]) + k * u * rF[B + r] + e64
+            Ecol0 += 2 * u * (rS[B + r] + rF[B + r]) + (u + k * u64) * rF[B + r] + e64
         else:
             Ecol0 += u * rS[B + r] + e64
     a = min(max(anchor_bits, RC + 1), L)
     Ecol = Ecol0 + np.expm1(2.0 ** a * np.log1p(u)) * (Cc + Ecol0)
-    EP0 = (k + 8) * u * bF + (L - RC) * u * CP + k * u * rF[B + RC:nf].sum()
+    EP0 = (u + (k + 8) * u64) * bF + (L - RC) * u * CP + (u + k * u64) * rF[B + RC:nf].sum()
     tP = 2.0 ** max(0, a - RC - 1) + 1
     EP = EP0 + np.expm1(tP * np.log1p(u)) * (CP + EP0)
     return (Ecol + (RC + 1) * u * (Cc + Ecol) + EP + (u * CL + e64) + u * (Cc + CL) + u * CT + u * (CT + CP)

@@ -160,6 +160,20 @@ def test_n44_fp32_bench_plan_subcube_golden(q):
     assert np.allclose(r.topk_E, g["topk_E"], rtol=FLOAT_RTOL, atol=FLOAT_RTOL)
 
 
+def test_n44_fp32_rigorous_subcube_golden(q):
+    """The same 2^40-state sub-cube with QUBO_FLAG_RIGOROUS: 2^14-step walks re-anchored every
+    2^6 steps, where the rounding bound alone proves the candidate set at the 1e-3 margin."""
+    g = load_golden("cfg3_n44_sub40.json")
+    Q = wl.config3()
+    r = q.solve(Q, topk=16, states_cap=4096, fix_bits=g["fix_bits"], fix_value=g["fix_value"], rigorous=True)
+    i = r.info
+    assert (i["acc"], i["walk_bits"], i["anchor_bits"]) == ("f32", 14, 6), i
+    assert 2 * i["fp32_err_bound"] <= 1e-3 and i["fp32_max_drift"] <= 2 * i["fp32_err_bound"]
+    assert abs(r.min - g["min"]) <= FLOAT_RTOL * max(1.0, abs(g["min"]))
+    assert r.n_ties == g["n_ties"] and r.ties.tolist() == g["ties"] and r.topk.tolist() == g["topk"]
+    assert np.allclose(r.topk_E, g["topk_E"], rtol=FLOAT_RTOL, atol=FLOAT_RTOL)
+
+
 def test_n44_fp32_bench_step_golden(q):
     """One whole benchmark step of the n = 44 FP32 instance (2^42 states, top 2 bits = 1), in the
     benchmark's plan, against the oracle's stored FP64 result."""

@@ -88,11 +88,11 @@ def test_packed_chosen_exactly_when_bounded(q, lim):
     i = r.info
     if i["acc"] == "i16p":
         assert (i["suffix_bits"], i["walk_bits"]) == (10, 6)
-    lo, hi = column_range(Q, 10, 6, 3)  # default packed variant: 3 register rows
+    lo, hi = column_range(Q, 10, 6, 5)  # default packed variant: 5 register rows
     assert (i["acc"] == "i16p") == (lo >= -32768 and hi <= 32767), (lo, hi, i["acc"])
 
 
-@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("variant", range(18))
 def test_packed_variants_agree(q, variant, monkeypatch):
     monkeypatch.setenv("QUBO_SCAN_VARIANT", str(variant))
     Q = wl.maxcut_qubo(29, 0.5, seed=91)

@@ -285,6 +285,29 @@ def test_fp32_drift_guard_shortens_the_anchor_period(q):
     check_float(r, oracle.solve(Q, topk=4, fix_bits=4))
 
 
+def test_fp32_rigorous_mode(q):
+    """QUBO_FLAG_RIGOROUS: the FP32 scan re-anchors at the period its rounding bound proves
+    (n = 34 SK sub-cubes, 2^14-step walks), results equal the oracle's; the measured drift and
+    the scan's energy errors stay within the reported bound; with a margin no period can meet
+    the scan runs in FP64, still exact."""
+    Q = wl.sk_float32(34, seed=36)
+    o = oracle.solve(Q, topk=8, fix_bits=4, fix_value=6)
+    r = q.solve(Q, topk=8, fix_bits=4, fix_value=6, walk_bits=14, rigorous=True)
+    i = r.info
+    assert i["acc"] == "f32" and i["walk_bits"] == 14
+    assert i["anchor_bits"] == min(10, i["fp32_rigorous_anchor_bits"]) and i["anchor_bits"] >= 5
+    assert 2 * i["fp32_err_bound"] <= 1e-3
+    assert i["fp32_max_drift"] <= 2 * i["fp32_err_bound"]
+    assert i["fp32_max_abs_err"] <= 2 * i["fp32_err_bound"]
+    check_float(r, o)
+    d = q.solve(Q, topk=8, fix_bits=4, fix_value=6, walk_bits=14)  # default: measured drift
+    assert d.info["anchor_bits"] == 10 and d.info["fp32_max_drift"] <= 2 * d.info["fp32_err_bound"]
+    check_float(d, o)
+    f = q.solve(Q, topk=8, fix_bits=4, fix_value=6, margin=1e-6, rigorous=True)
+    assert f.info["acc"] == "f64"
+    check_float(f, o)
+
+
 # --- batched ----------------------------------------------------------------------------------
 
 def test_batched_matches_per_instance(q):
@@ -347,7 +370,7 @@ def test_time_limit_returns_timeout(q):
 
 # --- compiled kernel variants and the n=44 FP32 configuration ---------------------------------
 
-@pytest.mark.parametrize("variant", range(8))
+@pytest.mark.parametrize("variant", range(18))
 def test_scan_variants_agree(q, variant, monkeypatch):
     monkeypatch.setenv("QUBO_SCAN_VARIANT", str(variant))
     Q = wl.upper_int(27, -300, 300, seed=90)
@@ -585,7 +608,7 @@ def test_fp32_lanes_rejected_when_out_of_range(q):
     """Entries of +-2^22: column values exceed 2^24, so the int32 kernel must run."""
     Q = wl.upper_int(21, -(1 << 22), 1 << 22, seed=8)
     r = q.solve(Q, topk=8)
-    assert not fp32_lanes_fit(Q, r.info["suffix_bits"], r.info["walk_bits"], 4)
+    assert not fp32_lanes_fit(Q, r.info["suffix_bits"], r.info["walk_bits"], r.info["reg_rows"])
     assert r.info["acc"] == "i32"
     check_int(r, oracle.solve(Q, topk=8))
 
@@ -600,6 +623,6 @@ def test_fp32_lanes_chosen_exactly_when_bounded(q, lim, monkeypatch):
     r = q.solve(Q, topk=8, walk_bits=5)  # the same plan for either kernel (both 9 suffix bits)
     check_int(r, oracle.solve(Q, topk=8))
     i = r.info
-    assert (i["suffix_bits"], i["walk_bits"]) == (9, 5)
-    expect = "i32f" if fp32_lanes_fit(Q, 9, 5, 4) else "i32"  # default variant: 4 register rows
+    assert (i["suffix_bits"], i["walk_bits"], i["reg_rows"]) == (9, 5, 4)  # a 4-register-row variant
+    expect = "i32f" if fp32_lanes_fit(Q, 9, 5, 4) else "i32"
     assert i["acc"] == expect

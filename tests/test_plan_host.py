@@ -51,7 +51,8 @@ def test_fp32_lane_admission(q, lim, monkeypatch):
     monkeypatch.setenv("QUBO_NO_I32Z", "1")
     Q = wl.upper_int(27, -lim, lim, seed=9)
     p = q.plan_query(Q, topk=8, walk_bits=5)
-    assert (p["suffix_bits"], p["walk_bits"]) == (9, 5)
+    # a 5-bit walk is shorter than the default variant takes: the 4-register-row variant runs
+    assert (p["suffix_bits"], p["walk_bits"], p["reg_rows"]) == (9, 5, 4)
     assert p["acc"] == ("i32f" if fp32_lanes_fit(Q, 9, 5, 4) else "i32")
 
 
@@ -61,7 +62,7 @@ def test_packed_admission(q, lim, monkeypatch):
     monkeypatch.setenv("QUBO_NO_I32Z", "1")
     Q = wl.upper_int(24, -lim, lim, seed=11)
     p = q.plan_query(Q, topk=8, walk_bits=6)
-    lo, hi = column_range(Q, 10, 6, 3)  # default packed variant: 10 suffix bits, 3 register rows
+    lo, hi = column_range(Q, 10, 6, 5)  # default packed variant: 10 suffix bits, 5 register rows
     assert (p["acc"] == "i16p") == (lo >= -32768 and hi <= 32767), (lo, hi, p)
 
 
@@ -76,8 +77,9 @@ def test_fp32_lanes_fall_back_to_shorter_walks(q, monkeypatch):
         Q = wl.upper_int(40, -1000, 1000, seed=40)
         Q[13:21, 21:23] = big
         Q[21, 22] = big
-        assert fp32_lanes_fit(Q, 9, 14, 4) == (expect == 14) and fp32_lanes_fit(Q, 9, 12, 4)
         p = q.plan_query(Q, fix_bits=2)
+        rc = p["reg_rows"]
+        assert fp32_lanes_fit(Q, 9, 14, rc) == (expect == 14) and fp32_lanes_fit(Q, 9, 12, rc)
         assert (p["acc"], p["walk_bits"]) == ("i32f", expect), (big, p)
 
 
@@ -119,3 +121,45 @@ def test_plan_shapes_are_consistent(q, seed):
         assert p["split_k"] >= fb and p["walk_bits"] >= (3 if factored else 4), p
         if factored:
             assert 3 <= p["zero_rows"] <= p["walk_bits"], p
+
+
+@pytest.mark.parametrize("case", ["n44_step", "n44_subcube", "sk30", "n26_walk8"])
+def test_fp32_rounding_bound_matches_its_definition(q, case):
+    """The FP32 scan's worst-case rounding bound the host reports (qubo_result.fp32_err_bound)
+    equals the bound recomputed in numpy from the folded matrix and the plan (tests/plan_checks.py
+    states it term by term), at the run's period and, through the margin, at the longest period
+    the bound admits; the rigorous option anchors there, or scans in FP64 when no period does."""
+    from plan_checks import fp32_bound
+
+    Q, kw = {"n44_step": (wl.config3(), dict(fix_bits=2)),
+             "n44_subcube": (wl.config3(), dict(fix_bits=6, fix_value=37)),
+             "sk30": (wl.sk_float32(30, seed=3), {}),
+             "n26_walk8": (wl.sk_float32(26, seed=4), dict(walk_bits=8))}[case]
+    p = q.plan_query(Q, **kw)
+    B, L, RC = p["suffix_bits"], p["walk_bits"], p["reg_rows"]
+    assert p["acc"] == "f32" and p["anchor_bits"] == min(10, L) and RC >= 2
+    ref = fp32_bound(Q, B, L, RC, p["anchor_bits"])
+    assert p["fp32_err_bound"] == pytest.approx(ref, rel=1e-9)
+    bounds = [fp32_bound(Q, B, L, RC, a) for a in range(RC + 1, L + 1)]
+    assert all(x < y for x, y in zip(bounds, bounds[1:]))  # longer periods, larger bound
+    for margin in (1e-4, 1e-3, 3e-3, 1e-2):
+        pm = q.plan_query(Q, margin=margin, **kw)
+        a = pm["fp32_rigorous_anchor_bits"]
+        fits = [RC + 1 + i for i, b in enumerate(bounds) if 2 * b <= margin]
+        assert a == (max(fits) if fits else -1), (margin, a, fits)
+        pr = q.plan_query(Q, margin=margin, rigorous=True, **kw)
+        if a < 0:
+            assert pr["acc"] == "f64"
+        else:
+            assert pr["acc"] == "f32" and pr["anchor_bits"] == min(10, a)
+            assert 2 * pr["fp32_err_bound"] <= margin
+
+
+def test_fp32_rigorous_period_of_the_benchmark_instance(q):
+    """n = 44 SK instance in the benchmark's plan (2^14-step walks): the bound at the default
+    2^10-step period is above what the 1e-3 margin admits (there correctness rests on the drift
+    measured at every re-anchoring); re-anchoring every 2^6 steps is proven."""
+    p = q.plan_query(wl.config3(), fix_bits=2)
+    assert p["walk_bits"] == 14 and p["anchor_bits"] == 10
+    assert 2 * p["fp32_err_bound"] > 1e-3
+    assert p["fp32_rigorous_anchor_bits"] == 6
