@@ -30,18 +30,19 @@ constexpr int kRegRows = 4;
 // Compiled scan variants of the 4-byte accumulators: columns per thread S, register rows,
 // minimum resident blocks per SM, how the adds are issued (0: compiler's choice, 4: FP32 adds as
 // paired f32x2 operations, two columns per instruction, 5, 6, 7: a half, a quarter or three
-// quarters of them paired; the paired modes do not apply to integer columns, whose adds are
-// left to the compiler), 2- or 3-input mins, and whether a register-row step issues its adds and
+// quarters of them paired; the paired modes do not apply to integer columns; 2, 3: in the
+// interleaved form, one integer column in four / in eight updated by a 3-input add on the ALU
+// pipe), 2- or 3-input mins, and whether a register-row step issues its adds and
 // the first level of its min tree interleaved (each triple of columns reduced as soon as its adds
 // are issued) or all adds first.  The 8-byte accumulators compile one variant: S = 16 with
 // variant 0's register rows, blocks and min inputs.
-constexpr int kScanVariants = 18;
-constexpr int kVariantCols[kScanVariants] = {32, 16, 16, 16, 16, 16, 32, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
-constexpr int kVariantRegRows[kScanVariants] = {3, 4, 4, 3, 4, 4, 3, 4, 4, 4, 4, 3, 3, 3, 3, 3, 5, 5};
-constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 3, 3, 3, 3, 2, 3, 3, 3, 3, 4, 4, 4, 3, 3, 2, 2};
-constexpr int kVariantAddMode[kScanVariants] = {0, 6, 7, 0, 0, 4, 4, 5, 6, 5, 4, 6, 4, 0, 4, 4, 6, 0};
-constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
-constexpr int kVariantInterleave[kScanVariants] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 0, 1, 1, 1};
+constexpr int kScanVariants = 20;
+constexpr int kVariantCols[kScanVariants] = {32, 16, 16, 16, 16, 16, 32, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
+constexpr int kVariantRegRows[kScanVariants] = {3, 4, 4, 3, 4, 4, 3, 4, 4, 4, 4, 3, 3, 3, 3, 3, 5, 5, 5, 5};
+constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 3, 3, 3, 3, 2, 3, 3, 3, 3, 4, 4, 4, 3, 3, 2, 2, 2, 2};
+constexpr int kVariantAddMode[kScanVariants] = {0, 6, 7, 0, 0, 4, 4, 5, 6, 5, 4, 6, 4, 0, 4, 4, 6, 0, 3, 2};
+constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
+constexpr int kVariantInterleave[kScanVariants] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 0, 1, 1, 1, 1, 1};
 // Default variant per 4-byte accumulator (measured on GB300; see the profiles).
 constexpr int kDefaultVariantI32 = 16;
 constexpr int kDefaultVariantF32 = 16;
@@ -51,13 +52,13 @@ constexpr int kDefaultVariantI16P = 14;
 // minimum resident blocks per SM, and how the adds are issued (0: compiler's choice; 2 and 3: one
 // add in four or in eight as a 3-input add with a runtime 0, which the ALU pipe executes, so
 // that the ALU and FMA pipes share the adds).  All use 3-input mins.
-// Variants 8-14, 16 and 17 interleave the adds and the first min level as the 4-byte variants do
-// (their adds are plain 32-bit adds).
-constexpr int kPackedWords[kScanVariants] = {16, 16, 16, 16, 16, 32, 32, 16, 16, 16, 16, 16, 32, 16, 16, 16, 32, 16};
-constexpr int kPackedRegRows[kScanVariants] = {3, 3, 3, 3, 3, 2, 2, 2, 3, 3, 4, 2, 2, 4, 5, 4, 3, 5};
-constexpr int kPackedMinBlocks[kScanVariants] = {3, 3, 3, 4, 4, 2, 2, 4, 3, 4, 3, 4, 2, 2, 2, 2, 2, 1};
-constexpr int kPackedAddMode[kScanVariants] = {0, 3, 2, 0, 3, 0, 3, 3, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-constexpr int kPackedInterleave[kScanVariants] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 0, 1, 1};
+// Variants 8-14 and 16-19 interleave the adds and the first min level as the 4-byte variants do
+// (18 and 19 with one add in eight / in four on the ALU pipe, the others with plain adds).
+constexpr int kPackedWords[kScanVariants] = {16, 16, 16, 16, 16, 32, 32, 16, 16, 16, 16, 16, 32, 16, 16, 16, 32, 16, 16, 16};
+constexpr int kPackedRegRows[kScanVariants] = {3, 3, 3, 3, 3, 2, 2, 2, 3, 3, 4, 2, 2, 4, 5, 4, 3, 5, 5, 5};
+constexpr int kPackedMinBlocks[kScanVariants] = {3, 3, 3, 4, 4, 2, 2, 4, 3, 4, 3, 4, 2, 2, 2, 2, 2, 1, 2, 2};
+constexpr int kPackedAddMode[kScanVariants] = {0, 3, 2, 0, 3, 0, 3, 3, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 3, 2};
+constexpr int kPackedInterleave[kScanVariants] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 0, 1, 1, 1, 1};
 // Threads per block of the scan kernel (4 warps; every warp owns one work unit at a time).
 constexpr int kScanThreads = 128;
 // Longest Gray walk inside one work unit (also the FP32 re-anchoring period).

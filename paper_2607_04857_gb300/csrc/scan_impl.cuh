@@ -511,8 +511,18 @@ __device__ __forceinline__ void add_pair(TC &x, TC &y, TC a, TC b)
     }
 }
 
+// Integer column update as a 3-input add with a run-time zero, which issues to the ALU pipe
+// rather than the FMA-heavy pipe that takes the plain integer adds (shares the adds between the
+// two pipes; the value is the plain sum).
+template <bool NEG, class TC>
+__device__ __forceinline__ void add_alu(TC &x, TC a, TC z)
+{
+    x = NEG ? (x - a) + z : (x + a) + z;
+}
+
+// ADDM 2 / 3 (integer columns): one column in four / in eight updated on the ALU pipe.
 template <class TC, int S, int ADDM, bool NEG>
-__device__ __forceinline__ TC add_min_interleaved(TC (&E)[S], const TC (&M)[S])
+__device__ __forceinline__ TC add_min_interleaved(TC (&E)[S], const TC (&M)[S], TC z = TC(0))
 {
     constexpr int NT = S / 3, NL = NT + S % 3;
     TC l1[NL];
@@ -520,7 +530,13 @@ __device__ __forceinline__ TC add_min_interleaved(TC (&E)[S], const TC (&M)[S])
         constexpr int pr = decltype(pc)::value, q = 2 * pr;
         constexpr bool paired = ADDM == 4 || (ADDM == 5 && pr % 2 == 0) || (ADDM == 6 && pr % 4 == 0) ||
                                 (ADDM == 7 && pr % 4 != 0);
-        add_pair<paired, NEG>(E[q], E[q + 1], M[q], M[q + 1]);
+        constexpr bool alu = !std::is_same_v<TC, float> && ((ADDM == 2 && q % 4 == 0) || (ADDM == 3 && q % 8 == 0));
+        if constexpr (alu) {
+            add_alu<NEG>(E[q], M[q], z);
+            E[q + 1] = NEG ? E[q + 1] - M[q + 1] : E[q + 1] + M[q + 1];
+        } else {
+            add_pair<paired, NEG>(E[q], E[q + 1], M[q], M[q + 1]);
+        }
         // triples completed by this pair: (3t, 3t+1, 3t+2) with 3t+2 in {q, q+1}
         static_for<2>([&](auto cc) {
             constexpr int c = q + decltype(cc)::value;
@@ -718,7 +734,7 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
             TC mfused{};
             if constexpr (fused) {
                 constexpr int kk = ctzc(p);
-                mfused = add_min_interleaved<TC, S, ADDM, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk]);
+                mfused = add_min_interleaved<TC, S, ADDM, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk], (TC)a.zero);
             } else if constexpr (p > 0) {
                 constexpr int kk = ctzc(p);
                 if constexpr (kk < RC) {
@@ -946,7 +962,8 @@ __device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &
             uint32_t mfused = 0;
             if constexpr (fused) {
                 constexpr int kk = ctzc(p);
-                mfused = add_min_interleaved<uint32_t, S, 0, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk]);
+                mfused = add_min_interleaved<uint32_t, S, ADDM, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk],
+                                                                                           (uint32_t)a.zero);
             } else if constexpr (p > 0) {
                 constexpr int kk = ctzc(p);
                 if constexpr (kk < RC) {

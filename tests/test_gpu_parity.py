@@ -370,7 +370,7 @@ def test_time_limit_returns_timeout(q):
 
 # --- compiled kernel variants and the n=44 FP32 configuration ---------------------------------
 
-@pytest.mark.parametrize("variant", range(18))
+@pytest.mark.parametrize("variant", range(20))
 def test_scan_variants_agree(q, variant, monkeypatch):
     monkeypatch.setenv("QUBO_SCAN_VARIANT", str(variant))
     Q = wl.upper_int(27, -300, 300, seed=90)
