@@ -17,6 +17,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libqubo.so")
+# The checked build: every device check of QUBO_DEBUG compiled in (an out-of-range index records
+# its site and the call returns QUBO_ERR_INTERNAL); slower, for tests and debugging only.
+DEBUG_OUT_DIR = os.path.join(PKG, "_build_debug")
+DEBUG_LIB = os.path.join(PKG, "libqubo_debug.so")
 
 SOURCES = ["scan_i32.cu", "scan_i64.cu", "scan_f32.cu", "scan_f64.cu", "scan_i32f.cu", "scan_i16p.cu", "scan_sparse.cu", "finalize.cu", "plan.cu", "api.cu", "noalloc.cu"]
 HEADERS = ["internal.h", "scan_impl.cuh", "zscan.h", "host.h"]
@@ -38,23 +42,26 @@ def _inputs():
     return files
 
 
-def is_stale() -> bool:
-    if not os.path.exists(LIB):
+def is_stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(f) > t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    """Compile every CUDA translation unit and link libqubo.so; returns its path."""
-    if not force and not is_stale():
-        return LIB
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, debug: bool = False) -> str:
+    """Compile every CUDA translation unit and link libqubo.so (debug=True: the checked build,
+    libqubo_debug.so, with -DQUBO_DEBUG); returns its path."""
+    lib, out_dir = (DEBUG_LIB, DEBUG_OUT_DIR) if debug else (LIB, OUT_DIR)
+    if not force and not is_stale(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(OUT_DIR, exist_ok=True)
+    os.makedirs(out_dir, exist_ok=True)
+    flags = NVCC_FLAGS + (["-DQUBO_DEBUG"] if debug else [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(out_dir, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc, *ARCH, *flags, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -67,13 +74,13 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     workers = jobs or min(len(SOURCES), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc, *ARCH, "-shared", *objs, "-o", tmp], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -131,6 +131,7 @@ struct Part {
     uint64_t scanned = 0, candidates = 0;
     double drift = 0.0, err = 0.0;
     bool overflow = false;
+    uint64_t dbg = 0;  // QUBO_DEBUG builds: site of the first failed device check
     // energy-window mode: every state with E <= min + window, (E, code) ascending (energies as
     // double; integer energies are exact in double below 2^53)
     std::vector<std::pair<double, uint64_t>> win;
@@ -832,6 +833,7 @@ Part part_from(const Down &d, const Job &j, int i)
         p.drift = ubits_to_double(d.sts[i].drift);
         p.err = ubits_to_double(d.sts[i].err);
         p.overflow = d.sts[i].dropped > 0;
+        p.dbg = d.sts[i].dbg;
     }
     return p;
 }
@@ -860,6 +862,14 @@ int job_finish(Workspace &ws, Job &j, std::vector<Part> &parts, double *gpu_seco
     }
     CK(cudaStreamSynchronize(j.stream));
     job_unpack(ws, j, parts, gpu_seconds);
+    for (size_t i = 0; i < parts.size(); ++i)
+        if (parts[i].dbg) {
+#ifdef QUBO_DEBUG
+            std::fprintf(stderr, "qubo: device check %llu failed (instance %zu of the launch)\n",
+                         (unsigned long long)parts[i].dbg, i);
+#endif
+            return QUBO_ERR_INTERNAL;
+        }
     if (j.window >= 0.0 && !parts.empty() && parts[0].has) {
         Part &p = parts[0];
         const bool fl = acc_float(j.acc);

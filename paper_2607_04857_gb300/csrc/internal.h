@@ -107,8 +107,18 @@ struct InstState {
     unsigned long long dropped;  // candidates not stored (buffer full)
     unsigned long long drift;    // float: max re-anchoring drift (bits of a non-negative double)
     unsigned long long err;      // float: max |E_scan - E64| (bits of a non-negative double)
-    unsigned long long pad;
+    unsigned long long dbg;      // QUBO_DEBUG builds: first failed device check (site number), else 0
 };
+
+// Device checks of a QUBO_DEBUG build (libqubo_debug.so): an index outside its table, a walked
+// row outside the walk, a work item outside its instance.  The first failure of an instance
+// records its site number in InstState::dbg and the access is skipped or clamped; the host then
+// returns QUBO_ERR_INTERNAL.  Nothing traps.  Release builds compile the checks away.
+#ifdef QUBO_DEBUG
+#define QUBO_DCHECK(cond, st, site) ((cond) ? true : (atomicCAS(&(st)->dbg, 0ull, (unsigned long long)(site)), false))
+#else
+#define QUBO_DCHECK(cond, st, site) true
+#endif
 
 // Per-instance result written by the extraction kernel.
 struct ResOut {

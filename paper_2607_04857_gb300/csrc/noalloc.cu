@@ -309,7 +309,7 @@ extern "C" int qubo_solve_noalloc(const void *Q_host, int n, qubo_dtype dtype, i
         NA_CK(cudaMemcpyAsync(out_states, base + lo.ties, sizeof(uint64_t) * states_cap, cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
 #undef NA_CK
-    if (!res.has || fin.scanned != (1ull << n) || fin.dropped)
+    if (!res.has || fin.scanned != (1ull << n) || fin.dropped || fin.dbg)
         return QUBO_ERR_INTERNAL;
     *out_min = res.min_i;
     *out_n_ties = res.n_ties;

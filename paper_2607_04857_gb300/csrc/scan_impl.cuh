@@ -641,6 +641,8 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
 
     // Flip of a walked row kk >= RC (row from memory, runtime sign).
     auto high_flip = [&](int kk, int sgn) {
+        if (!QUBO_DCHECK(kk >= RC && kk < L, st, 1))
+            kk = RC;
         const TC *row = Mt + (size_t)kk * NB;
         const TC sg = (TC)sgn;
 #pragma unroll
@@ -681,7 +683,9 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
                 fr[g * V + e] = bv[e];
         }
         for (unsigned bits = (unsigned)gi >> RC; bits; bits &= bits - 1) {
-            const int r = RC + __ffs(bits) - 1;
+            int r = RC + __ffs(bits) - 1;
+            if (!QUBO_DCHECK(r < L, st, 2))
+                r = RC;
             Pf = Pf + wsm[r];
             const TC *row = Mt + (size_t)r * NB;
 #pragma unroll
@@ -713,6 +717,8 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
     const int nblk = 1 << (L - RC - 1);
     const uint64_t cbase = unit << BL;
 
+    if (!QUBO_DCHECK(L >= RC + 1 && L <= kMaxWalkBits && nblk * BODY == (1 << L), st, 3))
+        return;
     for (int blk = 0; blk < nblk; ++blk) {
         const int i0 = blk * BODY;
         if constexpr (Tr<T>::kFloat) {
@@ -932,6 +938,8 @@ __device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &
     int32_t u = Treg + mu - P;
 
     auto high_flip = [&](int kk, int sgn) {
+        if (!QUBO_DCHECK(kk >= RC && kk < L, st, 4))
+            kk = RC;
         const uint32_t *row = Mt + (size_t)kk * NW;
         const uint32_t sg = (uint32_t)sgn;
 #pragma unroll
@@ -949,6 +957,8 @@ __device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &
     const int32_t *ELp = (const int32_t *)d.EL;
     const int nblk = 1 << (L - RC - 1);
     const uint64_t cbase = unit << BL;
+    if (!QUBO_DCHECK(L >= RC + 1 && L <= kMaxWalkBits && nblk * BODY == (1 << L), st, 5))
+        return;
 
     for (int blk = 0; blk < nblk; ++blk) {
         const int i0 = blk * BODY;
@@ -1115,7 +1125,12 @@ __device__ __forceinline__ void persistent_units(const ScanArgs &a, int lane, ty
                 cur = inst;
                 Treg = Tr<T>::thr_load(a.state + inst);
             }
+            if (!QUBO_DCHECK(inst >= 0 && inst < a.n_inst && item >= a.item_base[inst] && item < a.item_base[inst + 1],
+                             a.state + (inst >= 0 && inst < a.n_inst ? inst : 0), 6))
+                continue;
             const Inst d = a.inst[inst];
+            if (!QUBO_DCHECK(d.small || item - a.item_base[inst] < d.units, a.state + inst, 7))
+                continue;
             if (d.small) {
                 small_unit<T>(a, d, inst, lane);  // counts its own states
             } else {
