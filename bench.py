@@ -445,6 +445,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--compare-loop", action="store_true",
                     help="batched workload: also time a host loop of single solves")
+    ap.add_argument("--by-size", action="store_true",
+                    help="batched workload: also time sub-batches of the instances grouped by size n")
     ap.add_argument("--no-secondary", action="store_true",
                     help="default workload: skip the same-GPU comparisons (int32 kernel, FP32 vs FP64, batched)")
     args = ap.parse_args()
@@ -548,6 +550,30 @@ def main():
         e2e_note = ("qubo_solve_batched from host buffers in its packed layout (host preparation and copies "
                     "inside every step)")
         loop_rate = None
+        by_size = None
+        if args.by_size:
+            # where the batch's time goes: each size group alone as a device-resident batch
+            by_size = []
+            for lo, hi in ((16, 20), (21, 24), (25, 28), (29, 30), (31, 32)):
+                sub = [Q for Q in mats if lo <= Q.shape[0] <= hi]
+                if not sub:
+                    continue
+                b = q.Batch(sub, topk=0, states_cap=64)
+                b.run(stream)
+                b.fetch()
+                best = None
+                for _ in range(3):
+                    a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    b.run(stream)
+                    b.fetch()
+                    c.record(stream)
+                    torch.cuda.synchronize(dev)
+                    best = min(best or 1e9, a.elapsed_time(c) / 1000.0)
+                b.close()
+                st = sum(1 << Q.shape[0] for Q in sub)
+                by_size.append({"n": [lo, hi], "instances": len(sub), "states": st, "ms": best * 1000,
+                                "states_per_s": st / best, "instances_per_s": len(sub) / best})
         if args.compare_loop:
             # the plain form: one qubo_solve per instance, looped on the host
             t = time.perf_counter()
@@ -721,6 +747,8 @@ def main():
             line["cpu_baseline"] = cpu
         if sec:
             line["secondary"] = sec
+        if W["name"] == "batched" and by_size:
+            line["by_size"] = by_size
         if loop_rate:
             line["loop_baseline"] = {"value": loop_rate, "unit": "instances/s",
                                      "how": "qubo_solve per instance, looped on the host"}
