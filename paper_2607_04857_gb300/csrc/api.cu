@@ -1117,6 +1117,8 @@ void fill_plan_info(const HostInst &h, const SolveStats &stats, double t0, qubo_
     info->suffix_bits = h.small ? 0 : h.B;
     info->cols_per_thread = h.small ? 0 : acc_cols_per_thread(h.acc, h.variant);
     info->reg_rows = h.small ? 0 : variant_reg_rows(h);
+    info->fp32_err_bound = 0.0;  // single-instance calls fill these in (fill_fp32_bound)
+    info->fp32_rigorous_anchor_bits = -1;
     info->zero_rows = acc_factored(h.acc) ? h.Z : 0;
     info->anchor_bits = (h.acc == ACC_F32 && !h.small) ? std::min(h.anchor_bits, h.L) : 0;
     info->threads = kScanThreads;
