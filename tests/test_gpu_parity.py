@@ -503,6 +503,28 @@ def test_autotune_batched(q):
         q.autotune_clear()
 
 
+def test_autotune_batched_float_and_wide_accumulator(q):
+    """The batch autotuner on an FP32 batch (SK instances, n = 18..24) and on an int64 batch
+    (entries too wide for int32 energies): the tuned plans run and the results equal the
+    oracle's."""
+    fl = [wl.sk_float32(n, seed=600 + n) for n in (18, 19, 21, 22, 24)]
+    wide = [wl.upper_int(n, -(1 << 26), 1 << 26, seed=700 + n) for n in (17, 20, 23)]
+    try:
+        for insts, is_float in ((fl, True), (wide, False)):
+            q.autotune_clear()
+            p = q.autotune_batched(insts)
+            assert p["trials"] >= 1
+            for Q, r in zip(insts, q.solve_batched(insts, topk=3)):
+                o = oracle.solve(Q, topk=3, cap=64)
+                if is_float:
+                    check_float(r, o)
+                else:
+                    assert r.info["acc"] == "i64"
+                    check_int(r, o)
+    finally:
+        q.autotune_clear()
+
+
 def test_autotune_batched_per_size_plans_on_config4(q, tmp_path):
     """The batch autotuner on the 4096-instance configuration: one variant for the launch, a walk
     per instance size; the tuned plans are what the next batch runs (every instance's walk is its
