@@ -364,6 +364,27 @@ def secondary(q, torch, stream, l2buf, dev, gpu_index):
     return out
 
 
+def datapath_probe(clock_mhz: float):
+    """Cycles one Gray step's operation mix takes on one scheduler in isolation (the arithmetic
+    probe, csrc/pipe_probe.cu): the floor the scan kernels are held to.  None if it cannot run."""
+    try:
+        r = subprocess.run([sys.executable, "-m", "paper_2607_04857_gb300.pipe_probe", "--clock-mhz",
+                            f"{clock_mhz:.0f}"], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    except (OSError, subprocess.TimeoutExpired):
+        return None
+    out = {}
+    for line in r.stdout.splitlines():
+        for key, label in (("fp32_lane_step", "FP32-lane Gray step"), ("int32_step", "int32 Gray step"),
+                           ("packed_step", "packed 16-bit Gray step"), ("fadd", "FADD "),
+                           ("fmin3", "FMNMX3 (3 inputs)")):
+            if line.startswith(label):
+                try:
+                    out[key] = float(line.split("ms")[1].split("cycles")[0])
+                except (IndexError, ValueError):
+                    pass
+    return out if r.returncode == 0 and out else None
+
+
 # ---------------------------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------------------------
@@ -712,9 +733,9 @@ def main():
             "traffic": None, "kernel": "scan_kernel",
             "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes" + (" x 2 packed 16-bit halves" if halves == 2 else "")
                           + f" x {clk_max:.0f} MHz; {ops_per_state:.4g} ops/state"
-                          + " (one add and one min-reduction per lane and cycle: the 32-lane datapath the adds and"
-                            " mins share, measured by paper_2607_04857_gb300.pipe_probe)"
-                          + (" (add + min)" if acc not in ("i32z", "f32z") else
+                          + (" (one add and one min-reduction per state; adds and mins share the 32-lane datapath,"
+                             " one operation per lane and cycle: paper_2607_04857_gb300.pipe_probe)"
+                             if acc not in ("i32z", "f32z") else
                              f" (factored scan: 2/2^Z + 2/2^B, Z = {infos[0]['zero_rows']}, B = {infos[0]['suffix_bits']})")}
     if clocks and clocks.get("sm_mhz"):
         roof["frac_at_sampled_clock"] = achieved / (halves * sms * LANES_PER_SM * clocks["sm_mhz"] * 1e-3)
@@ -733,6 +754,19 @@ def main():
     sec = None
     if W["name"] == "n50_int32" and world == 1 and not args.no_secondary:
         sec = secondary(q, torch, stream, l2buf, dev, local)
+        # the dense scan's step floor on this GPU: cycles per 16-column step (512 states per warp)
+        # of the kernel against the same operation mix timed alone
+        clk = (clocks or {}).get("sm_mhz") or 2070.0
+        probe = datapath_probe(clk)
+        if probe and acc == "i32f" and probe.get("fp32_lane_step"):
+            kernel_cycles = sms * 4 * clk * 1e6 / ((per_launch_states / mean_scan) / 512.0)
+            roof["datapath"] = {"kernel_cycles_per_step": kernel_cycles,
+                                "probe_cycles_per_step": probe["fp32_lane_step"],
+                                "probe_cycles_per_16_fadd": probe.get("fadd"),
+                                "probe_cycles_per_16_fmnmx3": probe.get("fmin3"),
+                                "basis": "one Gray step = 16 columns x 32 lanes = 512 states per warp; probe: the "
+                                         "step's adds and mins alone with a loop counter (python -m "
+                                         "paper_2607_04857_gb300.pipe_probe)"}
 
     if rank == 0:
         line = {"metric": W["metric"], "value": value, "unit": W["unit"], "n_gpus": world, "steps": args.steps,
