@@ -568,6 +568,8 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
         d.k = h.k;
         d.small = h.small;
         d.clampC = h.clampC;
+        d.el_fused = j.acc == ACC_I16P ? h.el_fused : 0;
+        d.elmin = h.elmin;
         d.unit_begin = h.unit_begin;
         d.units = h.units;
         d.sub_base = h.sub_base;
@@ -1252,6 +1254,8 @@ int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
                                 (h.small || (alt_acc == ACC_I16P ? i16p_exact(h) : i32f_exact(h, &h.clampC)));
                 if (!ok)
                     all = false;
+                else if (alt_acc == ACC_I16P)
+                    i16p_fuse_el(h);
             }
         };
         parallel(alt_range);
@@ -2312,8 +2316,12 @@ int qubo_autotune_batched_ex(const void *Q_packed, const int *n, const size_t *o
                 return false;
             if (h.small)
                 return true;
-            if (acc == ACC_I16P)
-                return i16p_exact(h);
+            if (acc == ACC_I16P) {
+                if (!i16p_exact(h))
+                    return false;
+                i16p_fuse_el(h);
+                return true;
+            }
             if (acc == ACC_I32F)
                 return i32f_exact(h, &h.clampC);
             return true;

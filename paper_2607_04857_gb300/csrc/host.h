@@ -60,6 +60,7 @@ struct HostInst {
     double thr0 = 0.0;  // initial threshold (a bound on the K-th lowest energy of the range)
     int32_t clampC = 0; // ACC_I32F: threshold clamp
     int32_t col_lo = 0, col_hi = 0;  // ACC_I16P: proven range of every column value
+    int32_t el_fused = 0, elmin = 0; // ACC_I16P: E_L added to the packed minima (i16p_fuse_el)
     int Z = 0;                  // ACC_I32Z / ACC_F32Z: walked rows without suffix couplings
     std::vector<uint8_t> perm;  // ACC_I32Z / ACC_F32Z: caller's variable at each scan position
     bool no_factored = false;   // the factored FP32 scan used up its margin: plan the dense one
@@ -73,7 +74,7 @@ struct PlanFields {
     Acc acc;
     int variant, B, L, k, small, fix_bits;
     uint64_t fix_value, unit_begin, units, sub_base, sub_count, items, states;
-    int32_t clampC, col_lo, col_hi;
+    int32_t clampC, col_lo, col_hi, el_fused, elmin;
 };
 
 // Plans, saved and restored without the matrices.
@@ -104,6 +105,7 @@ bool i32f_allowed();
 void col_range_exact(const HostInst &h, int64_t &lo, int64_t &hi);
 int64_t walked_energy_max(const HostInst &h);
 bool i16p_exact(HostInst &h);
+void i16p_fuse_el(HostInst &h);
 bool i16p_allowed();
 int zero_rows_search(HostInst &h);
 bool i32z_allowed();

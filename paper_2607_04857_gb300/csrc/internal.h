@@ -96,6 +96,9 @@ struct Inst {
     int32_t Z;            // ACC_I32Z: walked rows 0..Z-1 have no coupling to a suffix variable
     int32_t anchor;       // float scans: re-anchor every 2^anchor walk steps (0 or >= L: at the end only)
     const uint8_t *perm;  // ACC_I32Z: variable of the caller's order at each scan position
+    int32_t el_fused;     // ACC_I16P: E_L stored as (E_L - elmin) in both 16-bit halves and added to the
+                          // packed column minima without a carry (the host proves the sums fit 16 bits)
+    int32_t elmin;        // ACC_I16P with el_fused: a lower bound of every E_L value
 };
 
 // Mutable per-instance state, updated with atomics.

@@ -23,8 +23,9 @@ namespace host {
 
 PlanFields plan_fields(const HostInst &h)
 {
-    return {h.acc,        h.variant, h.B,     h.L,        h.k,         h.small,  h.fix_bits, h.fix_value, h.unit_begin,
-            h.units,      h.sub_base, h.sub_count, h.items, h.states, h.clampC, h.col_lo,   h.col_hi};
+    return {h.acc,   h.variant,  h.B,         h.L,     h.k,      h.small,  h.fix_bits, h.fix_value, h.unit_begin,
+            h.units, h.sub_base, h.sub_count, h.items, h.states, h.clampC, h.col_lo,   h.col_hi,    h.el_fused,
+            h.elmin};
 }
 
 void set_plan_fields(HostInst &h, const PlanFields &p)
@@ -46,6 +47,8 @@ void set_plan_fields(HostInst &h, const PlanFields &p)
     h.clampC = p.clampC;
     h.col_lo = p.col_lo;
     h.col_hi = p.col_hi;
+    h.el_fused = p.el_fused;
+    h.elmin = p.elmin;
 }
 
 bool dtype_ok(qubo_dtype dt) { return dt == QUBO_I16 || dt == QUBO_I32 || dt == QUBO_F32 || dt == QUBO_F64; }
@@ -370,6 +373,50 @@ bool i16p_exact(HostInst &h)
     return true;
 }
 
+// Packed scan of a proven plan: whether E_L can be added to the packed column minima of a step
+// as one 32-bit add, E_L - elmin in both halves.  A half holds a column value plus 2^15, at most
+// col_hi + 2^15; the sum stays at most 65535 (no carry into the other half) when
+// col_hi + (max E_L - elmin) <= 32767.  Quick accept with elmin = -S_ww (S_ww = sum of |U| among
+// the walked variables bounds every |E_L|), else the exact E_L range by enumeration.
+// QUBO_NO_PACKED_FUSED=1 keeps the separate lane combine and add.
+void i16p_fuse_el(HostInst &h)
+{
+    h.el_fused = 0;
+    h.elmin = 0;
+    const char *v = std::getenv("QUBO_NO_PACKED_FUSED");
+    if (h.acc != ACC_I16P || h.small || (v && v[0] == '1'))
+        return;
+    const int n = h.n, B = h.B, L = h.L;
+    auto U = [&](int i, int j) { return i < j ? h.Ui[(size_t)i * n + j] : h.Ui[(size_t)j * n + i]; };
+    int64_t sww = 0;
+    for (int r = 0; r < L; ++r)
+        for (int t = r; t < L; ++t)
+            sww += std::llabs(U(B + r, B + t));
+    if ((int64_t)h.col_hi + 2 * sww <= 32767) {
+        h.el_fused = 1;
+        h.elmin = (int32_t)-sww;
+        return;
+    }
+    std::vector<int64_t> field(L, 0);
+    std::vector<int> x(L, 0);
+    int64_t e = 0, emin = 0, emax = 0;  // E_L of the empty pattern is 0
+    for (uint64_t i = 1; i < (1ull << L); ++i) {
+        const int r = __builtin_ctzll(i);
+        const int sg = x[r] ? -1 : 1;
+        e += sg * (U(B + r, B + r) + field[r]);
+        x[r] ^= 1;
+        for (int t = 0; t < L; ++t)
+            if (t != r)
+                field[t] += sg * U(B + r, B + t);
+        emin = std::min(emin, e);
+        emax = std::max(emax, e);
+    }
+    if ((int64_t)h.col_hi + (emax - emin) <= 32767) {
+        h.el_fused = 1;
+        h.elmin = (int32_t)emin;
+    }
+}
+
 // Factored scan of sparse instances: choose up to kZMaxRows walked variables with no coupling
 // to any of the B suffix variables (any order of the variables is allowed, Sec. 2.4), and a
 // scan order: suffix, those zero rows, the other walked rows, the unit's fixed bits, then the
@@ -520,8 +567,10 @@ int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int wal
             h.acc = ACC_I16P;
             h.variant = pick_variant(h.acc, variant_req);
             h.variant = fit_variant(h, fix_bits, split_k, walk_bits, variant_req, h.variant);
-            if (plan(h, fix_bits, fix_value, split_k, walk_bits) == QUBO_OK && i16p_exact(h))
+            if (plan(h, fix_bits, fix_value, split_k, walk_bits) == QUBO_OK && i16p_exact(h)) {
                 chosen = ACC_I16P;
+                i16p_fuse_el(h);
+            }
         }
         if (chosen == ACC_I32 && i32f_allowed()) {
             h.acc = ACC_I32F;

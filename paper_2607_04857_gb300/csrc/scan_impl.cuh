@@ -397,10 +397,14 @@ __global__ void tables_kernel(const Inst *insts)
                     if ((g >> r2) & 1)
                         acc += W[(B + r) * n + (B + r2)];
             }
-            if constexpr (kPacked)  // stored minus the lane bias: threshold - E_L is then a lane value
-                ((TP *)d.EL)[i] = (TP)acc - kLaneBias;
-            else
+            if constexpr (kPacked) {
+                if (d.el_fused)  // E_L - elmin in both halves, added to the packed minima of a step
+                    ((uint32_t *)d.EL)[i] = (uint32_t)((TP)acc - d.elmin) * 0x10001u;
+                else  // stored minus the lane bias: threshold - E_L is then a lane value
+                    ((TP *)d.EL)[i] = (TP)acc - kLaneBias;
+            } else {
                 ((TC *)d.EL)[i] = (TC)acc;
+            }
         }
     }
 }
@@ -960,123 +964,154 @@ __device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &
     if (!QUBO_DCHECK(L >= RC + 1 && L <= kMaxWalkBits && nblk * BODY == (1 << L), st, 5))
         return;
 
-    for (int blk = 0; blk < nblk; ++blk) {
-        const int i0 = blk * BODY;
-        int32_t elv[V];
-        bool hit = false;
-        int32_t Pmid = P;
-        int32_t acc_lo, acc_hi, mprev;  // as in scan_unit, in lane units
-        static_for<BODY>([&](auto pc) {
-            constexpr int p = decltype(pc)::value;
-            constexpr bool fused = ILV && MINM == 3 && p > 0 && ctzc(p) < RC;
-            uint32_t mfused = 0;
-            if constexpr (fused) {
-                constexpr int kk = ctzc(p);
-                mfused = add_min_interleaved<uint32_t, S, ADDM, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk],
-                                                                                           (uint32_t)a.zero);
-            } else if constexpr (p > 0) {
-                constexpr int kk = ctzc(p);
-                if constexpr (kk < RC) {
-                    constexpr bool neg = (p >> (kk + 1)) & 1;
-                    if constexpr (ADDM == 2 || ADDM == 3) {
-                        const uint32_t z = (uint32_t)a.zero;
-#pragma unroll
-                        for (int q = 0; q < S; ++q) {
-                            if (q % (ADDM == 2 ? 4 : 8) == 0)
-                                E[q] = neg ? (E[q] - Mr[kk][q]) + z : (E[q] + Mr[kk][q]) + z;
-                            else
+    const uint32_t *EL2p = (const uint32_t *)d.EL;
+    // the Gray walk, with E_L added per step (as int32) or fused into the packed minima
+    auto walk = [&](auto elf) {
+        for (int blk = 0; blk < nblk; ++blk) {
+            const int i0 = blk * BODY;
+            int32_t elv[V];
+            uint32_t el2v[V];
+            bool hit = false;
+            int32_t Pmid = P;
+            int32_t acc_lo, acc_hi, mprev;  // as in scan_unit, in lane units
+            uint32_t acc2_lo, acc2_hi, mprev2;  // fused: packed running minima of (lanes + E_L - elmin)
+            static_for<BODY>([&](auto pc) {
+                constexpr int p = decltype(pc)::value;
+                constexpr bool fused = ILV && MINM == 3 && p > 0 && ctzc(p) < RC;
+                uint32_t mfused = 0;
+                if constexpr (fused) {
+                    constexpr int kk = ctzc(p);
+                    mfused = add_min_interleaved<uint32_t, S, ADDM, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk],
+                                                                                               (uint32_t)a.zero);
+                } else if constexpr (p > 0) {
+                    constexpr int kk = ctzc(p);
+                    if constexpr (kk < RC) {
+                        constexpr bool neg = (p >> (kk + 1)) & 1;
+                        if constexpr (ADDM == 2 || ADDM == 3) {
+                            const uint32_t z = (uint32_t)a.zero;
+    #pragma unroll
+                            for (int q = 0; q < S; ++q) {
+                                if (q % (ADDM == 2 ? 4 : 8) == 0)
+                                    E[q] = neg ? (E[q] - Mr[kk][q]) + z : (E[q] + Mr[kk][q]) + z;
+                                else
+                                    E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
+                            }
+                        } else {
+    #pragma unroll
+                            for (int q = 0; q < S; ++q)
                                 E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
                         }
                     } else {
-#pragma unroll
-                        for (int q = 0; q < S; ++q)
-                            E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
+                        Pmid = P;
+                        high_flip(RC, (blk & 1) ? -1 : 1);
                     }
+                }
+                uint32_t mw;
+                if constexpr (fused)
+                    mw = mfused;
+                else
+                    mw = tree_min<uint32_t, MINM, S>(E);
+                constexpr int HALF = BODY / 2, ph = p % HALF;
+                if constexpr (decltype(elf)::value) {
+                    // E_L - elmin added to both halves at once (no carry: proven on the host), packed
+                    // running minimum; the halves are combined once per half body
+                    if constexpr (p % V == 0)
+                        vload<uint32_t>(EL2p + i0 + p, el2v);
+                    const uint32_t sp = mw + el2v[p % V];
+                    uint32_t &acc2 = p < HALF ? acc2_lo : acc2_hi;
+                    if constexpr (ph % 2 == 0)
+                        mprev2 = sp;
+                    else if constexpr (ph == 1)
+                        acc2 = __vminu2(mprev2, sp);
+                    else
+                        acc2 = __vimin3_u16x2(acc2, mprev2, sp);
+                    if constexpr (p == HALF - 1)
+                        hit = min((int32_t)(acc2_lo & 0xffffu), (int32_t)(acc2_lo >> 16)) <= u - d.elmin + kLaneBias;
                 } else {
-                    Pmid = P;
-                    high_flip(RC, (blk & 1) ? -1 : 1);
+                    if constexpr (p % V == 0)
+                        vload<int32_t>(ELp + i0 + p, elv);
+                    const int32_t mp = min((int32_t)(mw & 0xffffu), (int32_t)(mw >> 16)) + elv[p % V];
+                    int32_t &acc = p < HALF ? acc_lo : acc_hi;
+                    if constexpr (ph % 2 == 0)
+                        mprev = mp;
+                    else if constexpr (ph == 1)
+                        acc = min(mprev, mp);
+                    else
+                        acc = __vimin3_s32(acc, mprev, mp);
+                    if constexpr (p == HALF - 1)
+                        hit = acc_lo <= u;
                 }
-            }
-            if constexpr (p % V == 0)
-                vload<int32_t>(ELp + i0 + p, elv);
-            uint32_t mw;
-            if constexpr (fused)
-                mw = mfused;
+            });
+            if constexpr (decltype(elf)::value)
+                hit = hit || min((int32_t)(acc2_hi & 0xffffu), (int32_t)(acc2_hi >> 16)) <= u - d.elmin + kLaneBias;
             else
-                mw = tree_min<uint32_t, MINM, S>(E);
-            const int32_t mp = min((int32_t)(mw & 0xffffu), (int32_t)(mw >> 16)) + elv[p % V];
-            constexpr int HALF = BODY / 2, ph = p % HALF;
-            int32_t &acc = p < HALF ? acc_lo : acc_hi;
-            if constexpr (ph % 2 == 0)
-                mprev = mp;
-            else if constexpr (ph == 1)
-                acc = min(mprev, mp);
-            else
-                acc = __vimin3_s32(acc, mprev, mp);
-            if constexpr (p == HALF - 1)
-                hit = acc_lo <= u;
-        });
-        hit = hit || acc_hi <= u;
-        if (hit) {
-            const int iend = i0 + BODY - 1;
-            const int gend = iend ^ (iend >> 1);
-            const uint32_t *rowRC = Mt + (size_t)RC * NW;
-#pragma unroll 1
-            for (int p = 0; p < BODY; ++p) {
-                const int i = i0 + p;
-                const int gp = i ^ (i >> 1);
-                uint32_t sr[RC];
-#pragma unroll
-                for (int r = 0; r < RC; ++r)
-                    sr[r] = (uint32_t)(((gp >> r) & 1) - ((gend >> r) & 1));
-                const int dRC = ((gp >> RC) & 1) - ((gend >> RC) & 1);
-                const uint32_t sRC = (uint32_t)dRC;
-                const int32_t Pp = dRC == 0 ? P : Pmid;
-                const int32_t el = ELp[i] + kLaneBias;
-                int32_t tp = Treg + mu - Pp - el;
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    uint32_t mv[V];
-                    vload<uint32_t>(rowRC + (g * 32 + lane) * V, mv);
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        const int q = g * V + e;
-                        uint32_t ev = E[q];
-#pragma unroll
-                        for (int r = 0; r < RC; ++r)
-                            ev = ev + sr[r] * Mr[r][q];
-                        stage[q * 32 + lane] = ev + sRC * mv[e];
+                hit = hit || acc_hi <= u;
+            if (hit) {
+                const int iend = i0 + BODY - 1;
+                const int gend = iend ^ (iend >> 1);
+                const uint32_t *rowRC = Mt + (size_t)RC * NW;
+    #pragma unroll 1
+                for (int p = 0; p < BODY; ++p) {
+                    const int i = i0 + p;
+                    const int gp = i ^ (i >> 1);
+                    uint32_t sr[RC];
+    #pragma unroll
+                    for (int r = 0; r < RC; ++r)
+                        sr[r] = (uint32_t)(((gp >> r) & 1) - ((gend >> r) & 1));
+                    const int dRC = ((gp >> RC) & 1) - ((gend >> RC) & 1);
+                    const uint32_t sRC = (uint32_t)dRC;
+                    const int32_t Pp = dRC == 0 ? P : Pmid;
+                    const int32_t el = decltype(elf)::value ? (int32_t)(EL2p[i] & 0xffffu) + d.elmin : ELp[i] + kLaneBias;
+                    int32_t tp = Treg + mu - Pp - el;
+    #pragma unroll
+                    for (int g = 0; g < G; ++g) {
+                        uint32_t mv[V];
+                        vload<uint32_t>(rowRC + (g * 32 + lane) * V, mv);
+    #pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            const int q = g * V + e;
+                            uint32_t ev = E[q];
+    #pragma unroll
+                            for (int r = 0; r < RC; ++r)
+                                ev = ev + sr[r] * Mr[r][q];
+                            stage[q * 32 + lane] = ev + sRC * mv[e];
+                        }
                     }
-                }
-                const uint64_t cb = cbase | ((uint64_t)gp << B);
-                const int32_t Ep = Pp + el;
-#pragma unroll 1
-                for (int q = 0; q < 2 * S; ++q) {
-                    const uint32_t word = stage[(q >> 1) * 32 + lane];
-                    const int32_t col = (int32_t)((q & 1) ? (word >> 16) : (word & 0xffffu)) - kLaneBias;
-                    if (col <= tp) {
-                        const int32_t Et = col + Ep;
-                        const int qw = q >> 1;
-                        const uint32_t j = (uint32_t)(((qw / V) * 32 + lane) * V + (qw % V)) + ((q & 1) ? NW : 0);
-                        record<T>(a, inst, Et, cb | j);
-                        if (K1 && Et < Treg) {
-                            Treg = Et;
-                            tp = Treg + mu - Pp - el;
-                            Tr<T>::thr_min(st, Et);
+                    const uint64_t cb = cbase | ((uint64_t)gp << B);
+                    const int32_t Ep = Pp + el;
+    #pragma unroll 1
+                    for (int q = 0; q < 2 * S; ++q) {
+                        const uint32_t word = stage[(q >> 1) * 32 + lane];
+                        const int32_t col = (int32_t)((q & 1) ? (word >> 16) : (word & 0xffffu)) - kLaneBias;
+                        if (col <= tp) {
+                            const int32_t Et = col + Ep;
+                            const int qw = q >> 1;
+                            const uint32_t j = (uint32_t)(((qw / V) * 32 + lane) * V + (qw % V)) + ((q & 1) ? NW : 0);
+                            record<T>(a, inst, Et, cb | j);
+                            if (K1 && Et < Treg) {
+                                Treg = Et;
+                                tp = Treg + mu - Pp - el;
+                                Tr<T>::thr_min(st, Et);
+                            }
                         }
                     }
                 }
+                u = Treg + mu - P;
             }
-            u = Treg + mu - P;
+            if (blk + 1 < nblk) {
+                const int ip = (blk + 1) * BODY;
+                const int kk = __ffs(ip) - 1;
+                high_flip(kk, ((ip >> (kk + 1)) & 1) ? -1 : 1);
+            }
         }
-        if (blk + 1 < nblk) {
-            const int ip = (blk + 1) * BODY;
-            const int kk = __ffs(ip) - 1;
-            high_flip(kk, ((ip >> (kk + 1)) & 1) ? -1 : 1);
-        }
-    }
 
 
+
+    };
+    if (d.el_fused)
+        walk(std::true_type{});
+    else
+        walk(std::false_type{});
 }
 
 // Persistent work loop: a warp claims work units from the queue, kChunk at a time (the next claim

@@ -105,6 +105,20 @@ def test_packed_variants_agree(q, variant, monkeypatch):
     check_int(r, oracle.solve(Qk1.astype(np.int32)))
 
 
+@pytest.mark.parametrize("fused", [True, False])
+def test_packed_fused_and_separate_el(q, fused, monkeypatch):
+    """The packed scan adds E_L to a step's packed column minima as one 32-bit add when the host
+    proves no half can carry (the default when it can), else combines the halves first; both
+    give the oracle's results, on Max-Cut and int16-entry instances and a walk of 2^12 steps."""
+    if not fused:
+        monkeypatch.setenv("QUBO_NO_PACKED_FUSED", "1")
+    for Q, kw in ((wl.maxcut_qubo(30, 0.5, seed=77), {}), (wl.upper_int(29, -127, 127, seed=78, dtype=np.int16), {}),
+                  (wl.upper_int(31, -127, 127, seed=79, dtype=np.int16), {"walk_bits": 12})):
+        r = q.solve(Q, topk=16, **kw)
+        assert r.info["acc"] == "i16p"
+        check_int(r, oracle.solve(Q.astype(np.int32), topk=16))
+
+
 @pytest.mark.parametrize("walk_bits", [4, 5, 7, 10, 13])
 def test_packed_plan_shapes(q, walk_bits):
     Q = wl.upper_int(28, -60, 60, seed=12, dtype=np.int16)
