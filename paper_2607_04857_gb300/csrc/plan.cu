@@ -376,9 +376,10 @@ bool i16p_exact(HostInst &h)
 // Packed scan of a proven plan: whether E_L can be added to the packed column minima of a step
 // as one 32-bit add, E_L - elmin in both halves.  A half holds a column value plus 2^15, at most
 // col_hi + 2^15; the sum stays at most 65535 (no carry into the other half) when
-// col_hi + (max E_L - elmin) <= 32767.  Quick accept with elmin = -S_ww (S_ww = sum of |U| among
-// the walked variables bounds every |E_L|), else the exact E_L range by enumeration.
-// QUBO_NO_PACKED_FUSED=1 keeps the separate lane combine and add.
+// col_hi + (max E_L - elmin) <= 32767.  Quick accept with elmin = the sum of the negative entries
+// among the walked variables (a lower bound of every E_L, and E_L - elmin is at most S_ww, the sum
+// of their |U|), else the exact E_L range by enumeration.  QUBO_NO_PACKED_FUSED=1 keeps the
+// separate lane combine and add.
 void i16p_fuse_el(HostInst &h)
 {
     h.el_fused = 0;
@@ -388,13 +389,16 @@ void i16p_fuse_el(HostInst &h)
         return;
     const int n = h.n, B = h.B, L = h.L;
     auto U = [&](int i, int j) { return i < j ? h.Ui[(size_t)i * n + j] : h.Ui[(size_t)j * n + i]; };
-    int64_t sww = 0;
+    int64_t sww = 0, neg = 0;
     for (int r = 0; r < L; ++r)
-        for (int t = r; t < L; ++t)
-            sww += std::llabs(U(B + r, B + t));
-    if ((int64_t)h.col_hi + 2 * sww <= 32767) {
+        for (int t = r; t < L; ++t) {
+            const int64_t w = U(B + r, B + t);
+            sww += std::llabs(w);
+            neg += w < 0 ? w : 0;
+        }
+    if ((int64_t)h.col_hi + sww <= 32767) {
         h.el_fused = 1;
-        h.elmin = (int32_t)-sww;
+        h.elmin = (int32_t)neg;
         return;
     }
     std::vector<int64_t> field(L, 0);
