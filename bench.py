@@ -375,7 +375,7 @@ def datapath_probe(clock_mhz: float):
     out = {}
     for line in r.stdout.splitlines():
         for key, label in (("fp32_lane_step", "FP32-lane Gray step"), ("int32_step", "int32 Gray step"),
-                           ("packed_step", "packed 16-bit Gray step"), ("fadd", "FADD "),
+                           ("packed_step", "packed 16-bit Gray step"), ("fadd", "FADD "), ("fadd2", "FADD2 ("),
                            ("fmin3", "FMNMX3 (3 inputs)")):
             if line.startswith(label):
                 try:
@@ -721,6 +721,12 @@ def main():
     # the packed scan holds two 16-bit columns in each 32-bit lane: twice the lane-ops per cycle
     halves = 2 if acc == "i16p" else 1
     ops_per_state = ALG_OPS_PER_STATE
+    grouped = bool(infos[0].get("grouped"))
+    if grouped:
+        # grouped form: one add per state, and one min per column per group of 16 Gray steps (the
+        # exact minimum at the group's first state); the min tree of a group runs only when its
+        # lower bound reaches the threshold
+        ops_per_state = 1.0 + 1.0 / 16
     if acc in ("i32z", "f32z"):
         # factored scan: one add and one min per column per block of 2^Z walk steps, and one
         # add and one min per walk step per 2^B columns (the block minima of E_L)
@@ -733,7 +739,10 @@ def main():
             "traffic": None, "kernel": "scan_kernel",
             "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes" + (" x 2 packed 16-bit halves" if halves == 2 else "")
                           + f" x {clk_max:.0f} MHz; {ops_per_state:.4g} ops/state"
-                          + (" (one add and one min-reduction per state; adds and mins share the 32-lane datapath,"
+                          + (" (grouped form: one add per state and one min per column per group of 16 Gray steps;"
+                             " a group's min tree runs only when its lower bound reaches the threshold; one operation"
+                             " per lane and cycle: paper_2607_04857_gb300.pipe_probe)" if grouped else
+                             " (one add and one min-reduction per state; adds and mins share the 32-lane datapath,"
                              " one operation per lane and cycle: paper_2607_04857_gb300.pipe_probe)"
                              if acc not in ("i32z", "f32z") else
                              f" (factored scan: 2/2^Z + 2/2^B, Z = {infos[0]['zero_rows']}, B = {infos[0]['suffix_bits']})")}
@@ -758,15 +767,17 @@ def main():
         # of the kernel against the same operation mix timed alone
         clk = (clocks or {}).get("sm_mhz") or 2070.0
         probe = datapath_probe(clk)
-        if probe and acc == "i32f" and probe.get("fp32_lane_step"):
+        key = "fadd2" if grouped else "fp32_lane_step"
+        if probe and acc == "i32f" and probe.get(key):
             kernel_cycles = sms * 4 * clk * 1e6 / ((per_launch_states / mean_scan) / 512.0)
             roof["datapath"] = {"kernel_cycles_per_step": kernel_cycles,
-                                "probe_cycles_per_step": probe["fp32_lane_step"],
+                                "probe_cycles_per_step": probe[key],
                                 "probe_cycles_per_16_fadd": probe.get("fadd"),
                                 "probe_cycles_per_16_fmnmx3": probe.get("fmin3"),
-                                "basis": "one Gray step = 16 columns x 32 lanes = 512 states per warp; probe: the "
-                                         "step's adds and mins alone with a loop counter (python -m "
-                                         "paper_2607_04857_gb300.pipe_probe)"}
+                                "basis": "one Gray step = 16 columns x 32 lanes = 512 states per warp; probe: "
+                                         + ("the step's 16 column adds as 8 paired f32x2 adds alone (the grouped "
+                                            "form's floor)" if grouped else "the step's adds and mins alone")
+                                         + " with a loop counter (python -m paper_2607_04857_gb300.pipe_probe)"}
 
     if rank == 0:
         line = {"metric": W["metric"], "value": value, "unit": W["unit"], "n_gpus": world, "steps": args.steps,

@@ -71,7 +71,7 @@ class ResultInfo(ctypes.Structure):
         ("passes", ctypes.c_int32), ("kernel_launches", ctypes.c_int32), ("zero_rows", ctypes.c_int32),
         ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
         ("fp32_err_bound", ctypes.c_double), ("fp32_rigorous_anchor_bits", ctypes.c_int32),
-        ("reg_rows", ctypes.c_int32),
+        ("reg_rows", ctypes.c_int32), ("variant", ctypes.c_int32), ("grouped", ctypes.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -447,7 +447,8 @@ def plan_query(Q, topk: int = 0, split_k: int = 0, walk_bits: int = 0, fix_bits:
     _check(lib.qubo_plan_query(_ptr(Qm), Qm.shape[0], dt, ctypes.byref(o), ctypes.byref(info)), "qubo_plan_query")
     d = info.as_dict()
     return {k: d[k] for k in ("acc", "n", "split_k", "walk_bits", "suffix_bits", "cols_per_thread", "zero_rows",
-                              "anchor_bits", "fp32_err_bound", "fp32_rigorous_anchor_bits", "reg_rows")}
+                              "anchor_bits", "fp32_err_bound", "fp32_rigorous_anchor_bits", "reg_rows",
+                              "variant", "grouped")}
 
 
 def solve_window(Q, window: float, cap: int = 1 << 16, fix_bits: int = 0, fix_value: int = 0, plain: bool = False,

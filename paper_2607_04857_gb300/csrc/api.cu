@@ -514,8 +514,8 @@ int job_layout(Job &j)
         j.off_M[i] = o;
         o = align_up(o + eb * NB * h.L, 256);
         j.off_EL[i] = o;
-        o = align_up(o + eb * NL, 256);
-        j.max_entries = std::max(j.max_entries, (int)(NB * (h.L + 1) + NL));
+        o = align_up(o + eb * (NL + NL / 16 + 1), 256);  // E_L, then its group minima (FP32 lanes)
+        j.max_entries = std::max(j.max_entries, (int)(NB * (h.L + 1) + NL + NL / 16));
     }
     // results
     size_t d = 0;
@@ -1119,6 +1119,8 @@ void fill_plan_info(const HostInst &h, const SolveStats &stats, double t0, qubo_
     info->suffix_bits = h.small ? 0 : h.B;
     info->cols_per_thread = h.small ? 0 : acc_cols_per_thread(h.acc, h.variant);
     info->reg_rows = h.small ? 0 : variant_reg_rows(h);
+    info->variant = h.small || acc_factored(h.acc) ? -1 : h.variant;
+    info->grouped = !h.small && grouped_form(h.acc, h.variant);
     info->fp32_err_bound = 0.0;  // single-instance calls fill these in (fill_fp32_bound)
     info->fp32_rigorous_anchor_bits = -1;
     info->zero_rows = acc_factored(h.acc) ? h.Z : 0;
@@ -1259,6 +1261,15 @@ int batch_plan(std::vector<HostInst> &hs, int topk, std::vector<int> &order)
             }
         };
         parallel(alt_range);
+        if (all && alt_acc == ACC_I16P) {
+            // one kernel for the batch: the fused-only twin when every instance's E_L is fused
+            bool fused = true;
+            for (const HostInst &h : hs)
+                fused = fused && (h.small || h.el_fused);
+            const int v3 = packed_variant_for(v2, fused);
+            for (HostInst &h : hs)
+                h.variant = v3;
+        }
         if (all)
             break;
         for (int i = 0; i < count; ++i)
@@ -2320,7 +2331,8 @@ int qubo_autotune_batched_ex(const void *Q_packed, const int *n, const size_t *o
                 if (!i16p_exact(h))
                     return false;
                 i16p_fuse_el(h);
-                return true;
+                // a fused-only packed kernel takes only plans whose E_L is fused
+                return h.el_fused || !packed_fused_only(h.variant);
             }
             if (acc == ACC_I32F)
                 return i32f_exact(h, &h.clampC);

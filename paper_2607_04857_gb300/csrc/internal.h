@@ -23,42 +23,79 @@ enum Acc : int32_t {
     ACC_F32Z = 8
 };
 
-// Walked prefix rows kept in registers by the scan kernel (the largest of the compiled
-// variants); the inner loop is unrolled over 2^(RC+1) Gray steps so that every register-row
-// flip has a compile-time sign.  A plan needs walk_bits >= kRegRows + 1.
+// The shortest walk the allocation-free plan and the autotuner's walk sweep consider is
+// kRegRows + 1 bits.  Each compiled variant keeps RC walked rows (2 to 5) in registers and
+// unrolls its inner loop over 2^(RC+1) Gray steps, so that every register-row flip has a
+// compile-time sign; a plan needs walk_bits >= RC + 1, checked per variant.
 constexpr int kRegRows = 4;
 // Compiled scan variants of the 4-byte accumulators: columns per thread S, register rows,
 // minimum resident blocks per SM, how the adds are issued (0: compiler's choice, 4: FP32 adds as
 // paired f32x2 operations, two columns per instruction, 5, 6, 7: a half, a quarter or three
 // quarters of them paired; the paired modes do not apply to integer columns; 2, 3: in the
 // interleaved form, one integer column in four / in eight updated by a 3-input add on the ALU
-// pipe), 2- or 3-input mins, and whether a register-row step issues its adds and
-// the first level of its min tree interleaved (each triple of columns reduced as soon as its adds
-// are issued) or all adds first.  The 8-byte accumulators compile one variant: S = 16 with
-// variant 0's register rows, blocks and min inputs.
-constexpr int kScanVariants = 20;
-constexpr int kVariantCols[kScanVariants] = {32, 16, 16, 16, 16, 16, 32, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
-constexpr int kVariantRegRows[kScanVariants] = {3, 4, 4, 3, 4, 4, 3, 4, 4, 4, 4, 3, 3, 3, 3, 3, 5, 5, 5, 5};
-constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 3, 3, 3, 3, 2, 3, 3, 3, 3, 4, 4, 4, 3, 3, 2, 2, 2, 2};
-constexpr int kVariantAddMode[kScanVariants] = {0, 6, 7, 0, 0, 4, 4, 5, 6, 5, 4, 6, 4, 0, 4, 4, 6, 0, 3, 2};
-constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
-constexpr int kVariantInterleave[kScanVariants] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 0, 1, 1, 1, 1, 1};
+// pipe), 2- or 3-input mins, and the step form: 0, all adds first, then the min tree; 1, the adds
+// interleaved with the first level of the min tree (each triple of columns reduced as soon as its
+// adds are issued); 2 (integers in FP32 lanes; form 1 for the other accumulators), the grouped
+// form: groups of 16 steps skip the min tree while a per-thread lower bound of the column
+// minimum, moved by the steps' smallest column deltas, proves that no column can reach the
+// threshold.  The 8-byte
+// accumulators compile one variant: S = 16 with variant 0's register rows, blocks and min inputs.
+constexpr int kScanVariants = 24;
+constexpr int kVariantCols[kScanVariants] = {32, 16, 16, 16, 16, 16, 32, 16, 16, 16, 16, 16,
+                                             16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
+constexpr int kVariantRegRows[kScanVariants] = {3, 4, 4, 3, 4, 4, 3, 4, 4, 4, 4, 3, 3, 3, 3, 3, 5, 5, 5, 5, 5, 4, 5, 4};
+constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 3, 3, 3, 3, 2, 3, 3, 3, 3, 4, 4, 4, 3, 3, 2, 2, 2, 2, 3, 3, 2, 3};
+constexpr int kVariantAddMode[kScanVariants] = {0, 6, 7, 0, 0, 4, 4, 5, 6, 5, 4, 6, 4, 0, 4, 4, 6, 0, 3, 2, 4, 4, 4, 6};
+constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3,
+                                                  3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
+constexpr int kVariantInterleave[kScanVariants] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2};
+// The step form a kernel of an accumulator compiles for a variant: the grouped form only for
+// integers in FP32 lanes.
+constexpr int step_form(int variant, bool int_in_fp32)
+{
+    return kVariantInterleave[variant] == 2 && !int_in_fp32 ? 1 : kVariantInterleave[variant];
+}
+// Whether a plan's scan kernel runs the grouped form.
+constexpr bool grouped_form(Acc acc, int variant)
+{
+    return acc == ACC_I32F && variant >= 0 && variant < kScanVariants && kVariantInterleave[variant] == 2;
+}
 // Default variant per 4-byte accumulator (measured on GB300; see the profiles).
 constexpr int kDefaultVariantI32 = 16;
 constexpr int kDefaultVariantF32 = 16;
-constexpr int kDefaultVariantI32F = 16;
+constexpr int kDefaultVariantI32F = 20;
 constexpr int kDefaultVariantI16P = 14;
 // Compiled variants of the packed 16-bit scan: S words per thread (2 S columns), register rows,
 // minimum resident blocks per SM, and how the adds are issued (0: compiler's choice; 2 and 3: one
 // add in four or in eight as a 3-input add with a runtime 0, which the ALU pipe executes, so
 // that the ALU and FMA pipes share the adds).  All use 3-input mins.
 // Variants 8-14 and 16-19 interleave the adds and the first min level as the 4-byte variants do
-// (18 and 19 with one add in eight / in four on the ALU pipe, the others with plain adds).
-constexpr int kPackedWords[kScanVariants] = {16, 16, 16, 16, 16, 32, 32, 16, 16, 16, 16, 16, 32, 16, 16, 16, 32, 16, 16, 16};
-constexpr int kPackedRegRows[kScanVariants] = {3, 3, 3, 3, 3, 2, 2, 2, 3, 3, 4, 2, 2, 4, 5, 4, 3, 5, 5, 5};
-constexpr int kPackedMinBlocks[kScanVariants] = {3, 3, 3, 4, 4, 2, 2, 4, 3, 4, 3, 4, 2, 2, 2, 2, 2, 1, 2, 2};
-constexpr int kPackedAddMode[kScanVariants] = {0, 3, 2, 0, 3, 0, 3, 3, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 3, 2};
-constexpr int kPackedInterleave[kScanVariants] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 0, 1, 1, 1, 1};
+// (18 and 19 with one add in eight / in four on the ALU pipe, the others with plain adds), and
+// carry both forms of the E_L step (added to the packed minimum, or after the lane combine),
+// chosen per instance at run time.  Variants 20-23 are 14, 13, 8 and 11 compiled with the fused
+// form alone (interleave 2), half the code, for plans whose E_L is fused.
+constexpr int kPackedWords[kScanVariants] = {16, 16, 16, 16, 16, 32, 32, 16, 16, 16, 16, 16,
+                                             32, 16, 16, 16, 32, 16, 16, 16, 16, 16, 16, 16};
+constexpr int kPackedRegRows[kScanVariants] = {3, 3, 3, 3, 3, 2, 2, 2, 3, 3, 4, 2, 2, 4, 5, 4, 3, 5, 5, 5, 5, 4, 3, 2};
+constexpr int kPackedMinBlocks[kScanVariants] = {3, 3, 3, 4, 4, 2, 2, 4, 3, 4, 3, 4, 2, 2, 2, 2, 2, 1, 2, 2, 2, 2, 3, 4};
+constexpr int kPackedAddMode[kScanVariants] = {0, 3, 2, 0, 3, 0, 3, 3, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 3, 2, 0, 0, 0, 0};
+constexpr int kPackedInterleave[kScanVariants] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 1, 0, 1, 1, 1, 1, 2, 2, 2, 2};
+// The packed variant a plan runs: the fused-only twin of a variant when its E_L is fused and the
+// twin exists, else the variant that carries both forms.
+constexpr int packed_variant_for(int variant, bool el_fused)
+{
+    constexpr int kBoth[4] = {14, 13, 8, 11};
+    int both = variant;
+    for (int t = 0; t < 4; ++t)
+        if (variant == 20 + t)
+            both = kBoth[t];
+    if (el_fused)
+        for (int t = 0; t < 4; ++t)
+            if (both == kBoth[t])
+                return 20 + t;
+    return both;
+}
+constexpr bool packed_fused_only(int variant) { return variant >= 0 && variant < kScanVariants && kPackedInterleave[variant] == 2; }
 // Threads per block of the scan kernel (4 warps; every warp owns one work unit at a time).
 constexpr int kScanThreads = 128;
 // Longest Gray walk inside one work unit (also the FP32 re-anchoring period).

@@ -574,6 +574,7 @@ int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int wal
             if (plan(h, fix_bits, fix_value, split_k, walk_bits) == QUBO_OK && i16p_exact(h)) {
                 chosen = ACC_I16P;
                 i16p_fuse_el(h);
+                h.variant = packed_variant_for(h.variant, h.el_fused);
             }
         }
         if (chosen == ACC_I32 && i32f_allowed()) {

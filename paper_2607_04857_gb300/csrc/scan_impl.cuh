@@ -55,6 +55,9 @@ struct i16p {};
 
 template <>
 struct Tr<int32_t> {
+    // No grouped step form: integer adds are associative, so the compiler folds a skipped group's
+    // 15 column updates into one, and the scan would no longer form every state's energy.
+    static constexpr bool kGrouped = false;
     using TC = int32_t;
     using TP = int32_t;
     static constexpr bool kIntInFloat = false;
@@ -74,6 +77,7 @@ struct Tr<int32_t> {
 
 template <>
 struct Tr<int64_t> {
+    static constexpr bool kGrouped = false;
     using TC = int64_t;
     using TP = int64_t;
     static constexpr bool kIntInFloat = false;
@@ -93,6 +97,7 @@ struct Tr<int64_t> {
 
 template <>
 struct Tr<float> {
+    static constexpr bool kGrouped = false;
     using TC = float;
     using TP = float;
     static constexpr bool kIntInFloat = false;
@@ -117,6 +122,7 @@ struct Tr<float> {
 
 template <>
 struct Tr<double> {
+    static constexpr bool kGrouped = false;
     using TC = double;
     using TP = double;
     static constexpr bool kIntInFloat = false;
@@ -140,6 +146,7 @@ struct Tr<double> {
 // Symmetric coupling matrix in the table precision (tables) and in the unit-field precision.
 template <>
 struct Tr<i32f> {
+    static constexpr bool kGrouped = true;  // compiles the grouped step form (variants 20-23)
     using TC = float;
     using TP = int32_t;
     static constexpr bool kIntInFloat = true;
@@ -162,6 +169,7 @@ struct Tr<i32f> {
 // instruction.  The table rows are stored as packed deltas lo + 65536 * hi.
 template <>
 struct Tr<i16p> {
+    static constexpr bool kGrouped = false;
     using TC = uint32_t;
     using TP = int32_t;
     static constexpr bool kIntInFloat = false;
@@ -352,7 +360,10 @@ __global__ void tables_kernel(const Inst *insts)
     const int n = d.n, B = d.B, L = d.L;
     const long NB = 1l << B, NL = 1l << L;
     const long NM = kPacked ? NB / 2 : NB;  // words per interaction row
-    const long total = NB + NM * L + NL;
+    // the grouped scan (integers in FP32 lanes): after E_L, the minimum of E_L over each group of
+    // 16 walk steps
+    const long NLG = Tr<T>::kGrouped ? NL / 16 : 0;
+    const long total = NB + NM * L + NL + NLG;
     const F *W = field_matrix<T>(d);
     // M_int row r at column j: coupling of walked variable r to the suffix pattern j
     auto m_entry = [&](long r, long j) {
@@ -387,16 +398,28 @@ __global__ void tables_kernel(const Inst *insts)
                 ((TC *)d.M)[r * NM + w] = (TC)m_entry(r, w);
         } else {  // E_L(g(i)): energy of the i-th walked pattern, stored in walk order
             const long i = idx - NB - NM * L;
-            const long g = i ^ (i >> 1);
-            F acc = 0;
-            for (int r = 0; r < L; ++r) {
-                if (!((g >> r) & 1))
-                    continue;
-                acc += W[(B + r) * n + (B + r)];
-                for (int r2 = r + 1; r2 < L; ++r2)
-                    if ((g >> r2) & 1)
-                        acc += W[(B + r) * n + (B + r2)];
+            auto el_of = [&](long ii) {
+                const long g = ii ^ (ii >> 1);
+                F e = 0;
+                for (int r = 0; r < L; ++r) {
+                    if (!((g >> r) & 1))
+                        continue;
+                    e += W[(B + r) * n + (B + r)];
+                    for (int r2 = r + 1; r2 < L; ++r2)
+                        if ((g >> r2) & 1)
+                            e += W[(B + r) * n + (B + r2)];
+                }
+                return e;
+            };
+            if (i >= NL) {  // group minimum (grouped scans)
+                const long g0 = 16 * (i - NL);
+                F m = el_of(g0);
+                for (int t = 1; t < 16; ++t)
+                    m = min(m, el_of(g0 + t));
+                ((TC *)d.EL)[i] = (TC)m;
+                continue;
             }
+            const F acc = el_of(i);
             if constexpr (kPacked) {
                 if (d.el_fused)  // E_L - elmin in both halves, added to the packed minima of a step
                     ((uint32_t *)d.EL)[i] = (uint32_t)((TP)acc - d.elmin) * 0x10001u;
@@ -494,6 +517,32 @@ __device__ __forceinline__ void column_fields(F f0, int lane, F &lin_t, F (&lin_
 #pragma unroll
         for (int g = 0; g < (1 << i); ++g)
             lin_g[g + (1 << i)] = lin_g[g] + vb;
+    }
+}
+
+// One register-row Gray step of S columns, adds only: E[q] +- M[q], pairs of FP32 columns as one
+// f32x2 instruction where the add mode says so (4: all pairs, 5: every 2nd, 6: every 4th, 7: 3 of 4).
+template <class TC, int S, int ADDM, bool NEG>
+__device__ __forceinline__ void add_row(TC (&E)[S], const TC (&M)[S])
+{
+    if constexpr (ADDM >= 4 && std::is_same_v<TC, float>) {
+#pragma unroll
+        for (int q = 0; q < S; q += 2) {
+            const int pr = q / 2;
+            if (ADDM == 4 || (ADDM == 5 && pr % 2 == 0) || (ADDM == 6 && pr % 4 == 0) || (ADDM == 7 && pr % 4 != 0)) {
+                if constexpr (NEG)
+                    sub_f32x2(E[q], E[q + 1], M[q], M[q + 1]);
+                else
+                    add_f32x2(E[q], E[q + 1], M[q], M[q + 1]);
+            } else {
+                E[q] = NEG ? E[q] - M[q] : E[q] + M[q];
+                E[q + 1] = NEG ? E[q + 1] - M[q + 1] : E[q + 1] + M[q + 1];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < S; ++q)
+            E[q] = NEG ? E[q] - M[q] : E[q] + M[q];
     }
 }
 
@@ -632,6 +681,48 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
         }
     }
 
+    // Step form 2 (integers in FP32 lanes): the walk runs in groups of 16 states, and a group
+    // skips the min tree when no column of it can reach the threshold.  At a group's first state
+    // the exact column minimum m of each thread is taken; a register-row step adds +-M_r[q] to
+    // column q, so over the group's next 15 steps (rows 0-3, the same pattern in every group but
+    // for the sign of row 3, which alternates) the minimum never falls below m + D, D the
+    // smallest running sum of the steps' smallest column moves (min_q M_r[q] on an add,
+    // -max_q M_r[q] on a subtract), computed once per unit in int32 and rounded down.  With
+    // min E_L over the group's states (a table), m + D > uc - min E_L in every lane proves that
+    // the group holds no candidate, and it runs its adds alone.  m + D is summed rounding down;
+    // uc - min E_L is exact (|uc|, |E_L| and their difference stay below 2^24).
+    constexpr bool BOUND = ILV == 2 && Tr<T>::kGrouped;
+    static_assert(!BOUND || (RC >= 4 && MINM == 3), "the grouped form needs register rows 0-3 and 3-input mins");
+    // D per parity of the group index, rounded down to FP32
+    using DT = float;
+    DT Dgrp[2] = {0, 0};
+    if constexpr (BOUND) {
+        int64_t dpos[4], dneg[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            TC lo = Mr[r][0], hi = Mr[r][0];
+#pragma unroll
+            for (int q = 1; q < S; ++q) {
+                lo = emin(lo, Mr[r][q]);
+                hi = hi > Mr[r][q] ? hi : Mr[r][q];
+            }
+            dpos[r] = (int64_t)lo;
+            dneg[r] = -(int64_t)hi;
+        }
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+            int64_t cum = 0, lo = 0;
+#pragma unroll
+            for (int t = 1; t < 16; ++t) {
+                const int kk = ctzc(t);
+                const bool neg = kk == 3 ? par != 0 : ((t >> (kk + 1)) & 1) != 0;
+                cum += neg ? dneg[kk] : dpos[kk];
+                lo = min(lo, cum);
+            }
+            Dgrp[par] = __ll2float_rd(lo);
+        }
+    }
+
     // Threshold: a state is recorded when its energy is <= Treg (+ margin).
     {
         const TP tg = Tr<T>::thr_load(st);
@@ -723,6 +814,7 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
 
     if (!QUBO_DCHECK(L >= RC + 1 && L <= kMaxWalkBits && nblk * BODY == (1 << L), st, 3))
         return;
+    const TC *ELg = ELp + (1 << L);  // step form 2: min E_L over each group of 16 states
     for (int blk = 0; blk < nblk; ++blk) {
         const int i0 = blk * BODY;
         if constexpr (Tr<T>::kFloat) {
@@ -736,6 +828,50 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
         // moves the threshold) of (minimum over the columns + E_L of the step); a column can be
         // at or below the threshold exactly when its half's minimum is at or below uc.
         TC acc_lo, acc_hi, mprev;
+        if constexpr (BOUND) {
+            constexpr int NG = BODY / 16;
+            TC elg[NG];
+#pragma unroll
+            for (int g = 0; g < NG; ++g)
+                elg[g] = ELg[(i0 >> 4) + g];
+            static_for<NG>([&](auto gc) {
+                constexpr int g = decltype(gc)::value, p0 = 16 * g;
+                if constexpr (g > 0) {  // the step into the group's first state
+                    constexpr int kk = ctzc(p0);
+                    if constexpr (kk < RC) {
+                        add_row<TC, S, ADDM, ((p0 >> (kk + 1)) & 1) != 0>(E, Mr[kk]);
+                    } else {
+                        Pmid = P;
+                        high_flip(RC, (blk & 1) ? -1 : 1);
+                    }
+                }
+                const TC m0 = tree_min<TC, MINM, S>(E);
+                const bool skip = __all_sync(kFull, __fadd_rd(m0, Dgrp[g & 1]) > uc - elg[g]);
+                if (__builtin_expect(skip, 1)) {
+                    static_for<15>([&](auto tc) {
+                        constexpr int t = decltype(tc)::value + 1, p = 16 * decltype(gc)::value + t, kk = ctzc(t);
+                        add_row<TC, S, ADDM, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk]);
+                    });
+                } else {
+                    // the group's states as in the interleaved form: column minima + E_L, running
+                    // minimum compared with the threshold at the group's end
+                    TC ev[V], rm;
+                    static_for<16>([&](auto tc) {
+                        constexpr int t = decltype(tc)::value, p = 16 * decltype(gc)::value + t, kk = t > 0 ? ctzc(t) : 0;
+                        TC mc;
+                        if constexpr (t == 0)
+                            mc = m0;
+                        else
+                            mc = add_min_interleaved<TC, S, ADDM, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk], (TC)a.zero);
+                        if constexpr (t % V == 0)
+                            vload<TC>(ELp + i0 + p, ev);
+                        const TC mp = mc + ev[t % V];
+                        rm = t == 0 ? mp : emin(rm, mp);
+                    });
+                    hit = hit || rm <= uc;
+                }
+            });
+        } else {
         // Fast path: per step one add per column, a min over the columns, one add of the step's
         // E_L and half a 3-input min into the running minimum; one compare per half body.
         static_for<BODY>([&](auto pc) {
@@ -748,28 +884,7 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
             } else if constexpr (p > 0) {
                 constexpr int kk = ctzc(p);
                 if constexpr (kk < RC) {
-                    constexpr bool neg = (p >> (kk + 1)) & 1;
-                    if constexpr (ADDM >= 4 && std::is_same_v<TC, float>) {
-                        // pairs taken as f32x2: all (4), every 2nd (5), every 4th (6), 3 of 4 (7)
-#pragma unroll
-                        for (int q = 0; q < S; q += 2) {
-                            const int pr = q / 2;
-                            if (ADDM == 4 || (ADDM == 5 && pr % 2 == 0) || (ADDM == 6 && pr % 4 == 0) ||
-                                (ADDM == 7 && pr % 4 != 0)) {
-                                if constexpr (neg)
-                                    sub_f32x2(E[q], E[q + 1], Mr[kk][q], Mr[kk][q + 1]);
-                                else
-                                    add_f32x2(E[q], E[q + 1], Mr[kk][q], Mr[kk][q + 1]);
-                            } else {
-                                E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
-                                E[q + 1] = neg ? E[q + 1] - Mr[kk][q + 1] : E[q + 1] + Mr[kk][q + 1];
-                            }
-                        }
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < S; ++q)
-                            E[q] = neg ? E[q] - Mr[kk][q] : E[q] + Mr[kk][q];
-                    }
+                    add_row<TC, S, ADDM, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk]);
                 } else {
                     Pmid = P;
                     high_flip(RC, (blk & 1) ? -1 : 1);
@@ -795,6 +910,7 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
                 hit = acc_lo <= uc;  // before the row-RC flip moves uc
         });
         hit = hit || acc_hi <= uc;
+        }
         if (hit) {
             // Slow path (rare): rebuild every step of this body from the body-end registers and
             // record each column at or below the threshold.  Step p differs from the last step
@@ -1108,10 +1224,16 @@ __device__ __forceinline__ void scan_unit_packed(const ScanArgs &a, const Inst &
 
 
     };
-    if (d.el_fused)
-        walk(std::true_type{});
-    else
-        walk(std::false_type{});
+    if constexpr (ILV == 2) {
+        // fused-only kernel: the host runs it only on plans whose E_L is fused
+        if (QUBO_DCHECK(d.el_fused, st, 8))
+            walk(std::true_type{});
+    } else {
+        if (d.el_fused)
+            walk(std::true_type{});
+        else
+            walk(std::false_type{});
+    }
 }
 
 // Persistent work loop: a warp claims work units from the queue, kChunk at a time (the next claim

@@ -92,7 +92,7 @@ def test_packed_chosen_exactly_when_bounded(q, lim):
     assert (i["acc"] == "i16p") == (lo >= -32768 and hi <= 32767), (lo, hi, i["acc"])
 
 
-@pytest.mark.parametrize("variant", range(20))
+@pytest.mark.parametrize("variant", range(24))
 def test_packed_variants_agree(q, variant, monkeypatch):
     monkeypatch.setenv("QUBO_SCAN_VARIANT", str(variant))
     Q = wl.maxcut_qubo(29, 0.5, seed=91)

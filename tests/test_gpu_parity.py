@@ -370,7 +370,7 @@ def test_time_limit_returns_timeout(q):
 
 # --- compiled kernel variants and the n=44 FP32 configuration ---------------------------------
 
-@pytest.mark.parametrize("variant", range(20))
+@pytest.mark.parametrize("variant", range(24))
 def test_scan_variants_agree(q, variant, monkeypatch):
     monkeypatch.setenv("QUBO_SCAN_VARIANT", str(variant))
     Q = wl.upper_int(27, -300, 300, seed=90)
@@ -386,6 +386,37 @@ def test_scan_variants_agree(q, variant, monkeypatch):
     r = q.solve(Qf, topk=8)
     assert r.info["acc"] == "f32"
     check_float(r, oracle.solve(Qf, topk=8))
+
+
+@pytest.mark.parametrize("lim", [3, 300, 60000, 350000])
+def test_grouped_form_parity(q, lim, monkeypatch):
+    """The grouped step form (the default in FP32 lanes): groups of 16 Gray steps skip the min
+    over the columns while a lower bound proves they hold no candidate.  Entries from tie-heavy
+    (+-3, most groups reach the threshold, many ties) to the FP32-lane limit (the bound's sum
+    rounded down near 2^24; the largest entries leave the FP32 lanes for the int32 kernel, which
+    has no grouped form); top-16, K = 1 and the tie set against the oracle."""
+    for k, v in LANES["i32f"].items():
+        monkeypatch.setenv(k, v)
+    for n, seed in ((27, 120 + lim % 7), (29, 121)):
+        Q = wl.upper_int(n, -lim, lim, seed=seed)
+        r = q.solve(Q, topk=16, states_cap=4096)
+        assert r.info["grouped"] == (r.info["acc"] == "i32f"), r.info
+        assert r.info["variant"] == (20 if r.info["acc"] == "i32f" else 16), r.info
+        check_int(r, oracle.solve(Q, topk=16, cap=4096))
+        r1 = q.solve(Q, states_cap=4096)
+        check_int(r1, oracle.solve(Q, cap=4096))
+
+
+def test_grouped_form_fires_on_every_group(q, monkeypatch):
+    """All-zero couplings but the diagonal: every state's column part is equal, so every group's
+    bound reaches the threshold and the min tree runs everywhere; the 2^k tie set is exact."""
+    monkeypatch.setenv("QUBO_NO_I32Z", "1")
+    monkeypatch.setenv("QUBO_NO_I16P", "1")
+    Q = np.zeros((26, 26), dtype=np.int32)
+    Q[np.arange(10), np.arange(10)] = -1  # 2^16 ties: the first 10 variables set, the rest free
+    r = q.solve(Q, states_cap=1 << 16)
+    assert r.info["grouped"] == 1
+    check_int(r, oracle.solve(Q, cap=1 << 16))
 
 
 def test_config3_subcube_stays_fp32(q):
