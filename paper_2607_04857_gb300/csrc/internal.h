@@ -43,9 +43,9 @@ constexpr int kRegRows = 4;
 constexpr int kScanVariants = 24;
 constexpr int kVariantCols[kScanVariants] = {32, 16, 16, 16, 16, 16, 32, 16, 16, 16, 16, 16,
                                              16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
-constexpr int kVariantRegRows[kScanVariants] = {3, 4, 4, 3, 4, 4, 3, 4, 4, 4, 4, 3, 3, 3, 3, 3, 5, 5, 5, 5, 5, 4, 5, 4};
-constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 3, 3, 3, 3, 2, 3, 3, 3, 3, 4, 4, 4, 3, 3, 2, 2, 2, 2, 3, 3, 2, 3};
-constexpr int kVariantAddMode[kScanVariants] = {0, 6, 7, 0, 0, 4, 4, 5, 6, 5, 4, 6, 4, 0, 4, 4, 6, 0, 3, 2, 4, 4, 4, 6};
+constexpr int kVariantRegRows[kScanVariants] = {3, 4, 4, 3, 4, 4, 3, 4, 4, 4, 4, 3, 3, 3, 3, 3, 5, 5, 5, 5, 5, 4, 5, 5};
+constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 3, 3, 3, 3, 2, 3, 3, 3, 3, 4, 4, 4, 3, 3, 2, 2, 2, 2, 3, 3, 3, 3};
+constexpr int kVariantAddMode[kScanVariants] = {0, 6, 7, 0, 0, 4, 4, 5, 6, 5, 4, 6, 4, 0, 4, 4, 6, 0, 3, 2, 4, 4, 0, 6};
 constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3,
                                                   3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
 constexpr int kVariantInterleave[kScanVariants] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2};

@@ -709,18 +709,17 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
             dpos[r] = (int64_t)lo;
             dneg[r] = -(int64_t)hi;
         }
-#pragma unroll
-        for (int par = 0; par < 2; ++par) {
+        static_for<2>([&](auto pc) {
+            constexpr int par = decltype(pc)::value;
             int64_t cum = 0, lo = 0;
-#pragma unroll
-            for (int t = 1; t < 16; ++t) {
-                const int kk = ctzc(t);
-                const bool neg = kk == 3 ? par != 0 : ((t >> (kk + 1)) & 1) != 0;
+            static_for<15>([&](auto tc) {
+                constexpr int t = decltype(tc)::value + 1, kk = ctzc(t);
+                constexpr bool neg = kk == 3 ? par != 0 : ((t >> (kk + 1)) & 1) != 0;
                 cum += neg ? dneg[kk] : dpos[kk];
                 lo = min(lo, cum);
-            }
+            });
             Dgrp[par] = __ll2float_rd(lo);
-        }
+        });
     }
 
     // Threshold: a state is recorded when its energy is <= Treg (+ margin).
