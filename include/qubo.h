@@ -154,9 +154,9 @@ typedef struct {
     int32_t variant;          /* plan: compiled scan variant (-1: states evaluated directly) */
     int32_t grouped;          /* plan: 1 when the scan runs in groups of 16 Gray steps that skip
                                  the min over the columns while a per-thread lower bound of the
-                                 column minimum proves the group holds no candidate (integers in
-                                 FP32 lanes, variants 20-23; every state's column add still
-                                 runs); 0 otherwise */
+                                 column minimum proves the group holds no candidate (FP32
+                                 column adds: integers in FP32 lanes and FP32, variants 20-23;
+                                 every state's column add still runs); 0 otherwise */
 } qubo_result;
 
 /*

@@ -570,6 +570,11 @@ int job_stage(Workspace &ws, Job &j, size_t extra_arena = 0)
         d.clampC = h.clampC;
         d.el_fused = j.acc == ACC_I16P ? h.el_fused : 0;
         d.elmin = h.elmin;
+        d.geps = 0.0f;
+        if (j.acc == ACC_F32) {  // 16 ulp of beta: every column and E_L value is at most beta
+            const float b = (float)h.beta;
+            d.geps = 16.0f * (std::nextafter(b, std::numeric_limits<float>::infinity()) - b);
+        }
         d.unit_begin = h.unit_begin;
         d.units = h.units;
         d.sub_base = h.sub_base;

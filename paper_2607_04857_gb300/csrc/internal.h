@@ -35,8 +35,7 @@ constexpr int kRegRows = 4;
 // interleaved form, one integer column in four / in eight updated by a 3-input add on the ALU
 // pipe), 2- or 3-input mins, and the step form: 0, all adds first, then the min tree; 1, the adds
 // interleaved with the first level of the min tree (each triple of columns reduced as soon as its
-// adds are issued); 2 (integers in FP32 lanes; form 1 for the other accumulators), the grouped
-// form: groups of 16 steps skip the min tree while a per-thread lower bound of the column
+// adds are issued); 2 (integers in FP32 lanes and FP32; form 1 for int32), the grouped form: groups of 16 steps skip the min tree while a per-thread lower bound of the column
 // minimum, moved by the steps' smallest column deltas, proves that no column can reach the
 // threshold.  The 8-byte
 // accumulators compile one variant: S = 16 with variant 0's register rows, blocks and min inputs.
@@ -49,20 +48,21 @@ constexpr int kVariantAddMode[kScanVariants] = {0, 6, 7, 0, 0, 4, 4, 5, 6, 5, 4,
 constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3,
                                                   3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
 constexpr int kVariantInterleave[kScanVariants] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2};
-// The step form a kernel of an accumulator compiles for a variant: the grouped form only for
-// integers in FP32 lanes.
-constexpr int step_form(int variant, bool int_in_fp32)
+// The step form a kernel of an accumulator compiles for a variant: the grouped form only for FP32
+// column adds (integers in FP32 lanes, FP32).
+constexpr int step_form(int variant, bool fp32_columns)
 {
-    return kVariantInterleave[variant] == 2 && !int_in_fp32 ? 1 : kVariantInterleave[variant];
+    return kVariantInterleave[variant] == 2 && !fp32_columns ? 1 : kVariantInterleave[variant];
 }
 // Whether a plan's scan kernel runs the grouped form.
 constexpr bool grouped_form(Acc acc, int variant)
 {
-    return acc == ACC_I32F && variant >= 0 && variant < kScanVariants && kVariantInterleave[variant] == 2;
+    return (acc == ACC_I32F || acc == ACC_F32) && variant >= 0 && variant < kScanVariants &&
+           kVariantInterleave[variant] == 2;
 }
 // Default variant per 4-byte accumulator (measured on GB300; see the profiles).
 constexpr int kDefaultVariantI32 = 16;
-constexpr int kDefaultVariantF32 = 16;
+constexpr int kDefaultVariantF32 = 22;
 constexpr int kDefaultVariantI32F = 20;
 constexpr int kDefaultVariantI16P = 14;
 // Compiled variants of the packed 16-bit scan: S words per thread (2 S columns), register rows,
@@ -136,6 +136,7 @@ struct Inst {
     int32_t el_fused;     // ACC_I16P: E_L stored as (E_L - elmin) in both 16-bit halves and added to the
                           // packed column minima without a carry (the host proves the sums fit 16 bits)
     int32_t elmin;        // ACC_I16P with el_fused: a lower bound of every E_L value
+    float geps;           // ACC_F32, grouped form: rounding allowance of a group's column updates
 };
 
 // Mutable per-instance state, updated with atomics.

@@ -594,6 +594,8 @@ int plan_run(HostInst &h, int fix_bits, uint64_t fix_value, int split_k, int wal
     h.variant = acc_bytes(h.acc) == 4 ? pick_variant(h.acc, variant_req) : 0;
     if (acc_bytes(h.acc) == 4)
         h.variant = fit_variant(h, fix_bits, split_k, walk_bits, variant_req, h.variant);
+    if (h.acc == ACC_I16P)  // the fused-E_L-only build of the variant when E_L is fused
+        h.variant = packed_variant_for(h.variant, h.el_fused);
     return plan(h, fix_bits, fix_value, split_k, walk_bits);
 }
 

@@ -97,7 +97,7 @@ struct Tr<int64_t> {
 
 template <>
 struct Tr<float> {
-    static constexpr bool kGrouped = false;
+    static constexpr bool kGrouped = true;
     using TC = float;
     using TP = float;
     static constexpr bool kIntInFloat = false;
@@ -360,8 +360,8 @@ __global__ void tables_kernel(const Inst *insts)
     const int n = d.n, B = d.B, L = d.L;
     const long NB = 1l << B, NL = 1l << L;
     const long NM = kPacked ? NB / 2 : NB;  // words per interaction row
-    // the grouped scan (integers in FP32 lanes): after E_L, the minimum of E_L over each group of
-    // 16 walk steps
+    // the grouped scans (integers in FP32 lanes, FP32): after E_L, the minimum of E_L over each
+    // group of 16 walk steps, as stored
     const long NLG = Tr<T>::kGrouped ? NL / 16 : 0;
     const long total = NB + NM * L + NL + NLG;
     const F *W = field_matrix<T>(d);
@@ -411,7 +411,7 @@ __global__ void tables_kernel(const Inst *insts)
                 }
                 return e;
             };
-            if (i >= NL) {  // group minimum (grouped scans)
+            if (i >= NL) {  // group minimum (grouped scans; rounding to TC is monotonic)
                 const long g0 = 16 * (i - NL);
                 F m = el_of(g0);
                 for (int t = 1; t < 16; ++t)
@@ -690,14 +690,18 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
     // -max_q M_r[q] on a subtract), computed once per unit in int32 and rounded down.  With
     // min E_L over the group's states (a table), m + D > uc - min E_L in every lane proves that
     // the group holds no candidate, and it runs its adds alone.  m + D is summed rounding down;
-    // uc - min E_L is exact (|uc|, |E_L| and their difference stay below 2^24).
+    // with integers in FP32 lanes uc - min E_L is exact (|uc|, |E_L| and their difference stay
+    // below 2^24).  FP32 columns take 16 ulp of beta (geps) off the left side, more than the
+    // rounding of the group's 15 adds and of the E_L add the interleaved form compares, and round
+    // uc - min E_L up, so a group is skipped only when the interleaved form records nothing in it.
     constexpr bool BOUND = ILV == 2 && Tr<T>::kGrouped;
     static_assert(!BOUND || (RC >= 4 && MINM == 3), "the grouped form needs register rows 0-3 and 3-input mins");
-    // D per parity of the group index, rounded down to FP32
-    using DT = float;
-    DT Dgrp[2] = {0, 0};
+    // D per parity of the group index, rounded down to FP32 (summed exactly in int64 for integer
+    // columns, in FP64 for FP32 columns, whose table rows are FP32 values)
+    using DD = std::conditional_t<Tr<T>::kFloat, double, int64_t>;
+    float Dgrp[2] = {0, 0};
     if constexpr (BOUND) {
-        int64_t dpos[4], dneg[4];
+        DD dpos[4], dneg[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             TC lo = Mr[r][0], hi = Mr[r][0];
@@ -706,19 +710,22 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
                 lo = emin(lo, Mr[r][q]);
                 hi = hi > Mr[r][q] ? hi : Mr[r][q];
             }
-            dpos[r] = (int64_t)lo;
-            dneg[r] = -(int64_t)hi;
+            dpos[r] = (DD)lo;
+            dneg[r] = -(DD)hi;
         }
         static_for<2>([&](auto pc) {
             constexpr int par = decltype(pc)::value;
-            int64_t cum = 0, lo = 0;
+            DD cum = 0, lo = 0;
             static_for<15>([&](auto tc) {
                 constexpr int t = decltype(tc)::value + 1, kk = ctzc(t);
                 constexpr bool neg = kk == 3 ? par != 0 : ((t >> (kk + 1)) & 1) != 0;
                 cum += neg ? dneg[kk] : dpos[kk];
                 lo = min(lo, cum);
             });
-            Dgrp[par] = __ll2float_rd(lo);
+            if constexpr (Tr<T>::kFloat)
+                Dgrp[par] = __double2float_rd(lo);
+            else
+                Dgrp[par] = __ll2float_rd(lo);
         });
     }
 
@@ -845,7 +852,12 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
                     }
                 }
                 const TC m0 = tree_min<TC, MINM, S>(E);
-                const bool skip = __all_sync(kFull, __fadd_rd(m0, Dgrp[g & 1]) > uc - elg[g]);
+                bool clear;
+                if constexpr (Tr<T>::kFloat)  // less the rounding of the group's adds and E_L add
+                    clear = __fadd_rd(__fadd_rd(m0, Dgrp[g & 1]), -d.geps) > __fsub_ru(uc, elg[g]);
+                else
+                    clear = __fadd_rd(m0, Dgrp[g & 1]) > uc - elg[g];
+                const bool skip = __all_sync(kFull, clear);
                 if (__builtin_expect(skip, 1)) {
                     static_for<15>([&](auto tc) {
                         constexpr int t = decltype(tc)::value + 1, p = 16 * decltype(gc)::value + t, kk = ctzc(t);
