@@ -759,6 +759,12 @@ def main():
             issue = sms * LANES_PER_SM * clocks["sm_mhz"] * 1e6 / ips
             roof["issue_roofline"] = {"inst_per_state": ips, "states_per_s": issue,
                                       "frac": (per_launch_states / mean_scan) / issue}
+            if grouped and acc == "i32f":
+                roof["issue_roofline"]["note"] = (
+                    "the column adds issue as paired f32x2 instructions (two columns per instruction, two "
+                    "datapath cycles), so instruction issue is not this kernel's bound: the FP32 add datapath is "
+                    "(roofline.frac); the same form with scalar adds (QUBO_SCAN_VARIANT=22) issues twice the adds "
+                    "and runs slower")
 
     sec = None
     if W["name"] == "n50_int32" and world == 1 and not args.no_secondary:
