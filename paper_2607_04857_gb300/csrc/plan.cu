@@ -204,25 +204,38 @@ int pick_variant(Acc acc, int requested) { return requested >= 0 ? requested : s
 
 // The default variant keeps five walked rows in registers and needs walks of at least six bits.
 // When the walk is shorter (the caller's walk_bits, split_k leaving fewer walked bits, or a
-// (sub)cube with fewer free bits beyond the suffix) and the caller named no variant, the run
-// takes the measured best variant with fewer register rows and the same columns per thread, so
-// the suffix split is unchanged.
+// (sub)cube too small for 2^kTargetUnitsLog2 units walking four unrolled bodies each) and the
+// caller named no variant, the run takes the measured best variant with fewer register rows and
+// the same columns per thread, so the suffix split is unchanged; failing all, the one with the
+// fewest rows.  A small instance's units are then short bodies: a unit that runs its unrolled
+// body only once or twice pays for the straight-line code's instruction fetch, and a 64-step
+// body made every launch of a small solve about 0.2 ms longer than an 8-step one.
 int fit_variant(const HostInst &h, int fix_bits, int split_k, int walk_bits, int variant_req, int variant)
 {
     if (variant_req >= 0 || std::getenv("QUBO_SCAN_VARIANT"))
         return variant;
     const int B = acc_suffix_bits(h.acc, variant);
-    const int L = split_k > 0 ? h.n - B - split_k : (walk_bits > 0 ? walk_bits : h.n - fix_bits - B);
+    // the planner's own walk should give a unit at least four unrolled bodies (two more bits)
+    const int slack = split_k > 0 || walk_bits > 0 ? 0 : 2;
+    const int L = split_k > 0 ? h.n - B - split_k
+                              : (walk_bits > 0 ? walk_bits : h.n - fix_bits - B - kTargetUnitsLog2 - slack);
     if (L >= reg_rows_of(h.acc, variant) + 1)
         return variant;
     static constexpr int kShorter4[] = {8, 3};       // 4 register rows (interleaved), 3
     static constexpr int kShorterP[] = {13, 8, 11};  // packed: 4, 3, 2 register rows (interleaved)
     const int *cand = h.acc == ACC_I16P ? kShorterP : kShorter4;
     const int nc = h.acc == ACC_I16P ? 3 : 2;
-    for (int c = 0; c < nc; ++c)
-        if (acc_suffix_bits(h.acc, cand[c]) == B && L >= reg_rows_of(h.acc, cand[c]) + 1)
+    int last = variant;
+    for (int c = 0; c < nc; ++c) {
+        if (acc_suffix_bits(h.acc, cand[c]) != B)
+            continue;
+        if (L >= reg_rows_of(h.acc, cand[c]) + 1)
             return cand[c];
-    return variant;
+        last = cand[c];
+    }
+    // no candidate fits the walk the planner aims at: the fewest rows, if the caller's walk allows
+    const int Lmax = split_k > 0 ? h.n - B - split_k : (walk_bits > 0 ? walk_bits : h.n - fix_bits - B);
+    return Lmax >= reg_rows_of(h.acc, last) + 1 ? last : variant;
 }
 
 // Integer energies can be scanned exactly in FP32 lanes when every value held in an FP32 lane stays

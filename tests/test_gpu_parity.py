@@ -399,11 +399,12 @@ def test_grouped_form_parity(q, lim, monkeypatch):
         monkeypatch.setenv(k, v)
     for n, seed in ((27, 120 + lim % 7), (29, 121)):
         Q = wl.upper_int(n, -lim, lim, seed=seed)
-        r = q.solve(Q, topk=16, states_cap=4096)
+        # an 8-bit walk: small instances otherwise take a short-body variant
+        r = q.solve(Q, topk=16, states_cap=4096, walk_bits=8)
         assert r.info["grouped"] == (r.info["acc"] == "i32f"), r.info
         assert r.info["variant"] == (20 if r.info["acc"] == "i32f" else 16), r.info
         check_int(r, oracle.solve(Q, topk=16, cap=4096))
-        r1 = q.solve(Q, states_cap=4096)
+        r1 = q.solve(Q, states_cap=4096, walk_bits=8)
         check_int(r1, oracle.solve(Q, cap=4096))
 
 
@@ -414,7 +415,7 @@ def test_grouped_form_fires_on_every_group(q, monkeypatch):
     monkeypatch.setenv("QUBO_NO_I16P", "1")
     Q = np.zeros((26, 26), dtype=np.int32)
     Q[np.arange(10), np.arange(10)] = -1  # 2^16 ties: the first 10 variables set, the rest free
-    r = q.solve(Q, states_cap=1 << 16)
+    r = q.solve(Q, states_cap=1 << 16, walk_bits=8)
     assert r.info["grouped"] == 1
     check_int(r, oracle.solve(Q, cap=1 << 16))
 

@@ -118,7 +118,8 @@ def test_plan_shapes_are_consistent(q, seed):
             continue
         assert p["split_k"] + p["walk_bits"] + p["suffix_bits"] == n, p
         factored = p["acc"] in ("i32z", "f32z")
-        assert p["split_k"] >= fb and p["walk_bits"] >= (3 if factored else 4), p
+        assert p["split_k"] >= fb and p["walk_bits"] >= (3 if factored else p["reg_rows"] + 1), p
+        assert factored or p["reg_rows"] >= 2, p
         if factored:
             assert 3 <= p["zero_rows"] <= p["walk_bits"], p
 
