@@ -5,7 +5,7 @@
     python tests/golden/make_golden.py cfg5_sub  # n=50, one 2^40-state sub-cube (~1 h, 8 cores)
     python tests/golden/make_golden.py cfg3_sub  # n=44 FP32, one 2^40-state sub-cube (~1 h, 8 cores)
     python tests/golden/make_golden.py cfg3_step # n=44 FP32, one benchmark step of 2^42 states (~4 h)
-    python tests/golden/make_golden.py cfg5_step # n=50, one benchmark step of 2^43 states (~8 h)
+    python tests/golden/make_golden.py cfg5_step # n=50, one benchmark step of 2^43 states (~9 h, 8 cores)
 
 The inputs come from the seeded generators in paper_2607_04857_gb300/workloads.py; the paper's
 benchmark matrices are uniformly random (Sec. 5.3), so the instances are synthetic stand-ins of
