@@ -35,33 +35,33 @@ constexpr int kRegRows = 4;
 // interleaved form, one integer column in four / in eight updated by a 3-input add on the ALU
 // pipe), 2- or 3-input mins, and the step form: 0, all adds first, then the min tree; 1, the adds
 // interleaved with the first level of the min tree (each triple of columns reduced as soon as its
-// adds are issued); 2 (int32, integers in FP32 lanes and FP32), the grouped form: groups of 16 steps skip the min tree while a per-thread lower bound of the column
+// adds are issued); 2 (integers in FP32 lanes and FP32; form 1 for int32), the grouped form: groups of 16 steps skip the min tree while a per-thread lower bound of the column
 // minimum, moved by the steps' smallest column deltas, proves that no column can reach the
 // threshold.  The 8-byte
 // accumulators compile one variant: S = 16 with variant 0's register rows, blocks and min inputs.
 constexpr int kScanVariants = 24;
 constexpr int kVariantCols[kScanVariants] = {32, 16, 16, 16, 16, 16, 32, 16, 16, 16, 16, 16,
                                              16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
-constexpr int kVariantRegRows[kScanVariants] = {3, 4, 4, 3, 4, 4, 3, 4, 4, 4, 4, 3, 3, 3, 3, 3, 5, 5, 5, 5, 5, 5, 5, 5};
-constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 3, 3, 3, 3, 2, 3, 3, 3, 3, 4, 4, 4, 3, 3, 2, 2, 2, 2, 3, 2, 3, 3};
+constexpr int kVariantRegRows[kScanVariants] = {3, 4, 4, 3, 4, 4, 3, 4, 4, 4, 4, 3, 3, 3, 3, 3, 5, 5, 5, 5, 5, 4, 5, 5};
+constexpr int kVariantMinBlocks[kScanVariants] = {2, 3, 3, 3, 3, 3, 2, 3, 3, 3, 3, 4, 4, 4, 3, 3, 2, 2, 2, 2, 3, 3, 3, 3};
 constexpr int kVariantAddMode[kScanVariants] = {0, 6, 7, 0, 0, 4, 4, 5, 6, 5, 4, 6, 4, 0, 4, 4, 6, 0, 3, 2, 4, 4, 0, 6};
 constexpr int kVariantMinInputs[kScanVariants] = {3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3,
                                                   3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3, 3};
 constexpr int kVariantInterleave[kScanVariants] = {0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 0, 1, 1, 1, 1, 1, 2, 2, 2, 2};
-// The step form a kernel of an accumulator compiles for a variant: the grouped form only for the
-// 4-byte column scans that have one (int32, integers in FP32 lanes, FP32).
-constexpr int step_form(int variant, bool grouped_scan)
+// The step form a kernel of an accumulator compiles for a variant: the grouped form only for FP32
+// column adds (integers in FP32 lanes, FP32).
+constexpr int step_form(int variant, bool fp32_columns)
 {
-    return kVariantInterleave[variant] == 2 && !grouped_scan ? 1 : kVariantInterleave[variant];
+    return kVariantInterleave[variant] == 2 && !fp32_columns ? 1 : kVariantInterleave[variant];
 }
 // Whether a plan's scan kernel runs the grouped form.
 constexpr bool grouped_form(Acc acc, int variant)
 {
-    return (acc == ACC_I32 || acc == ACC_I32F || acc == ACC_F32) && variant >= 0 && variant < kScanVariants &&
+    return (acc == ACC_I32F || acc == ACC_F32) && variant >= 0 && variant < kScanVariants &&
            kVariantInterleave[variant] == 2;
 }
 // Default variant per 4-byte accumulator (measured on GB300; see the profiles).
-constexpr int kDefaultVariantI32 = 20;
+constexpr int kDefaultVariantI32 = 16;
 constexpr int kDefaultVariantF32 = 22;
 constexpr int kDefaultVariantI32F = 20;
 constexpr int kDefaultVariantI16P = 14;

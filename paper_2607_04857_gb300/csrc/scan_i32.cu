@@ -10,7 +10,7 @@ constexpr auto kernel_of()
     constexpr int kS = cols_per_thread(sizeof(int32_t), VAR);
     static_assert(ilog2c(32 * kS) == suffix_bits(sizeof(int32_t), VAR), "suffix bits must match the column layout");
     return scan_kernel<int32_t, kS, kVariantRegRows[VAR], K1, kVariantMinBlocks[VAR], kVariantAddMode[VAR],
-                       kVariantMinInputs[VAR], step_form(VAR, true)>;
+                       kVariantMinInputs[VAR], step_form(VAR, false)>;
 }
 
 template <bool K1, int... V>

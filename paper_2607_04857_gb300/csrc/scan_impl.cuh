@@ -55,9 +55,9 @@ struct i16p {};
 
 template <>
 struct Tr<int32_t> {
-    // Grouped step form: a skipped group's column updates are issued as opaque adds (add_row_kept),
-    // since the compiler would otherwise fold the group's 15 associative integer adds into one.
-    static constexpr bool kGrouped = true;
+    // No grouped step form: integer adds are associative, so the compiler folds a skipped group's
+    // 15 column updates into one, and the scan would no longer form every state's energy.
+    static constexpr bool kGrouped = false;
     using TC = int32_t;
     using TP = int32_t;
     static constexpr bool kIntInFloat = false;
@@ -360,8 +360,8 @@ __global__ void tables_kernel(const Inst *insts)
     const int n = d.n, B = d.B, L = d.L;
     const long NB = 1l << B, NL = 1l << L;
     const long NM = kPacked ? NB / 2 : NB;  // words per interaction row
-    // the grouped scans (int32, integers in FP32 lanes, FP32): after E_L, the minimum of E_L over
-    // each group of 16 walk steps, as stored
+    // the grouped scans (integers in FP32 lanes, FP32): after E_L, the minimum of E_L over each
+    // group of 16 walk steps, as stored
     const long NLG = Tr<T>::kGrouped ? NL / 16 : 0;
     const long total = NB + NM * L + NL + NLG;
     const F *W = field_matrix<T>(d);
@@ -546,21 +546,6 @@ __device__ __forceinline__ void add_row(TC (&E)[S], const TC (&M)[S])
     }
 }
 
-// The same step on int32 columns as opaque 32-bit adds: integer addition is associative, and
-// without them the compiler folds a skipped group's 15 updates of a column into one, so that the
-// states between would no longer be formed.
-template <int S, bool NEG>
-__device__ __forceinline__ void add_row_kept(int32_t (&E)[S], const int32_t (&M)[S])
-{
-#pragma unroll
-    for (int q = 0; q < S; ++q) {
-        if constexpr (NEG)
-            asm("sub.s32 %0, %0, %1;" : "+r"(E[q]) : "r"(M[q]));
-        else
-            asm("add.s32 %0, %0, %1;" : "+r"(E[q]) : "r"(M[q]));
-    }
-}
-
 // One register-row Gray step of S columns fused with the min over them, in an interleaved order:
 // each triple of columns is reduced by a 3-input min as soon as its adds are issued, so the FMA
 // pipe (adds) and the ALU pipe (mins) receive alternating work from one warp.  Pair q of columns
@@ -714,8 +699,7 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
     // D per parity of the group index, rounded down to FP32 (summed exactly in int64 for integer
     // columns, in FP64 for FP32 columns, whose table rows are FP32 values)
     using DD = std::conditional_t<Tr<T>::kFloat, double, int64_t>;
-    using DG = std::conditional_t<std::is_same_v<TC, float>, float, int64_t>;  // int32 columns: exact
-    DG Dgrp[2] = {0, 0};
+    float Dgrp[2] = {0, 0};
     if constexpr (BOUND) {
         DD dpos[4], dneg[4];
 #pragma unroll
@@ -740,10 +724,8 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
             });
             if constexpr (Tr<T>::kFloat)
                 Dgrp[par] = __double2float_rd(lo);
-            else if constexpr (std::is_same_v<TC, float>)
-                Dgrp[par] = __ll2float_rd(lo);
             else
-                Dgrp[par] = lo;
+                Dgrp[par] = __ll2float_rd(lo);
         });
     }
 
@@ -873,18 +855,13 @@ __device__ __forceinline__ void scan_unit(const ScanArgs &a, const Inst &d, int 
                 bool clear;
                 if constexpr (Tr<T>::kFloat)  // less the rounding of the group's adds and E_L add
                     clear = __fadd_rd(__fadd_rd(m0, Dgrp[g & 1]), -d.geps) > __fsub_ru(uc, elg[g]);
-                else if constexpr (std::is_same_v<TC, float>)
+                else
                     clear = __fadd_rd(m0, Dgrp[g & 1]) > uc - elg[g];
-                else  // int32 columns: in int64, exact
-                    clear = (int64_t)m0 + Dgrp[g & 1] > (int64_t)uc - (int64_t)elg[g];
                 const bool skip = __all_sync(kFull, clear);
                 if (__builtin_expect(skip, 1)) {
                     static_for<15>([&](auto tc) {
                         constexpr int t = decltype(tc)::value + 1, p = 16 * decltype(gc)::value + t, kk = ctzc(t);
-                        if constexpr (std::is_same_v<TC, int32_t>)
-                            add_row_kept<S, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk]);
-                        else
-                            add_row<TC, S, ADDM, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk]);
+                        add_row<TC, S, ADDM, ((p >> (kk + 1)) & 1) != 0>(E, Mr[kk]);
                     });
                 } else {
                     // the group's states as in the interleaved form: column minima + E_L, running

@@ -388,22 +388,21 @@ def test_scan_variants_agree(q, variant, monkeypatch):
     check_float(r, oracle.solve(Qf, topk=8))
 
 
-@pytest.mark.parametrize("lanes", ["i32f", "i32"])
 @pytest.mark.parametrize("lim", [3, 300, 60000, 350000])
-def test_grouped_form_parity(q, lanes, lim, monkeypatch):
-    """The grouped step form (the default for int32 and FP32-lane columns): groups of 16 Gray
-    steps skip the min over the columns while a lower bound proves they hold no candidate.
-    Entries from tie-heavy (+-3, most groups reach the threshold, many ties) to the FP32-lane
-    limit (the bound's sum rounded down near 2^24; the largest entries leave the FP32 lanes for
-    the int32 kernel); top-16, K = 1 and the tie set against the oracle."""
-    for k, v in LANES[lanes].items():
+def test_grouped_form_parity(q, lim, monkeypatch):
+    """The grouped step form (the default in FP32 lanes): groups of 16 Gray steps skip the min
+    over the columns while a lower bound proves they hold no candidate.  Entries from tie-heavy
+    (+-3, most groups reach the threshold, many ties) to the FP32-lane limit (the bound's sum
+    rounded down near 2^24; the largest entries leave the FP32 lanes for the int32 kernel, which
+    has no grouped form); top-16, K = 1 and the tie set against the oracle."""
+    for k, v in LANES["i32f"].items():
         monkeypatch.setenv(k, v)
     for n, seed in ((27, 120 + lim % 7), (29, 121)):
         Q = wl.upper_int(n, -lim, lim, seed=seed)
         # an 8-bit walk: small instances otherwise take a short-body variant
         r = q.solve(Q, topk=16, states_cap=4096, walk_bits=8)
-        assert r.info["acc"] in (lanes, "i32"), r.info
-        assert r.info["grouped"] == 1 and r.info["variant"] == 20, r.info
+        assert r.info["grouped"] == (r.info["acc"] == "i32f"), r.info
+        assert r.info["variant"] == (20 if r.info["acc"] == "i32f" else 16), r.info
         check_int(r, oracle.solve(Q, topk=16, cap=4096))
         r1 = q.solve(Q, states_cap=4096, walk_bits=8)
         check_int(r1, oracle.solve(Q, cap=4096))
@@ -411,17 +410,14 @@ def test_grouped_form_parity(q, lanes, lim, monkeypatch):
 
 def test_grouped_form_fires_on_every_group(q, monkeypatch):
     """All-zero couplings but the diagonal: every state's column part is equal, so every group's
-    bound reaches the threshold and the min tree runs everywhere; the 2^k tie set is exact, in
-    FP32 lanes and in the int32 kernel."""
+    bound reaches the threshold and the min tree runs everywhere; the 2^k tie set is exact."""
     monkeypatch.setenv("QUBO_NO_I32Z", "1")
     monkeypatch.setenv("QUBO_NO_I16P", "1")
     Q = np.zeros((26, 26), dtype=np.int32)
     Q[np.arange(10), np.arange(10)] = -1  # 2^16 ties: the first 10 variables set, the rest free
-    o = oracle.solve(Q, cap=1 << 16)
-    for int32 in (False, True):
-        r = q.solve(Q, states_cap=1 << 16, walk_bits=8, int32=int32)
-        assert r.info["grouped"] == 1 and r.info["acc"] == ("i32" if int32 else "i32f")
-        check_int(r, o)
+    r = q.solve(Q, states_cap=1 << 16, walk_bits=8)
+    assert r.info["grouped"] == 1
+    check_int(r, oracle.solve(Q, cap=1 << 16))
 
 
 def test_config3_subcube_stays_fp32(q):
